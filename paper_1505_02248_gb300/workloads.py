@@ -1,0 +1,132 @@
+"""Seeded synthetic inputs for the LEM workloads (shared by the tests, the bench and the
+oracle's callers; this module holds none of the method's arithmetic).
+
+Every generator takes an explicit seed and uses numpy's PCG64. The workloads mirror the
+paper's model problems (Eq. ibv / Eq. ibv2d: advection-diffusion with constant or variable
+coefficients, Sec. 4) at the sizes the GPU path is built for:
+
+* ``heat1d``      1D heat, N = 1024, Dirichlet, mu = nu dt / h^2 = 10, 16 tiles of 64, H = 16,
+                  u0 = 8 sine modes with N(0, 1) amplitudes.
+* ``advdiff2d``   2D periodic advection-diffusion, 2048^2, h = 1, dt = 4, nu = 5 (mu = 20),
+                  velocity (1, 0.5) (C_x = 4, C_y = 2), first-order upwind + 5-point
+                  Laplacian, tiles 32^2 + H = 8, u0 = Gaussian random field (length 16 h).
+* ``vardiff2d``   2D Dirichlet diffusion-reaction div(k grad u) + u - u^3, 1024^2,
+                  k = exp(GRF(32 h)) (lognormal, sigma = 1), tiles 16^2 + H = 6.
+
+Stencil coefficients follow the C-ABI convention: entries of A (not dt-scaled) in the
+order C, W, E, S, N, where W/E are the x - 1 / x + 1 neighbours and S/N the y - 1 / y + 1
+neighbours of a row-major [y][x] mesh.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# --------------------------------------------------------------------------- fields
+def sine_modes_1d(n: int, nmodes: int, seed: int):
+    """u0_j = sum_{k=1..nmodes} a_k sin(pi k j / (n + 1)), j = 1..n, a_k ~ N(0, 1)."""
+    a = rng(seed).standard_normal(nmodes)
+    j = np.arange(1, n + 1)
+    u0 = np.zeros(n)
+    for k in range(1, nmodes + 1):
+        u0 += a[k - 1] * np.sin(np.pi * k * j / (n + 1))
+    return u0, {k: float(a[k - 1]) for k in range(1, nmodes + 1)}
+
+
+def grf_2d(shape, ell: float, seed: int, crop_from=None) -> np.ndarray:
+    """Gaussian random field: white N(0,1) noise filtered by exp(-|kappa|^2 ell^2 / 4)
+    in Fourier space, normalised to zero mean and unit standard deviation.
+    ``crop_from`` generates on a larger periodic mesh and keeps the top-left corner
+    (used for non-periodic problems)."""
+    gshape = tuple(crop_from) if crop_from is not None else tuple(shape)
+    w = rng(seed).standard_normal(gshape)
+    ky = 2 * np.pi * np.fft.fftfreq(gshape[0])[:, None]
+    kx = 2 * np.pi * np.fft.fftfreq(gshape[1])[None, :]
+    filt = np.exp(-(kx ** 2 + ky ** 2) * ell ** 2 / 4.0)
+    f = np.real(np.fft.ifft2(np.fft.fft2(w) * filt))
+    f = f[: shape[0], : shape[1]]
+    f = f - f.mean()
+    return f / f.std()
+
+
+def grf_1d(n: int, ell: float, seed: int) -> np.ndarray:
+    w = rng(seed).standard_normal(n)
+    k = 2 * np.pi * np.fft.fftfreq(n)
+    f = np.real(np.fft.ifft(np.fft.fft(w) * np.exp(-k ** 2 * ell ** 2 / 4.0)))
+    f = f - f.mean()
+    return f / f.std()
+
+
+# --------------------------------------------------------------------------- stencils
+def stencil_heat_1d(nu: float, h: float) -> dict:
+    """nu u_xx, centred: C = -2 nu/h^2, W = E = nu/h^2."""
+    d = nu / h ** 2
+    return {"C": -2 * d, "W": d, "E": d}
+
+
+def stencil_advdiff_1d(nu: float, a: float, h: float, upwind: bool = False) -> dict:
+    """-a u_x + nu u_xx: centred advection (Sec. 4 1D tests) or first-order upwind (a >= 0)."""
+    d = nu / h ** 2
+    if upwind:
+        c = a / h
+        return {"C": -2 * d - c, "W": d + c, "E": d}
+    c = a / (2 * h)
+    return {"C": -2 * d, "W": d + c, "E": d - c}
+
+
+def stencil_advdiff_2d(nu: float, ax: float, ay: float, h: float) -> dict:
+    """-a . grad u + nu Lap u with first-order upwind for a >= 0 and the 5-point Laplacian."""
+    d = nu / h ** 2
+    cx, cy = ax / h, ay / h
+    return {"C": -4 * d - cx - cy, "W": d + cx, "E": d, "S": d + cy, "N": d}
+
+
+def stencil_vardiff_2d(k: np.ndarray, h: float) -> dict:
+    """div(k grad u) with face coefficients k_{i+1/2} = (k_i + k_{i+1}) / 2; a face on a
+    Dirichlet wall takes the value of its interior node. Returns per-node arrays."""
+    kx = np.pad(k, ((0, 0), (1, 1)), mode="edge")
+    ky = np.pad(k, ((1, 1), (0, 0)), mode="edge")
+    W = 0.5 * (kx[:, 1:-1] + kx[:, :-2]) / h ** 2
+    E = 0.5 * (kx[:, 1:-1] + kx[:, 2:]) / h ** 2
+    S = 0.5 * (ky[1:-1, :] + ky[:-2, :]) / h ** 2
+    N = 0.5 * (ky[1:-1, :] + ky[2:, :]) / h ** 2
+    return {"C": -(W + E + S + N), "W": W, "E": E, "S": S, "N": N}
+
+
+# --------------------------------------------------------------------------- workloads
+def heat1d(n: int = 1024, tile: int = 64, overlap: int = 16, mu: float = 10.0,
+           nmodes: int = 8, seed: int = 0) -> dict:
+    h = 1.0 / (n + 1)
+    nu = 1.0
+    dt = mu * h ** 2 / nu
+    u0, amps = sine_modes_1d(n, nmodes, seed)
+    return dict(name=f"heat1d_N{n}", shape=(n,), bc=("dirichlet",),
+                coef=stencil_heat_1d(nu, h), dt=dt, tile=(tile,), overlap=(overlap,),
+                u0=u0, amps=amps, mu=mu, reaction=False)
+
+
+def advdiff2d(side: int = 2048, tile: int = 32, overlap: int = 8, nu: float = 5.0,
+              a=(1.0, 0.5), dt: float = 4.0, ell: float = 16.0, seed: int = 1) -> dict:
+    """a = (a_x, a_y); h = 1, so mu = nu dt = 20 and (C_x, C_y) = dt a = (4, 2) by default."""
+    coef = stencil_advdiff_2d(nu, a[0], a[1], 1.0)
+    u0 = grf_2d((side, side), ell, seed).ravel()
+    return dict(name=f"advdiff2d_{side}", shape=(side, side), bc=("periodic", "periodic"),
+                coef=coef, dt=dt, tile=(tile, tile), overlap=(overlap, overlap), u0=u0,
+                reaction=False)
+
+
+def vardiff2d(side: int = 1024, tile: int = 16, overlap: int = 6, ell_k: float = 32.0,
+              sigma: float = 1.0, ell_u: float = 16.0, seed: int = 2) -> dict:
+    """Variable-coefficient diffusion-reaction; dt from median(k) dt / h^2 = 2."""
+    h = 1.0 / (side + 1)
+    g = grf_2d((side, side), ell_k, seed, crop_from=(2 * side, 2 * side))
+    k = np.exp(sigma * g)
+    dt = 2.0 * h ** 2 / float(np.median(k))
+    u0 = 0.5 * grf_2d((side, side), ell_u, seed + 100, crop_from=(2 * side, 2 * side))
+    return dict(name=f"vardiff2d_{side}", shape=(side, side), bc=("dirichlet", "dirichlet"),
+                coef=stencil_vardiff_2d(k, h), dt=dt, tile=(tile, tile),
+                overlap=(overlap, overlap), u0=u0.ravel(), reaction=True)
