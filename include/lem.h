@@ -1,0 +1,155 @@
+/*
+ * lem.h -- C ABI of the GB300 (sm_103a) Local Exponential Method library (liblem.so).
+ *
+ * The Local Exponential Method (L. Bonaventura, "Local Exponential Methods: a domain
+ * decomposition approach to exponential time integration of PDEs", arXiv 1505.02248)
+ * replaces the global exponential step of a semi-discrete linear (or linearised) PDE
+ *     du/dt = A u + g                                  (Sec. 2, Eq. spacedisc)
+ * by independent local problems on overlapping windows M_i = D_i U B_i (Sec. 3):
+ *     v^{n+1}_{M_i} = v^n_{M_i} + dt phi_1(dt A_{M_i}) (A_{M_i} v^n_{M_i} + g_{M_i}(t^n))
+ *                                                      (Sec. 3, Eq. lem)
+ * after which only the owner rows D_i are written back (Sec. 3, step 3).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Meshes are 1D (n[0] = N) or 2D (n[0] = ny rows, n[1] = nx columns); states are
+ *   contiguous row-major [y][x] arrays of double, one value per interior mesh node.
+ * - The operator A is a 3-point (1D) or 5-point (2D) stencil given by its entries in
+ *   the order C (diagonal), W (x-1), E (x+1), S (y-1), N (y+1); NOT multiplied by dt.
+ *   Homogeneous Dirichlet walls drop the outside neighbour (g = 0); periodic axes wrap.
+ * - Tiles D_i are tile[a] nodes per axis (the last tile of an axis may be ragged);
+ *   windows add overlap[a] nodes per side, clipped at Dirichlet walls, wrapped on
+ *   periodic axes (a periodic window that would reach around the axis is the whole axis).
+ * - LEM_MODE_PHI uses the neighbour values frozen at t^n as the artificial-boundary data
+ *   (the literal Eq. lem); LEM_MODE_EXP uses zero data: u_D <- R_D exp(dt A_M) u_M.
+ * - All windows read u^n (Jacobi update); every node is written by its owner tile only.
+ * - Device pointers are CUDA device addresses on the context's device; host pointers are
+ *   ordinary CPU memory. The caller owns every buffer it passes; the library copies what
+ *   it keeps (coefficients) and owns its propagators and workspaces.
+ * - Errors: every call returns a lem_status; nothing is thrown across the ABI.
+ *   lem_last_error() returns a thread-local message for the last failure.
+ *   A context is not re-entrant: calls on one context must not overlap.
+ */
+#ifndef LEM_H
+#define LEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LEM_OK = 0,
+  LEM_EINVAL = 1,     /* invalid argument or descriptor */
+  LEM_ENOMEM = 2,     /* device or host allocation failed (or was refused by a budget) */
+  LEM_ECUDA = 3,      /* a CUDA runtime/driver call failed; see lem_last_error() */
+  LEM_EBUSY = 4,      /* resource in use (server queue full) */
+  LEM_ENOTREADY = 5,  /* propagators not built / result not ready */
+  LEM_ETIMEOUT = 6,   /* a bounded wait expired */
+  LEM_ENUMERIC = 7    /* singular Pade denominator or non-finite values */
+} lem_status;
+
+typedef enum { LEM_BC_DIRICHLET0 = 0, LEM_BC_PERIODIC = 1 } lem_bc;
+typedef enum { LEM_MODE_PHI = 0, LEM_MODE_EXP = 1 } lem_mode;
+/* LEM_PREC_FP64: propagators, residual and apply in IEEE binary64.
+ * LEM_PREC_SPLIT: propagators built in FP64, stored as a scaled FP16 hi + FP16 lo pair and
+ * applied on the tcgen05 tensor cores (three products, FP32 accumulation); the residual
+ * and the state update run in float-float (about 48-bit) arithmetic. */
+typedef enum { LEM_PREC_FP64 = 0, LEM_PREC_SPLIT = 1 } lem_prec;
+
+typedef struct {
+  int ndim;               /* 1 or 2 */
+  int64_t n[2];           /* mesh nodes per axis: {N, unused} or {ny, nx} */
+  int bc[2];              /* lem_bc per axis, same order as n */
+  const double* coef[5];  /* host pointers to C, W, E, S, N (S, N unused in 1D) */
+  int64_t coef_stride;    /* 0: each coef[k] points at one value (constant coefficients);
+                             1: each points at n[0]*n[1] values, row-major */
+  int reaction;           /* 0: linear; 1: adds u - u^3 to A u (exponential Euler-
+                             Rosenbrock, Jacobian A + diag(1 - 3u^2), Sec. 4) */
+  double dt;              /* time step (> 0) */
+  int tile[2];            /* owner-tile size per axis (>= 1) */
+  int overlap[2];         /* buffer width H per side and axis (>= 0) */
+  int mode;               /* lem_mode */
+  int prec;               /* lem_prec */
+  int refresh;            /* reaction only: rebuild the Jacobian propagators every
+                             `refresh` steps (0: build once at the first step) */
+} lem_problem_desc;
+
+typedef struct lem_ctx lem_ctx;
+
+/* Plan facts of a context (filled by lem_get_info). */
+typedef struct {
+  int64_t ntiles;         /* number of owner tiles D_i */
+  int64_t nclasses;       /* distinct local operators (propagators) */
+  int64_t n_loc;          /* padded window size (max |M_i|) */
+  int64_t n_int;          /* padded tile size (max |D_i|) */
+  int squarings_max;      /* largest scaling-and-squaring count s over the classes */
+  int built;              /* 1 once propagators exist */
+  int split_path;         /* 1 if lem_step runs the tcgen05 split-precision kernel */
+  int64_t device_bytes;   /* device memory held by the context */
+} lem_info;
+
+/* Create a context on CUDA device `device`, enqueueing its work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). Validates the descriptor, copies the
+ * coefficients, plans tiles/windows (Sec. 3, Fig. 3) and groups windows with identical
+ * local operators into classes. Allocates device memory. Does not build propagators.
+ * Errors: LEM_EINVAL (descriptor), LEM_ENOMEM, LEM_ECUDA. On error *out is NULL. */
+lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_stream, lem_ctx** out);
+
+/* Build every class's local propagator on the device (Sec. 3 step 2 with Pade
+ * approximation and scaling-and-squaring, Sec. 1 / Sec. 4): P = R_D phi_1(dt A_M)
+ * (PHI) or R_D exp(dt A_M) (EXP), degree-13 Pade, s from the exact 1-norm,
+ * FP64 products and LU with partial pivoting.
+ * d_state (device, FP64, may be NULL for linear problems) is the state at which the
+ * reaction Jacobian is taken. Synchronises the context stream before returning.
+ * Errors: LEM_EINVAL (reaction without state), LEM_ENUMERIC (singular denominator),
+ * LEM_ECUDA. */
+lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state);
+
+/* Advance the device state d_state (FP64, row-major, in/out) by nsteps LEM steps
+ * (Sec. 3 steps 1-3). Builds the propagators first if they do not exist; with the
+ * reaction it rebuilds them every `refresh` steps. Work is enqueued on the context
+ * stream; the call returns after enqueueing (no synchronisation) unless a rebuild is due.
+ * Errors: LEM_EINVAL (nsteps < 0, NULL state), LEM_ECUDA. */
+lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps);
+
+/* Same as lem_step on a HOST state (pinned or pageable): copies it to the device,
+ * advances nsteps, copies it back and synchronises. */
+lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
+
+/* Copy class `cls`'s propagator (n_int x n_loc, row-major, FP64, zero padded) into host
+ * memory h_out. Rows follow the tile's owner nodes in row-major order, columns the window
+ * nodes in row-major order. Errors: LEM_ENOTREADY (not built), LEM_EINVAL. */
+lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out);
+
+/* Class of tile `tile` (row-major over the tile grid) or -1 on a bad index. */
+int64_t lem_tile_class(const lem_ctx* ctx, int64_t tile);
+
+/* Squaring count s used for class `cls` (-1 before the build or on a bad index). */
+int lem_class_squarings(const lem_ctx* ctx, int64_t cls);
+
+lem_status lem_get_info(const lem_ctx* ctx, lem_info* out);
+
+/* Host-only planning query (no device is touched): validates `desc` and reports the
+ * decomposition of Sec. 3 -- number of tiles and classes, padded window and tile sizes.
+ * If tile_info is not NULL it receives 11 int32 per tile (row-major over the tile grid):
+ * window origin (y, x), window extent (y, x), owner offset in the window (y, x),
+ * owner extent (y, x), first owner node (y, x), class. 1D meshes use the x entries
+ * (y entries are 0, 1, 0, 1, 0). Errors: LEM_EINVAL. */
+lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t* nclasses,
+                          int64_t* n_loc, int64_t* n_int, int32_t* tile_info);
+
+/* Synchronise the context stream and return any deferred device error. */
+lem_status lem_sync(lem_ctx* ctx);
+
+void lem_destroy(lem_ctx* ctx);
+
+const char* lem_status_str(lem_status s);
+const char* lem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEM_H */

@@ -1,0 +1,284 @@
+// extern "C" entry points of liblem.so (declared in include/lem.h).
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lem_internal.h"
+
+namespace lem {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+lem_status fail(lem_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+lem_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? LEM_ENOMEM : LEM_ECUDA;
+}
+
+// Host-side fault injection for tests: LEM_FAULT=alloc makes every device allocation of
+// a context fail with LEM_ENOMEM (no GPU fault is involved).
+static bool fault_alloc() {
+  const char* f = std::getenv("LEM_FAULT");
+  return f && std::strcmp(f, "alloc") == 0;
+}
+
+lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (fault_alloc()) return fail(LEM_ENOMEM, "device allocation refused (LEM_FAULT=alloc)");
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(LEM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                cudaGetErrorString(e));
+  }
+  ctx->device_bytes += int64_t(bytes);
+  return LEM_OK;
+}
+
+}  // namespace lem
+
+lem::Stencil lem_ctx::stencil() const {
+  lem::Stencil s{};
+  const int64_t step = desc.coef_stride ? npts : 1;
+  for (int k = 0; k < 5; ++k) s.c[k] = d_coef + k * step;
+  s.stride = desc.coef_stride;
+  return s;
+}
+
+using namespace lem;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void free_ctx(lem_ctx* c) {
+  if (!c) return;
+  split_destroy(c);
+  cudaFree(c->d_coef);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_class_order);
+  cudaFree(c->d_P);
+  cudaFree(c->d_r);
+  cudaFree(c->d_U);
+  cudaFree(c->d_Y);
+  cudaFree(c->d_state_tmp);
+  cudaFree(c->d_status);
+  delete c;
+}
+
+lem_status init_plan(lem_ctx* c, const lem_problem_desc* desc) {
+  LEM_TRY(validate(desc));
+  c->desc = *desc;
+  for (int k = 0; k < 5; ++k) c->desc.coef[k] = nullptr;  // host pointers are not kept
+  if (desc->ndim == 1) {
+    c->ny = 1; c->nx = desc->n[0];
+    c->bcy = LEM_BC_DIRICHLET0; c->bcx = desc->bc[0];
+  } else {
+    c->ny = desc->n[0]; c->nx = desc->n[1];
+    c->bcy = desc->bc[0]; c->bcx = desc->bc[1];
+  }
+  c->npts = c->ny * c->nx;
+  LEM_TRY(make_plan(c));
+  if (c->tiles.size() > 65535) return fail(LEM_EINVAL, "more than 65535 tiles");
+  return LEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lem_status_str(lem_status s) {
+  switch (s) {
+    case LEM_OK: return "LEM_OK";
+    case LEM_EINVAL: return "LEM_EINVAL";
+    case LEM_ENOMEM: return "LEM_ENOMEM";
+    case LEM_ECUDA: return "LEM_ECUDA";
+    case LEM_EBUSY: return "LEM_EBUSY";
+    case LEM_ENOTREADY: return "LEM_ENOTREADY";
+    case LEM_ETIMEOUT: return "LEM_ETIMEOUT";
+    case LEM_ENUMERIC: return "LEM_ENUMERIC";
+  }
+  return "LEM_UNKNOWN";
+}
+
+const char* lem_last_error(void) { return lem::g_last_error.c_str(); }
+
+lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t* nclasses,
+                          int64_t* n_loc, int64_t* n_int, int32_t* tile_info) {
+  lem_ctx tmp;
+  LEM_TRY(init_plan(&tmp, desc));
+  if (ntiles) *ntiles = int64_t(tmp.tiles.size());
+  if (nclasses) *nclasses = int64_t(tmp.classes.size());
+  if (n_loc) *n_loc = tmp.n_loc;
+  if (n_int) *n_int = tmp.n_int;
+  if (tile_info) {
+    for (size_t i = 0; i < tmp.tiles.size(); ++i) {
+      const TileDesc& t = tmp.tiles[i];
+      int32_t* o = tile_info + 11 * i;
+      o[0] = t.org[0]; o[1] = t.org[1]; o[2] = t.wext[0]; o[3] = t.wext[1];
+      o[4] = t.iofs[0]; o[5] = t.iofs[1]; o[6] = t.iext[0]; o[7] = t.iext[1];
+      o[8] = t.t0[0]; o[9] = t.t0[1]; o[10] = t.cls;
+    }
+  }
+  return LEM_OK;
+}
+
+lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_stream, lem_ctx** out) {
+  if (!out) return fail(LEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  lem_ctx* c = new (std::nothrow) lem_ctx();
+  if (!c) return fail(LEM_ENOMEM, "host allocation failed");
+  lem_status s = init_plan(c, desc);
+  if (s != LEM_OK) { delete c; return s; }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    delete c;
+    if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(e, "cudaGetDeviceCount"); }
+    return fail(LEM_EINVAL, "device index out of range");
+  }
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  // dt-scaled coefficients
+  const int64_t per = desc->coef_stride ? c->npts : 1;
+  std::vector<double> hc(5 * per, 0.0);
+  const int ncoef = desc->ndim == 1 ? 3 : 5;
+  for (int k = 0; k < ncoef; ++k)
+    for (int64_t i = 0; i < per; ++i) hc[k * per + i] = desc->dt * desc->coef[k][i];
+  const size_t nt = c->tiles.size(), nc = c->classes.size();
+  s = dev_alloc(c, reinterpret_cast<void**>(&c->d_coef), sizeof(double) * hc.size());
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_tiles), sizeof(TileDesc) * nt);
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_class_order), sizeof(int32_t) * nt);
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_P), sizeof(double) * nc * c->n_int * c->n_loc);
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_r), sizeof(double) * c->npts);
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
+  if (s != LEM_OK) { free_ctx(c); return s; }
+  e = cudaMemcpy(c->d_coef, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * nt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_class_order, c->class_order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "lem_create upload"); }
+  if (desc->prec == LEM_PREC_SPLIT) {
+    if (!split_eligible(c)) {
+      free_ctx(c);
+      return fail(LEM_EINVAL, "LEM_PREC_SPLIT needs one shared propagator (constant coefficients, "
+                              "periodic, tiles dividing the mesh), LEM_MODE_PHI and a 2D mesh");
+    }
+    s = split_prepare(c);
+    if (s != LEM_OK) { free_ctx(c); return s; }
+  }
+  *out = c;
+  return LEM_OK;
+}
+
+lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  LEM_TRY(build_propagators(ctx, d_state));
+  if (ctx->split) {
+    // repack the FP64 propagator for the tensor-core path (split_step does it lazily)
+  }
+  return LEM_OK;
+}
+
+lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  if (!d_state) return fail(LEM_EINVAL, "state is NULL");
+  if (nsteps < 0) return fail(LEM_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return LEM_OK;
+  DeviceGuard g(ctx->device);
+  if (!ctx->built) LEM_TRY(build_propagators(ctx, d_state));
+  if (ctx->split) return split_step(ctx, d_state, nsteps);
+  for (int k = 0; k < nsteps; ++k) {
+    if (ctx->desc.reaction && ctx->desc.refresh > 0 && ctx->steps_since_build >= ctx->desc.refresh)
+      LEM_TRY(build_propagators(ctx, d_state));
+    LEM_TRY(step_fp64(ctx, d_state));
+    ctx->steps_since_build++;
+  }
+  return LEM_OK;
+}
+
+lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  if (!h_state) return fail(LEM_EINVAL, "state is NULL");
+  DeviceGuard g(ctx->device);
+  if (!ctx->d_state_tmp)
+    LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_state_tmp), sizeof(double) * ctx->npts));
+  const size_t bytes = sizeof(double) * ctx->npts;
+  LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_state_tmp, h_state, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  LEM_TRY(lem_step(ctx, ctx->d_state_tmp, nsteps));
+  LEM_CUDA_TRY(cudaMemcpyAsync(h_state, ctx->d_state_tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LEM_OK;
+}
+
+lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out) {
+  if (!ctx || !h_out) return fail(LEM_EINVAL, "NULL argument");
+  if (cls < 0 || cls >= int64_t(ctx->classes.size())) return fail(LEM_EINVAL, "class out of range");
+  if (!ctx->built) return fail(LEM_ENOTREADY, "propagators not built");
+  DeviceGuard g(ctx->device);
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  LEM_CUDA_TRY(cudaMemcpy(h_out, ctx->d_P + cls * ctx->n_int * ctx->n_loc,
+                          sizeof(double) * ctx->n_int * ctx->n_loc, cudaMemcpyDeviceToHost));
+  return LEM_OK;
+}
+
+int64_t lem_tile_class(const lem_ctx* ctx, int64_t tile) {
+  if (!ctx || tile < 0 || tile >= int64_t(ctx->tiles.size())) return -1;
+  return ctx->tiles[tile].cls;
+}
+
+int lem_class_squarings(const lem_ctx* ctx, int64_t cls) {
+  if (!ctx || cls < 0 || cls >= int64_t(ctx->classes.size())) return -1;
+  return ctx->squarings[cls];
+}
+
+lem_status lem_get_info(const lem_ctx* ctx, lem_info* out) {
+  if (!ctx || !out) return fail(LEM_EINVAL, "NULL argument");
+  out->ntiles = int64_t(ctx->tiles.size());
+  out->nclasses = int64_t(ctx->classes.size());
+  out->n_loc = ctx->n_loc;
+  out->n_int = ctx->n_int;
+  int smax = -1;
+  for (int s : ctx->squarings) smax = s > smax ? s : smax;
+  out->squarings_max = smax;
+  out->built = ctx->built ? 1 : 0;
+  out->split_path = ctx->split ? 1 : 0;
+  out->device_bytes = ctx->device_bytes;
+  return LEM_OK;
+}
+
+lem_status lem_sync(lem_ctx* ctx) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return LEM_OK;
+}
+
+void lem_destroy(lem_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal declarations shared by the liblem translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lem.h"
+
+namespace lem {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+lem_status fail(lem_status s, const std::string& msg);
+lem_status cuda_fail(cudaError_t e, const char* what);
+
+#define LEM_CUDA_TRY(call)                                 \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::lem::cuda_fail(e_, #call); \
+  } while (0)
+
+#define LEM_TRY(call)                   \
+  do {                                  \
+    lem_status s_ = (call);             \
+    if (s_ != LEM_OK) return s_;        \
+  } while (0)
+
+// ---------------------------------------------------------------- plan
+// One owner tile D_i and its window M_i (Sec. 3). Window node (a, b) is mesh node
+// ((org[0] + a) mod ny, (org[1] + b) mod nx); 1D problems use axis 1 only (ny = 1).
+struct TileDesc {
+  int32_t org[2];   // window origin (may be negative on a periodic axis)
+  int32_t wext[2];  // window extent per axis
+  int32_t iofs[2];  // owner-tile offset inside the window
+  int32_t iext[2];  // owner-tile extent per axis
+  int32_t t0[2];    // first owner node per axis (mesh coordinates)
+  int32_t cls;      // propagator class
+  int32_t pad;
+};
+
+// One distinct local operator: windows with identical local matrices share it.
+struct ClassDesc {
+  int32_t rep_tile;  // a tile of this class (its window defines the local matrix)
+  int32_t ntiles;
+  int32_t wext[2];
+  int32_t iext[2];
+  int32_t iofs[2];
+  int32_t whole[2];  // window covers a whole periodic axis (wrap couplings inside)
+};
+
+// Device-side stencil: per node (stride 1) or constant (stride 0), dt-scaled.
+struct Stencil {
+  const double* c[5];  // C, W, E, S, N
+  int64_t stride;
+};
+
+struct SplitPlan;  // tcgen05 split-precision state (step_split.cu)
+
+}  // namespace lem
+
+struct lem_ctx {
+  lem_problem_desc desc;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t ny = 1, nx = 1, npts = 0;
+  int bcy = LEM_BC_DIRICHLET0, bcx = LEM_BC_DIRICHLET0;
+  // plan
+  std::vector<lem::TileDesc> tiles;
+  std::vector<lem::ClassDesc> classes;
+  std::vector<int32_t> class_order;    // tiles sorted by class
+  std::vector<int32_t> class_offset;   // start of each class in class_order (nclasses+1)
+  std::vector<int> squarings;          // per class, after the build
+  int64_t n_loc = 0, n_int = 0;        // padded window / tile sizes
+  bool built = false;
+  int steps_since_build = 0;
+  // device buffers (owned)
+  double* d_coef = nullptr;            // 5 * (stride ? npts : 1), dt-scaled
+  lem::TileDesc* d_tiles = nullptr;
+  int32_t* d_class_order = nullptr;
+  double* d_P = nullptr;               // nclasses * n_int * n_loc
+  double* d_r = nullptr;               // npts (residual)
+  double* d_U = nullptr;               // ntiles * n_loc (gathered windows)
+  double* d_Y = nullptr;               // ntiles * n_int (local results)
+  double* d_state_tmp = nullptr;       // npts (host-state path)
+  int* d_status = nullptr;             // device error word
+  int64_t device_bytes = 0;
+  lem::SplitPlan* split = nullptr;
+  lem::Stencil stencil() const;
+};
+
+namespace lem {
+// plan.cpp
+lem_status validate(const lem_problem_desc* d);
+lem_status make_plan(lem_ctx* ctx);
+// builder.cu
+lem_status build_propagators(lem_ctx* ctx, const double* d_state);
+// step_fp64.cu
+lem_status step_fp64(lem_ctx* ctx, double* d_u);
+// step_split.cu
+lem_status split_prepare(lem_ctx* ctx);
+lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
+void split_destroy(lem_ctx* ctx);
+bool split_eligible(const lem_ctx* ctx);
+// allocation helper that tracks bytes
+lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes);
+}  // namespace lem

@@ -1,0 +1,216 @@
+"""Thin ctypes binding of liblem.so (include/lem.h): argument marshalling only.
+
+Every step of the LEM path runs in the library's CUDA kernels; this module only turns
+Python values into the C descriptor and passes device pointers (torch tensors) or host
+buffers (numpy arrays) through. There is no fallback: if liblem.so is missing or fails to
+load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblem.so")
+
+LEM_OK, LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA, LEM_EBUSY, LEM_ENOTREADY, LEM_ETIMEOUT, LEM_ENUMERIC = range(8)
+BC = {"dirichlet": 0, "periodic": 1}
+MODE = {"phi": 0, "exp": 1}
+PREC = {"fp64": 0, "split": 1}
+
+
+class LemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int),
+        ("n", C.c_int64 * 2),
+        ("bc", C.c_int * 2),
+        ("coef", C.POINTER(C.c_double) * 5),
+        ("coef_stride", C.c_int64),
+        ("reaction", C.c_int),
+        ("dt", C.c_double),
+        ("tile", C.c_int * 2),
+        ("overlap", C.c_int * 2),
+        ("mode", C.c_int),
+        ("prec", C.c_int),
+        ("refresh", C.c_int),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("ntiles", C.c_int64), ("nclasses", C.c_int64), ("n_loc", C.c_int64), ("n_int", C.c_int64),
+        ("squarings_max", C.c_int), ("built", C.c_int), ("split_path", C.c_int),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+_lib = None
+
+# (name, restype, argtypes) for every entry point of include/lem.h
+SIGNATURES = [
+    ("lem_create", C.c_int, [C.POINTER(ProblemDesc), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("lem_build_propagators", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("lem_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("lem_step_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("lem_get_propagator", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    ("lem_tile_class", C.c_int64, [C.c_void_p, C.c_int64]),
+    ("lem_class_squarings", C.c_int, [C.c_void_p, C.c_int64]),
+    ("lem_get_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    ("lem_plan_query", C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]),
+    ("lem_sync", C.c_int, [C.c_void_p]),
+    ("lem_destroy", None, [C.c_void_p]),
+    ("lem_status_str", C.c_char_p, [C.c_int]),
+    ("lem_last_error", C.c_char_p, []),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load liblem.so (raises if it is missing: there is no non-CUDA implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblem.so not built at {path}: run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, what: str = "") -> None:
+    if status != LEM_OK:
+        lib = load()
+        raise LemError(status, f"{what}: {lib.lem_status_str(status).decode()}: {lib.lem_last_error().decode()}")
+
+
+def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec="fp64",
+              reaction=False, refresh=0):
+    """Build a ProblemDesc; returns (desc, keepalive) -- keep the second alive while used."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    d = ProblemDesc()
+    d.ndim = nd
+    for a in range(2):
+        d.n[a] = shape[a] if a < nd else 0
+        d.bc[a] = BC[bc[a]] if a < nd else 0
+        d.tile[a] = int(tile[a]) if a < nd else 0
+        d.overlap[a] = int(overlap[a]) if a < nd else 0
+    keep = []
+    names = ["C", "W", "E", "S", "N"][: 3 if nd == 1 else 5]
+    arrays = [np.ascontiguousarray(np.asarray(coef[k], dtype=np.float64).ravel()) for k in names]
+    stride = 0 if all(a.size == 1 for a in arrays) else 1
+    npts = int(np.prod(shape))
+    for k, a in enumerate(arrays):
+        if stride == 1 and a.size == 1:
+            a = np.full(npts, float(a[0]))
+        keep.append(a)
+        d.coef[k] = a.ctypes.data_as(C.POINTER(C.c_double))
+    d.coef_stride = stride
+    d.reaction = 1 if reaction else 0
+    d.dt = float(dt)
+    d.mode = MODE[mode]
+    d.prec = PREC[prec]
+    d.refresh = int(refresh)
+    return d, keep
+
+
+def plan_query(shape, bc, coef, dt, tile, overlap, **kw):
+    """Host-only decomposition (no device): dict with ntiles, nclasses, n_loc, n_int, tiles."""
+    lib = load()
+    d, keep = make_desc(shape, bc, coef, dt, tile, overlap, **kw)
+    nt, nc, nl, ni = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    check(lib.lem_plan_query(C.byref(d), C.byref(nt), C.byref(nc), C.byref(nl), C.byref(ni), None), "plan")
+    info = np.zeros((nt.value, 11), dtype=np.int32)
+    check(lib.lem_plan_query(C.byref(d), None, None, None, None, info.ctypes.data_as(C.c_void_p)), "plan")
+    return dict(ntiles=nt.value, nclasses=nc.value, n_loc=nl.value, n_int=ni.value, tiles=info)
+
+
+class Lem:
+    """One LEM context (lem_create ... lem_destroy) on a CUDA device."""
+
+    def __init__(self, shape, bc, coef, dt, tile, overlap, mode="phi", prec="fp64",
+                 reaction=False, refresh=0, device=0, stream=None):
+        lib = load()
+        self._lib = lib
+        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, prec, reaction, refresh)
+        self.shape = tuple(int(s) for s in shape)
+        self.npts = int(np.prod(self.shape))
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream is not None else None
+        check(lib.lem_create(C.byref(d), int(device), st, C.byref(h)), "lem_create")
+        del keep
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, wl: dict, **kw):
+        args = dict(mode="phi", prec="fp64", reaction=wl.get("reaction", False),
+                    refresh=wl.get("refresh", 0))
+        args.update(kw)
+        return cls(wl["shape"], wl["bc"], wl["coef"], wl["dt"], wl["tile"], wl["overlap"], **args)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls -------------------------------------------------------------------------
+    def build(self, state=None):
+        ptr = None if state is None else C.c_void_p(state.data_ptr())
+        check(self._lib.lem_build_propagators(self._h, ptr), "lem_build_propagators")
+
+    def step(self, state, nsteps: int):
+        """Advance a CUDA float64 tensor (contiguous, npts values) in place."""
+        assert state.is_cuda and state.dtype.itemsize == 8 and state.is_contiguous()
+        assert state.numel() == self.npts
+        check(self._lib.lem_step(self._h, C.c_void_p(state.data_ptr()), int(nsteps)), "lem_step")
+
+    def step_host(self, state: np.ndarray, nsteps: int):
+        """Advance a host float64 array in place (copies in and out inside the call)."""
+        assert state.dtype == np.float64 and state.flags.c_contiguous and state.size == self.npts
+        check(self._lib.lem_step_host(self._h, state.ctypes.data_as(C.c_void_p), int(nsteps)),
+              "lem_step_host")
+
+    def propagator(self, cls: int) -> np.ndarray:
+        inf = self.info()
+        out = np.zeros((inf["n_int"], inf["n_loc"]))
+        check(self._lib.lem_get_propagator(self._h, int(cls), out.ctypes.data_as(C.c_void_p)),
+              "lem_get_propagator")
+        return out
+
+    def tile_class(self, t: int) -> int:
+        return int(self._lib.lem_tile_class(self._h, int(t)))
+
+    def squarings(self, cls: int) -> int:
+        return int(self._lib.lem_class_squarings(self._h, int(cls)))
+
+    def info(self) -> dict:
+        i = Info()
+        check(self._lib.lem_get_info(self._h, C.byref(i)), "lem_get_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def sync(self):
+        check(self._lib.lem_sync(self._h), "lem_sync")

@@ -1,0 +1,160 @@
+"""GPU parity of the FP64 LEM path against the FP64 oracle (through the C-ABI).
+
+Bar: propagators within 1e-12 of the oracle's (max abs error / max |P|), identical
+squaring counts, and states within 1e-12 relative L2 after the stated number of steps.
+Cases span several tiles, ragged tails, clipped and wrapped windows, both modes, variable
+coefficients, the reaction with Jacobian refresh, and the full 2048^2 workload (sampled)."""
+import numpy as np
+import pytest
+
+from oracle import (assemble_operator, decompose, lem_run, lem_step, local_propagators, rel_l2,
+                    squaring_count)
+from paper_1505_02248_gb300 import lem as L
+from paper_1505_02248_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+# EXP mode applies P to the whole state every step (PHI only to the increment), so an FP64
+# rounding difference of about n_loc * eps ~ 1e-14 in P compounds to ~steps * 1e-14.
+TOL_EXP_PER_STEP = 5e-14
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_02248_gb300 import build as B
+    B.build()
+    L.load()
+
+
+def _oracle(wl, mode="phi", tiles=None):
+    X = assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    wins = decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
+    return X, wins
+
+
+def _check_propagators(ctx, wl, mode, X, wins, u=None):
+    from oracle import jacobian
+    Xj = jacobian(X, u, wl["dt"], True) if wl.get("reaction") else X
+    ncls = ctx.info()["nclasses"]
+    seen = set()
+    for t in range(len(wins)):
+        c = ctx.tile_class(t)
+        if c in seen:
+            continue
+        seen.add(c)
+        P_ref = local_propagators(Xj, wins, mode, tiles=[t])[t]
+        P = ctx.propagator(c)
+        ni, nl = P_ref.shape
+        scale = np.abs(P_ref).max()
+        assert np.abs(P[:ni, :nl] - P_ref).max() <= TOL * scale, f"class {c}"
+        assert not P[:ni, nl:].any() and not P[ni:, :].any()  # zero padding
+        XM = Xj[wins[t].M][:, wins[t].M].toarray()
+        nrm = np.abs(XM).sum(axis=0).max()
+        assert ctx.squarings(c) == squaring_count(max(nrm, 1.0) if mode == "phi" else nrm)
+        if len(seen) >= 6:
+            break
+    assert len(seen) >= min(ncls, 6)
+
+
+def _run_case(wl, mode, steps):
+    X, wins = _oracle(wl, mode)
+    ctx = L.Lem.from_workload(wl, mode=mode)
+    u = torch.tensor(wl["u0"], dtype=torch.float64, device="cuda")
+    ctx.build(u)
+    _check_propagators(ctx, wl, mode, X, wins, wl["u0"])
+    ctx.step(u, steps)
+    ctx.sync()
+    ref = lem_run(X, wl["u0"], wins, steps, mode, wl["dt"], wl.get("reaction", False),
+                  wl.get("refresh", 0))
+    err = rel_l2(u.cpu().numpy(), ref)
+    ctx.close()
+    return err
+
+
+@pytest.mark.parametrize("mode", ["phi", "exp"])
+def test_heat1d_100_steps(mode):
+    wl = W.heat1d()
+    assert _run_case(wl, mode, 100) <= (TOL if mode == "phi" else 100 * TOL_EXP_PER_STEP)
+
+
+@pytest.mark.parametrize("mode", ["phi", "exp"])
+def test_advdiff2d_periodic_small(mode):
+    wl = W.advdiff2d(side=128, tile=16, overlap=4, ell=8.0)
+    assert _run_case(wl, mode, 10) <= (TOL if mode == "phi" else 10 * TOL_EXP_PER_STEP)
+
+
+def test_ragged_dirichlet_variable_coefficients():
+    rng = np.random.default_rng(5)
+    k = np.exp(rng.standard_normal((37, 45)))
+    wl = dict(shape=(37, 45), bc=("dirichlet", "periodic"), coef=W.stencil_vardiff_2d(k, 1.0),
+              dt=0.6, tile=(16, 16), overlap=(4, 6), u0=rng.standard_normal(37 * 45))
+    assert _run_case(wl, "phi", 3) <= TOL
+
+
+def test_ragged_1d_periodic_whole_axis_and_zero_overlap():
+    rng = np.random.default_rng(6)
+    for n, tile, H in ((100, 32, 5), (50, 16, 30), (64, 16, 0)):
+        wl = dict(shape=(n,), bc=("periodic",), coef=W.stencil_advdiff_1d(1.0, 2.0, 1.0), dt=1.5,
+                  tile=(tile,), overlap=(H,), u0=rng.standard_normal(n))
+        assert _run_case(wl, "phi", 4) <= TOL
+
+
+def test_single_tile_covers_mesh():
+    wl = W.heat1d(n=200, tile=256, overlap=3)
+    assert _run_case(wl, "phi", 5) <= TOL
+
+
+def test_reaction_with_jacobian_refresh():
+    wl = W.vardiff2d(side=48, tile=16, overlap=6)
+    wl["refresh"] = 2
+    assert _run_case(wl, "phi", 5) <= TOL
+
+
+def test_host_state_path_matches_device_path():
+    wl = W.advdiff2d(side=64, tile=16, overlap=4, ell=4.0)
+    a = L.Lem.from_workload(wl)
+    b = L.Lem.from_workload(wl)
+    u = torch.tensor(wl["u0"], device="cuda")
+    a.step(u, 3)
+    a.sync()
+    h = wl["u0"].copy()
+    b.step_host(h, 3)
+    assert np.array_equal(u.cpu().numpy(), h)
+
+
+def test_zero_steps_is_identity_and_negative_rejected():
+    wl = W.heat1d(n=128, tile=32, overlap=4)
+    ctx = L.Lem.from_workload(wl)
+    u = torch.tensor(wl["u0"], device="cuda")
+    ctx.step(u, 0)
+    assert np.array_equal(u.cpu().numpy(), wl["u0"])
+    with pytest.raises(L.LemError) as e:
+        ctx.step(u, -1)
+    assert e.value.status == L.LEM_EINVAL
+
+
+def test_full_size_advdiff2d_fp64_sampled():
+    """2048^2, tiles 32^2 + H 8: the shared 1024 x 2304 propagator in full, and one step on
+    sampled tiles (interior, corners, wrapped edges)."""
+    wl = W.advdiff2d()
+    X, wins = _oracle(wl)
+    ctx = L.Lem.from_workload(wl)
+    u = torch.tensor(wl["u0"], device="cuda")
+    ctx.build()
+    assert ctx.info()["nclasses"] == 1 and ctx.squarings(0) == 6
+    P_ref = local_propagators(X, wins, "phi", tiles=[0])[0]
+    P = ctx.propagator(0)
+    assert np.abs(P - P_ref).max() <= TOL * np.abs(P_ref).max()
+    ctx.step(u, 1)
+    ctx.sync()
+    got = u.cpu().numpy()
+    sample = [0, 63, 64 * 63, 4095, 2080, 1000, 3333]
+    props = [P_ref if i in sample else None for i in range(len(wins))]
+    ref = lem_step(X, wl["u0"], wins, props, "phi", tiles=sample)
+    for t in sample:
+        D = wins[t].D
+        assert rel_l2(got[D], ref[D]) <= TOL
