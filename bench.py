@@ -1,0 +1,331 @@
+"""Benchmark of the LEM hot path on GB300: 2D periodic advection-diffusion, 2048^2 nodes,
+32^2 owner tiles + 8-node buffers (48^2 = 2304-node windows), one shared 1024 x 2304 phi_1
+propagator applied to all 4096 tiles every step (Sec. 3, Eq. lem).
+
+One bench step = one lem_step call advancing the state by --inner LEM time steps (the
+residual, the halo gather inside TMA, the propagator apply and the owner scatter for all
+4096 tiles, every LEM step). Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64] [--impl reference]
+
+Metric: LEM dof-steps/s = owner nodes x LEM steps / device time. L2 is flushed (256 MiB
+write) between timed calls; each call is bracketed by CUDA events on the context stream.
+Multi-GPU (torchrun): every rank advances its own independent problem (weak scaling, no
+collective on the data path); rank 0 reports the aggregate over ranks with the max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LEM dof-steps/s"
+WORKLOAD = "advdiff2d_2048x2048_periodic_tile32_H8_phi"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--inner", type=int, default=10, help="LEM time steps per bench step")
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("step_split.cu", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_1505_02248_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_hash):
+    """DRAM bytes per launch of the split GEMM from the committed ncu summary, if it was
+    captured from the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "split_gemm_advdiff2d_2048.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(side, max_seconds=20.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the shared
+    propagator build once, then LEM steps restricted to a subset of tiles."""
+    import oracle as O
+    from paper_1505_02248_gb300 import workloads as W
+    wl = W.advdiff2d(side=side)
+    X = O.assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    wins = O.decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
+    t0 = time.perf_counter()
+    P = O.local_propagators(X, wins, "phi", tiles=[0])[0]
+    t_build = time.perf_counter() - t0
+    ntile = 64
+    sample = list(range(0, len(wins), max(1, len(wins) // ntile)))[:ntile]
+    props = [P if i in set(sample) else None for i in range(len(wins))]
+    u = wl["u0"].copy()
+    steps, t_step = 0, 0.0
+    while t_step < max_seconds / 2 and steps < 50:
+        t0 = time.perf_counter()
+        u = O.lem_step(X, u, wins, props, "phi", tiles=sample)
+        t_step += time.perf_counter() - t0
+        steps += 1
+    dofs = sum(len(wins[i].D) for i in sample) * steps
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": dofs / t_step, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} of {len(wins)} tiles x {steps} LEM steps (numpy FP64 oracle); "
+                      f"the one-time propagator build took {t_build:.1f} s and is excluded"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = []
+    cb = None
+    for _ in range(a.warmup + a.steps):
+        cb = oracle_sample(a.side, max_seconds=4.0)
+        per.append(cb["value"])
+    v = statistics.median(per[a.warmup:]) if len(per) > a.warmup else per[-1]
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle on a tile sample"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_1505_02248_gb300 import lem as L
+    from paper_1505_02248_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    L.load()
+
+    wl = W.advdiff2d(side=a.side, seed=1 + rank)
+    npts = wl["u0"].size
+    stream = torch.cuda.current_stream(dev)
+    ctx = L.Lem.from_workload(wl, prec=a.prec, device=local, stream=stream.cuda_stream)
+    u = torch.tensor(wl["u0"], device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    t0 = time.perf_counter()
+    ctx.build()
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+
+    for _ in range(a.warmup):
+        ctx.step(u, a.inner)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.get_timing()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        for k in range(a.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            ctx.step(u, a.inner)
+            stops[k].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    gemm_ms, gemm_launches = ctx.get_timing()
+    ctx.set_timing(False)
+    if world > 1:
+        dist.barrier()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
+    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    total_lem_steps = a.warmup * a.inner + a.steps * a.inner
+
+    # end to end through the public host API: pinned host state, H2D + steps + D2H per call
+    h = torch.tensor(wl["u0"]).pin_memory()
+    hn = h.numpy()
+    ctx.step_host(hn, 1)
+    e2e_ms = []
+    for k in range(max(3, min(a.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.step_host(hn, a.inner)
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_ms_med = statistics.median(e2e_ms)
+
+    # numerical check of the timed run against the plain FP64 GPU LEM (same start, same steps)
+    err = None
+    fp64_rate = None
+    if a.prec == "split" and not a.no_fp64_compare and total_lem_steps <= 400:
+        ref = L.Lem.from_workload(wl, prec="fp64", device=local, stream=stream.cuda_stream)
+        v = torch.tensor(wl["u0"], device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ref.build()
+        e0.record(stream)
+        ref.step(v, total_lem_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_rate = npts * total_lem_steps / (e0.elapsed_time(e1) * 1e-3)
+        err = float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v))
+        ref.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    tflops_peak, hbm_peak, peak_src = peaks()
+    khash = kernel_source_hash()
+    value = npts * a.inner * a.steps * world / (dev_ms_max * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": METRIC,
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": dev_ms_max / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f16-split/f32-acc" if a.prec == "split" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": npts, "tiles": 4096 if a.side == 2048 else None,
+                   "propagator": "1024x2304 phi_1 (shared)", "lem_steps_per_step": a.inner,
+                   "prec": a.prec, "l2": "256 MiB write between timed steps",
+                   "parallelism": f"replicas x{world}", "build_ms": round(build_ms, 1)},
+        "gpu_launches": a.steps * (2 + 2 * a.inner) if a.prec == "split" else a.steps * a.inner * 4,
+    }
+    if gemm_launches:
+        avg_ms = gemm_ms / gemm_launches
+        if a.prec == "split":
+            flops = 4 * 2.0 * 1024 * 2304 * 4096 * (a.side / 2048) ** 2  # 4 split products
+            line["roofline"] = {"kernel": "split_gemm_kernel (tcgen05 kind::f16)", "bound": "tensor",
+                                "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": tflops_peak,
+                                "unit": "TFLOP/s", "frac": flops / (avg_ms * 1e-3) / 1e12 / tflops_peak,
+                                "traffic": ncu_traffic(khash), "avg_launch_us": avg_ms * 1e3,
+                                "launches": gemm_launches, "peak_source": f"{peak_src} bf16 dense (fp16 same rate)",
+                                "kernel_hash": khash}
+        else:
+            flops = 2.0 * 1024 * 2304 * 4096 * (a.side / 2048) ** 2
+            line["roofline"] = {"kernel": "dgemm_kernel (FP64 apply)", "bound": "alu",
+                                "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": 1.196, "unit": "TFLOP/s",
+                                "frac": flops / (avg_ms * 1e-3) / 1e12 / 1.196, "traffic": None,
+                                "avg_launch_us": avg_ms * 1e3, "launches": gemm_launches,
+                                "peak_source": "FP64 FMA chain probe on this pool's GB300 (1.196 TFLOP/s)"}
+    line["e2e"] = {"value": npts * a.inner / (e2e_ms_med * 1e-3), "unit": METRIC,
+                   "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts,
+                   "ms_per_step": e2e_ms_med}
+    line["clocks"] = clk.summary()
+    if err is not None:
+        line["rel_l2_vs_fp64_gpu"] = err
+        line["fp64_gpu_lem"] = {"value": fp64_rate, "unit": METRIC, "lem_steps": total_lem_steps}
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(a.side)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,15 @@ lem_status lem_get_info(const lem_ctx* ctx, lem_info* out);
 lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t* nclasses,
                           int64_t* n_loc, int64_t* n_int, int32_t* tile_info);
 
+/* Per-kernel timing of the dominant propagator-apply kernel (for benchmarks).
+ * lem_set_timing(ctx, 1) makes later lem_step calls bracket every launch of the apply
+ * kernel (the tcgen05 split GEMM, or the FP64 apply GEMMs) with CUDA events recorded on the
+ * context stream; lem_get_timing synchronises, adds the elapsed times of all recorded
+ * launches since the last call to *total_ms and their count to *launches, and resets them.
+ * Errors: LEM_EINVAL, LEM_ECUDA. */
+lem_status lem_set_timing(lem_ctx* ctx, int enable);
+lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
+
 /* Synchronise the context stream and return any deferred device error. */
 lem_status lem_sync(lem_ctx* ctx);
 

@@ -54,6 +54,28 @@ lem::Stencil lem_ctx::stencil() const {
   return s;
 }
 
+// Record a start event for one apply-kernel launch; returns its stop event through *stop.
+cudaError_t lem_ctx::timing_begin(cudaEvent_t* stop) {
+  *stop = nullptr;
+  if (!timing) return cudaSuccess;
+  if (ev_used + 2 > ev_pool.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t start = ev_pool[ev_used];
+  *stop = ev_pool[ev_used + 1];
+  ev_used += 2;
+  return cudaEventRecord(start, stream);
+}
+
+void lem_ctx::timing_end(cudaEvent_t stop) {
+  if (stop) cudaEventRecord(stop, stream);
+}
+
 using namespace lem;
 
 namespace {
@@ -72,6 +94,7 @@ struct DeviceGuard {
 void free_ctx(lem_ctx* c) {
   if (!c) return;
   split_destroy(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   cudaFree(c->d_coef);
   cudaFree(c->d_tiles);
   cudaFree(c->d_class_order);
@@ -180,8 +203,10 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   if (desc->prec == LEM_PREC_SPLIT) {
     if (!split_eligible(c)) {
       free_ctx(c);
-      return fail(LEM_EINVAL, "LEM_PREC_SPLIT needs one shared propagator (constant coefficients, "
-                              "periodic, tiles dividing the mesh), LEM_MODE_PHI and a 2D mesh");
+      return fail(LEM_EINVAL, "LEM_PREC_SPLIT needs a 2D periodic mesh with constant coefficients, "
+                              "LEM_MODE_PHI, tiles dividing the mesh, tile_y*tile_x a multiple of 128, "
+                              "tile_x a multiple of 8, window width tile_x + 2*overlap_x a multiple "
+                              "of 16 and at most 64, and a tile grid that groups into 128 windows");
     }
     s = split_prepare(c);
     if (s != LEM_OK) { free_ctx(c); return s; }
@@ -194,10 +219,7 @@ lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   DeviceGuard g(ctx->device);
   LEM_TRY(build_propagators(ctx, d_state));
-  if (ctx->split) {
-    // repack the FP64 propagator for the tensor-core path (split_step does it lazily)
-  }
-  return LEM_OK;
+  return LEM_OK;  // the split path repacks the new propagator lazily (build_gen)
 }
 
 lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
@@ -228,7 +250,7 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
   LEM_TRY(lem_step(ctx, ctx->d_state_tmp, nsteps));
   LEM_CUDA_TRY(cudaMemcpyAsync(h_state, ctx->d_state_tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  return LEM_OK;
+  return split_check_error(ctx);
 }
 
 lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out) {
@@ -267,11 +289,33 @@ lem_status lem_get_info(const lem_ctx* ctx, lem_info* out) {
   return LEM_OK;
 }
 
+lem_status lem_set_timing(lem_ctx* ctx, int enable) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  ctx->timing = enable != 0;
+  return LEM_OK;
+}
+
+lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx || !total_ms || !launches) return fail(LEM_EINVAL, "NULL argument");
+  DeviceGuard g(ctx->device);
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float ms = 0.0f;
+    LEM_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = int64_t(ctx->ev_used / 2);
+  ctx->ev_used = 0;
+  return LEM_OK;
+}
+
 lem_status lem_sync(lem_ctx* ctx) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   DeviceGuard g(ctx->device);
   LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  return LEM_OK;
+  return split_check_error(ctx);
 }
 
 void lem_destroy(lem_ctx* ctx) {

@@ -400,6 +400,7 @@ lem_status build_propagators(lem_ctx* ctx, const double* d_state) {
     LEM_TRY(build_batch(ctx, int(c0), nb, d_state));
   }
   ctx->built = true;
+  ctx->build_gen++;
   ctx->steps_since_build = 0;
   return LEM_OK;
 }

@@ -75,6 +75,7 @@ struct lem_ctx {
   std::vector<int> squarings;          // per class, after the build
   int64_t n_loc = 0, n_int = 0;        // padded window / tile sizes
   bool built = false;
+  int build_gen = 0;                   // incremented by every propagator build
   int steps_since_build = 0;
   // device buffers (owned)
   double* d_coef = nullptr;            // 5 * (stride ? npts : 1), dt-scaled
@@ -88,6 +89,12 @@ struct lem_ctx {
   int* d_status = nullptr;             // device error word
   int64_t device_bytes = 0;
   lem::SplitPlan* split = nullptr;
+  // optional event timing of the apply kernel
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop)
+  size_t ev_used = 0;
+  cudaError_t timing_begin(cudaEvent_t* stop);
+  void timing_end(cudaEvent_t stop);
   lem::Stencil stencil() const;
 };
 
@@ -103,6 +110,7 @@ lem_status step_fp64(lem_ctx* ctx, double* d_u);
 lem_status split_prepare(lem_ctx* ctx);
 lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
 void split_destroy(lem_ctx* ctx);
+lem_status split_check_error(lem_ctx* ctx);
 bool split_eligible(const lem_ctx* ctx);
 // allocation helper that tracks bytes
 lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes);

@@ -106,6 +106,8 @@ lem_status step_fp64(lem_ctx* ctx, double* d_u) {
     LEM_CUDA_TRY(cudaGetLastError());
   }
   // Y[tiles of class c] = U[tiles of class c] * P_c^T   (one gathered GEMM per class)
+  cudaEvent_t stop;
+  LEM_CUDA_TRY(ctx->timing_begin(&stop));
   const int64_t nc = int64_t(ctx->classes.size());
   for (int64_t c = 0; c < nc; ++c) {
     const int off = ctx->class_offset[c], cnt = ctx->class_offset[c + 1] - off;
@@ -119,6 +121,7 @@ lem_status step_fp64(lem_ctx* ctx, double* d_u) {
     g.rowidx = ctx->d_class_order + off;
     LEM_CUDA_TRY(dgemm(g, 1, st));
   }
+  ctx->timing_end(stop);
   {
     int bx = int(std::min<int64_t>((ctx->n_int + 255) / 256, 64));
     scatter_fp64_kernel<<<dim3(bx, unsigned(nt)), 256, 0, st>>>(d_u, ctx->d_Y, ctx->d_tiles,

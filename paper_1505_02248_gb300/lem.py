@@ -66,6 +66,8 @@ SIGNATURES = [
     ("lem_get_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
     ("lem_plan_query", C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]),
+    ("lem_set_timing", C.c_int, [C.c_void_p, C.c_int]),
+    ("lem_get_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     ("lem_sync", C.c_int, [C.c_void_p]),
     ("lem_destroy", None, [C.c_void_p]),
     ("lem_status_str", C.c_char_p, [C.c_int]),
@@ -211,6 +213,15 @@ class Lem:
         i = Info()
         check(self._lib.lem_get_info(self._h, C.byref(i)), "lem_get_info")
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def set_timing(self, on: bool):
+        check(self._lib.lem_set_timing(self._h, 1 if on else 0), "lem_set_timing")
+
+    def get_timing(self):
+        """(total_ms, launches) of the apply kernel since the last call."""
+        t, n = C.c_double(), C.c_int64()
+        check(self._lib.lem_get_timing(self._h, C.byref(t), C.byref(n)), "lem_get_timing")
+        return t.value, n.value
 
     def sync(self):
         check(self._lib.lem_sync(self._h), "lem_sync")
