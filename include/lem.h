@@ -150,6 +150,26 @@ lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t
 lem_status lem_set_timing(lem_ctx* ctx, int enable);
 lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
 
+/* Allocation-free FP64 step (the paper has no counterpart; this is a service to callers).
+ * Same result as lem_step on an LEM_PREC_FP64 context, for callers that must not allocate
+ * device memory while they step: code running under CUDA stream capture, runtimes that
+ * own all device memory through their own pool, and loops that cannot take cudaMalloc's
+ * implicit synchronisation. Its per-step scratch (residual, gathered windows and local
+ * results) comes from one static 8 MiB device array that every GPU loading liblem.so holds
+ * until the process exits; no call allocates or frees memory.
+ * - Needs built propagators (lem_build_propagators first: LEM_ENOTREADY otherwise) and
+ *   no Jacobian refresh (reaction with refresh > 0: LEM_EINVAL), since building allocates.
+ * - Problems whose scratch, npts + ntiles*(n_loc + n_int) doubles (each part rounded up to
+ *   32), exceeds 8 MiB are rejected with LEM_EINVAL and a message giving both sizes.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   which may load the library's device code on that device); make that first call before
+ *   any stream capture.
+ * - Every call on a device shares the one array, which keeps the last call's contents
+ *   (each step rewrites every element it reads, so nothing needs clearing). Calls whose
+ *   work overlaps on the GPU (other streams, other contexts, other threads) race on it.
+ * Errors: LEM_EINVAL, LEM_ENOTREADY, LEM_ECUDA. */
+lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int nsteps);
+
 /* Synchronise the context stream and return any deferred device error. */
 lem_status lem_sync(lem_ctx* ctx);
 

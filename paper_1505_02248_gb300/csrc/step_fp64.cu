@@ -132,3 +132,41 @@ lem_status step_fp64(lem_ctx* ctx, double* d_u) {
 }
 
 }  // namespace lem
+
+namespace lem {
+
+// One FP64 LEM step with caller-provided scratch: r (npts), U (ntiles x n_loc) and
+// Y (ntiles x n_int). Used by the allocation-free entry point; it launches the same
+// kernels as step_fp64 and writes every scratch element it later reads.
+lem_status step_fp64_scratch(lem_ctx* ctx, double* d_u, double* r, double* U, double* Y) {
+  cudaStream_t st = ctx->stream;
+  const int64_t nt = int64_t(ctx->tiles.size());
+  const bool phi = ctx->desc.mode == LEM_MODE_PHI;
+  const double* src = d_u;
+  if (phi) {
+    LEM_CUDA_TRY(launch_residual_fp64(ctx, r, d_u));
+    src = r;
+  }
+  int bx = int(std::min<int64_t>((ctx->n_loc + 255) / 256, 64));
+  gather_fp64_kernel<<<dim3(bx, unsigned(nt)), 256, 0, st>>>(U, src, ctx->d_tiles, ctx->n_loc, ctx->ny, ctx->nx);
+  LEM_CUDA_TRY(cudaGetLastError());
+  const int64_t nc = int64_t(ctx->classes.size());
+  for (int64_t c = 0; c < nc; ++c) {
+    const int off = ctx->class_offset[c], cnt = ctx->class_offset[c + 1] - off;
+    if (cnt == 0) continue;
+    DgemmArgs g{};
+    g.M = cnt; g.N = int(ctx->n_int); g.K = int(ctx->n_loc);
+    g.A = U; g.lda = ctx->n_loc; g.sA = 0;
+    g.B = ctx->d_P + c * ctx->n_int * ctx->n_loc; g.ldb = ctx->n_loc; g.sB = 0; g.transB = 1;
+    g.C = Y; g.ldc = ctx->n_int; g.sC = 0;
+    g.alpha = 1.0; g.beta = 0.0;
+    g.rowidx = ctx->d_class_order + off;
+    LEM_CUDA_TRY(dgemm(g, 1, st));
+  }
+  bx = int(std::min<int64_t>((ctx->n_int + 255) / 256, 64));
+  scatter_fp64_kernel<<<dim3(bx, unsigned(nt)), 256, 0, st>>>(d_u, Y, ctx->d_tiles, ctx->n_int, ctx->nx, phi ? 1 : 0);
+  LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
+}  // namespace lem

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("lem_get_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
     ("lem_plan_query", C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]),
+    ("lem_step_fp64_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lem_set_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("lem_get_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     ("lem_sync", C.c_int, [C.c_void_p]),
@@ -189,6 +190,13 @@ class Lem:
         assert state.is_cuda and state.dtype.itemsize == 8 and state.is_contiguous()
         assert state.numel() == self.npts
         check(self._lib.lem_step(self._h, C.c_void_p(state.data_ptr()), int(nsteps)), "lem_step")
+
+    def step_noalloc(self, state, nsteps: int):
+        """lem_step_fp64_noalloc: the FP64 step with static scratch (no device allocation)."""
+        assert state.is_cuda and state.dtype.itemsize == 8 and state.is_contiguous()
+        assert state.numel() == self.npts
+        check(self._lib.lem_step_fp64_noalloc(self._h, C.c_void_p(state.data_ptr()), int(nsteps)),
+              "lem_step_fp64_noalloc")
 
     def step_host(self, state: np.ndarray, nsteps: int):
         """Advance a host float64 array in place (copies in and out inside the call)."""
