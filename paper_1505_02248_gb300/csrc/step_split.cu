@@ -4,17 +4,17 @@
 //
 //  1. residual_split_kernel: r = dt A u^n from the float-float state (float-float
 //     arithmetic: the stencil differences of a smooth field cancel), scaled by one global
-//     power of two 2^er and written as three FP16 slices r*2^er = r_int + r2 + r3 into a
+//     power of two 2^er and written as two FP16 slices r*2^er = r_int + r2 into a
 //     ghost-padded [ny + 2Hy][pitch] array (the periodic halo is materialised here, so
 //     every window is a plain rectangle of it). r_int is an integer (|r_int| <= 2^rb),
-//     r2 and r3 carry the remainder to ~33 bits. er comes from the previous step's max|r|.
+//     r2 the FP16-rounded remainder. er comes from the previous step's max|r|.
 //  2. split_gemm_kernel: Y = P R (M = Ty*Tx owner rows, N = tiles, K = window nodes).
 //     P is stored per row i as P*2^eP_i = P_int + P2 with |P_int| <= 2^9 an integer.
 //     Each K block is one window row (Wx nodes, padded to 64 in the P layout): TMA loads
-//     P_int/P2 and the 128 windows' rows of r_int/r2/r3 straight from the padded residual
+//     P_int/P2 and the 128 windows' rows of r_int/r2 straight from the padded residual
 //     through a 4D tensor map (the halo gather happens inside TMA). One thread issues
-//     tcgen05.mma: P_int r_int into the main TMEM accumulator and P_int r2, P2 r_int,
-//     P2 r2, P_int r3 into a correction accumulator. Because sum_k |P_int| |r_int| < 2^24
+//     tcgen05.mma: P_int r_int into the main TMEM accumulator and P_int r2, P2 r_int and
+//     P2 r2 into a correction accumulator. Because sum_k |P_int| |r_int| < 2^24
 //     (checked when P is packed), every partial sum of the main product is an integer that
 //     FP32 holds exactly, whatever rounding the tensor pipe's accumulator applies; only the
 //     small correction products see that rounding. The epilogue forms
@@ -42,9 +42,9 @@ namespace {
 constexpr int BM = 128;            // owner rows per CTA tile (TMEM lanes)
 constexpr int BN = 128;            // windows per CTA tile (TMEM columns per accumulator)
 constexpr int KB = 64;             // fp16 elements per 128-byte K row
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * KB * 2;  // 16 KB (A and B tiles have 128 rows each)
-constexpr int NTILES_STAGE = 5;          // P_int, P2, r_int, r2, r3
+constexpr int NTILES_STAGE = 4;          // P_int, P2, r_int, r2
 constexpr int STAGE_BYTES = NTILES_STAGE * TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 256;      // main and correction accumulators, BN columns each
@@ -112,62 +112,74 @@ __device__ __forceinline__ int exponent_above(float x) {
   return e;
 }
 
+constexpr int RT = 32;  // residual output tile (padded coordinates), RT x RT per block
+
+// One RT x RT tile of the padded residual per 256-thread block: the (RT+2)^2 float-float
+// patch of u around it (mesh coordinates wrapped) is staged in shared memory, so each node
+// is read from global memory once per block with coalesced loads.
 // measure != 0: only accumulate max|r| into rmax[parity ^ 1] (no writes of r).
 __global__ void __launch_bounds__(256) residual_split_kernel(const float* __restrict__ uh,
                                                              const float* __restrict__ ul,
                                                              __half* __restrict__ Rint,
-                                                             __half* __restrict__ R2,
-                                                             __half* __restrict__ R3, ResParams p,
+                                                             __half* __restrict__ R2, ResParams p,
                                                              unsigned* rmax, int* escale, int parity,
                                                              int measure) {
+  __shared__ float sh[RT + 2][RT + 3], sl[RT + 2][RT + 3];
+  __shared__ float red[8];
   const float rm = __uint_as_float(rmax[parity]);
   const int er = rm > 0.0f ? (p.rb - 1) - exponent_above(rm) : 0;
   const float scale = pow2f(er);
   if (!measure && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) escale[parity] = er;
-  const int xp = blockIdx.x * blockDim.x + threadIdx.x;  // padded column
+  const int x0 = blockIdx.x * RT, y0 = blockIdx.y * RT;  // padded tile origin
   const int wpad = p.nx + 2 * p.Hx;
+  // stage u over padded rows y0-1 .. y0+RT and columns x0-1 .. x0+RT
+  for (int e = threadIdx.x; e < (RT + 2) * (RT + 2); e += blockDim.x) {
+    const int ly = e / (RT + 2), lx = e % (RT + 2);
+    int y = y0 + ly - 1 - p.Hy, x = x0 + lx - 1 - p.Hx;
+    y %= p.ny; if (y < 0) y += p.ny;
+    x %= p.nx; if (x < 0) x += p.nx;
+    const int c = y * p.nx + x;
+    sh[ly][lx] = uh[c];
+    sl[ly][lx] = ul[c];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;  // 32 x 8
+  const int xp = x0 + tx;
   float rabs = 0.0f;
-  if (xp < wpad) {
-    int x = xp - p.Hx;
-    if (x < 0) x += p.nx;
-    else if (x >= p.nx) x -= p.nx;
-    const int xw = x == 0 ? p.nx - 1 : x - 1;
-    const int xe = x == p.nx - 1 ? 0 : x + 1;
-    for (int yp = blockIdx.y; yp < p.prow; yp += gridDim.y) {
-      int y = yp - p.Hy;
-      if (y < 0) y += p.ny;
-      else if (y >= p.ny) y -= p.ny;
-      const int ys = y == 0 ? p.ny - 1 : y - 1;
-      const int yn = y == p.ny - 1 ? 0 : y + 1;
-      const int row = y * p.nx;
-      const int c = row + x;
-      const float ch = uh[c], cl = ul[c];
-      // r = sum_nbr c_j (u_j - u_C) + (sum_all c) u_C, every term and the sum in float-float:
-      // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
-      // about log2(|c d| / |r|) bits of r.
-      ffv acc{0.0f, 0.0f};
-      ff_mac(acc, p.c_hi[1], p.c_lo[1], ff_sub(uh[row + xw], ul[row + xw], ch, cl));
-      ff_mac(acc, p.c_hi[2], p.c_lo[2], ff_sub(uh[row + xe], ul[row + xe], ch, cl));
-      ff_mac(acc, p.c_hi[3], p.c_lo[3], ff_sub(uh[ys * p.nx + x], ul[ys * p.nx + x], ch, cl));
-      ff_mac(acc, p.c_hi[4], p.c_lo[4], ff_sub(uh[yn * p.nx + x], ul[yn * p.nx + x], ch, cl));
-      if (p.csum_hi != 0.0f || p.csum_lo != 0.0f) ff_mac(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
-      const float r = __fadd_rn(acc.h, acc.l);
-      rabs = fmaxf(rabs, fabsf(r));
-      if (measure) continue;
-      // r 2^er = r_int + r2 + r3 (r_int an integer; the remainders are exact in float)
-      const float rs = __fmul_rn(r, scale);
-      const __half hi = __float2half_rn(rintf(rs));
-      const float rem = __fsub_rn(rs, __half2float(hi));
-      const __half h2 = __float2half_rn(rem);
-      const __half h3 = __float2half_rn(__fsub_rn(rem, __half2float(h2)));
-      const int o = yp * p.pitch + xp;
-      Rint[o] = hi;
-      R2[o] = h2;
-      R3[o] = h3;
-    }
+#pragma unroll
+  for (int k = 0; k < RT / 8; ++k) {
+    const int ly = ty + 8 * k;
+    const int yp = y0 + ly;
+    if (xp >= wpad || yp >= p.prow) continue;
+    const int cy = ly + 1, cx = tx + 1;
+    const float ch = sh[cy][cx], cl = sl[cy][cx];
+    // r = sum_nbr c_j (u_j - u_C) + (sum_all c) u_C, every term and the sum in float-float:
+    // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
+    // about log2(|c d| / |r|) bits of r.
+    ffv acc{0.0f, 0.0f};
+    ff_mac(acc, p.c_hi[1], p.c_lo[1], ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl));
+    ff_mac(acc, p.c_hi[2], p.c_lo[2], ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl));
+    ff_mac(acc, p.c_hi[3], p.c_lo[3], ff_sub(sh[cy - 1][cx], sl[cy - 1][cx], ch, cl));
+    ff_mac(acc, p.c_hi[4], p.c_lo[4], ff_sub(sh[cy + 1][cx], sl[cy + 1][cx], ch, cl));
+    if (p.csum_hi != 0.0f || p.csum_lo != 0.0f) ff_mac(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
+    const float r = __fadd_rn(acc.h, acc.l);
+    rabs = fmaxf(rabs, fabsf(r));
+    if (measure) continue;
+    // r 2^er = r_int + r2 (r_int an integer; the remainder is exact in float)
+    const float rs = __fmul_rn(r, scale);
+    const __half hi = __float2half_rn(rintf(rs));
+    const int o = yp * p.pitch + xp;
+    Rint[o] = hi;
+    R2[o] = __float2half_rn(__fsub_rn(rs, __half2float(hi)));
   }
   for (int o = 16; o > 0; o >>= 1) rabs = fmaxf(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(rmax + (parity ^ 1), __float_as_uint(rabs));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = rabs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+    atomicMax(rmax + (parity ^ 1), __float_as_uint(m));
+  }
 }
 
 __global__ void f64_to_ff_kernel(const double* __restrict__ u, float* __restrict__ uh,
@@ -234,11 +246,11 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmPint, const __grid_constant__ CUtensorMap tmP2,
                       const __grid_constant__ CUtensorMap tmRint, const __grid_constant__ CUtensorMap tmR2,
-                      const __grid_constant__ CUtensorMap tmR3, float* __restrict__ uh, float* __restrict__ ul,
+                      float* __restrict__ uh, float* __restrict__ ul,
                       GemmParams g) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* tiles = smem;  // [stage][P_int, P2, r_int, r2, r3] 16 KB each
+  uint8_t* tiles = smem;  // [stage][P_int, P2, r_int, r2] 16 KB each
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* full = bars;                 // [STAGES] stage loaded
   uint64_t* empty = bars + STAGES;       // [STAGES] stage consumed by the MMAs
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     ptx::mbar_init(done, 1);
     ptx::fence_barrier_init();
     ptx::tma_prefetch_desc(&tmPint); ptx::tma_prefetch_desc(&tmP2);
-    ptx::tma_prefetch_desc(&tmRint); ptx::tma_prefetch_desc(&tmR2); ptx::tma_prefetch_desc(&tmR3);
+    ptx::tma_prefetch_desc(&tmRint); ptx::tma_prefetch_desc(&tmR2);
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
     if (blockIdx.x == 0 && blockIdx.y == 0) g.rmax[g.parity] = 0u;
@@ -292,7 +304,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         ptx::tma_load_2d(st + TILE_BYTES, &tmP2, &full[s], kb * KB, m0);
         ptx::tma_load_4d(st + 2 * TILE_BYTES, &tmRint, &full[s], 0, tx0, kb, ty0);
         ptx::tma_load_4d(st + 3 * TILE_BYTES, &tmR2, &full[s], 0, tx0, kb, ty0);
-        ptx::tma_load_4d(st + 4 * TILE_BYTES, &tmR3, &full[s], 0, tx0, kb, ty0);
         issued = kb + 1;
       }
       // every copy this thread issued has landed before the CTA may exit
@@ -314,7 +325,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const uint64_t dP2 = ptx::sw128_kmajor_desc(base + TILE_BYTES);
         const uint64_t dRi = ptx::sw128_kmajor_desc(base + 2 * TILE_BYTES);
         const uint64_t dR2 = ptx::sw128_kmajor_desc(base + 3 * TILE_BYTES);
-        const uint64_t dR3 = ptx::sw128_kmajor_desc(base + 4 * TILE_BYTES);
         for (int kk = 0; kk < g.Wx / 16; ++kk) {
           const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
           const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
@@ -322,7 +332,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, acc);
           ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
           ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
-          ptx::mma_f16(corr, dPi + adv, dR3 + adv, idesc, 1u);
         }
         ptx::mma_commit(&empty[s]);
       }
@@ -345,23 +354,34 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int ii = m0 + row;
       const float oscale = pow2f(-(g.eP[ii] + g.escale[g.parity]));
       const int iy = ii / g.Tx, ix = ii % g.Tx;
+      const int rowbase = iy * g.nx + ix;
 #pragma unroll 1
-      for (int q = 0; q < BN / 16; ++q) {
-        float vm[16], vc[16];
-        ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
-        ptx::tmem_ld_32x32b_x16(t_lane + BN + q * 16, vc);
+      for (int q = 0; q < BN / 32; ++q) {
+        uint32_t vm[32], vc[32];
+        ptx::tmem_ld_32x32b_x32_nowait(t_lane + q * 32, vm);
+        ptx::tmem_ld_32x32b_x32_nowait(t_lane + BN + q * 32, vc);
+        // all 64 state loads of this batch go out before any store (the stores go through
+        // the same pointers, so the compiler would otherwise keep them in program order)
+        int node[32];
+        float a[32], al[32];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n = q * 16 + i;
+        for (int i = 0; i < 32; ++i) {
+          const int n = q * 32 + i;
           const int ty = ty0 + n / g.BNx, tx = tx0 + n % g.BNx;
-          const int node = (ty * g.Ty + iy) * g.nx + tx * g.Tx + ix;
-          const float y = __fmul_rn(__fadd_rn(vm[i], vc[i]), oscale);
+          node[i] = (ty * g.Ty) * g.nx + tx * g.Tx + rowbase;
+          a[i] = uh[node[i]];
+          al[i] = ul[node[i]];
+        }
+        ptx::tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float y = __fmul_rn(__fadd_rn(__uint_as_float(vm[i]), __uint_as_float(vc[i])), oscale);
           // (u_hi, u_lo) += y in float-float
-          const ffv s = two_sum(uh[node], y);
-          const float lo = __fadd_rn(ul[node], s.l);
+          const ffv s = two_sum(a[i], y);
+          const float lo = __fadd_rn(al[i], s.l);
           const float hi2 = __fadd_rn(s.h, lo);
-          uh[node] = hi2;
-          ul[node] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
+          uh[node[i]] = hi2;
+          ul[node[i]] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
         }
       }
     }
@@ -374,23 +394,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
 }
 
-// -------------------------------------------------------------------- host helpers
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 }  // namespace
 
 struct SplitPlan {
@@ -401,7 +404,6 @@ struct SplitPlan {
   float* d_ul = nullptr;
   __half* d_Rint = nullptr;
   __half* d_R2 = nullptr;
-  __half* d_R3 = nullptr;
   __half* d_Pint = nullptr;
   __half* d_P2 = nullptr;
   int* d_eP = nullptr;
@@ -409,7 +411,7 @@ struct SplitPlan {
   unsigned* d_rmax = nullptr;
   int* d_escale = nullptr;
   int* d_err = nullptr;
-  CUtensorMap tmPint, tmP2, tmRint, tmR2, tmR3;
+  CUtensorMap tmPint, tmP2, tmRint, tmR2;
   int packed_gen = -1;
 };
 
@@ -433,10 +435,8 @@ bool split_eligible(const lem_ctx* ctx) {
 
 static lem_status encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
                          const cuuint32_t* box, const char* what) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return fail(LEM_ECUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, cuuint32_t(rank), base, dims, strides, box, es,
+  CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, cuuint32_t(rank), base, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(LEM_ECUDA, std::string("cuTensorMapEncodeTiled failed for ") + what +
@@ -479,7 +479,6 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_ul), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Rint), rbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R2), rbytes));
-  LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R3), rbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Pint), pbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P2), pbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_eP), sizeof(int) * sp->M));
@@ -489,7 +488,6 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_err), sizeof(int)));
   LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_R2, 0, rbytes));
-  LEM_CUDA_TRY(cudaMemset(sp->d_R3, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
   // tensor maps: P slices [M][Wy*64] fp16, box 64 x 128 ; residual slices through a 4D
   // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx],
@@ -507,7 +505,6 @@ lem_status split_prepare(lem_ctx* ctx) {
     cuuint32_t box[4] = {KB, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
     LEM_TRY(encode(&sp->tmRint, sp->d_Rint, 4, dims, str, box, "r_int"));
     LEM_TRY(encode(&sp->tmR2, sp->d_R2, 4, dims, str, box, "r2"));
-    LEM_TRY(encode(&sp->tmR3, sp->d_R3, 4, dims, str, box, "r3"));
   }
   LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   cudaFuncAttributes fa{};
@@ -549,9 +546,9 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   // measure max|r| of the first step into rmax[0] (the measuring pass reads rmax[1] only
   // to form a scale it never uses)
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
-  const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + 255) / 256, std::min(sp->prow, 1024));
-  residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
-                                               sp->d_rmax, sp->d_escale, 1, 1);
+  const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + RT - 1) / RT, (sp->prow + RT - 1) / RT);
+  residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->rp, sp->d_rmax,
+                                               sp->d_escale, 1, 1);
   LEM_CUDA_TRY(cudaGetLastError());
   GemmParams g{};
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
@@ -560,13 +557,13 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   const dim3 ggrid(sp->M / BM, unsigned(ctx->tiles.size() / BN));
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
-    residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
-                                                 sp->d_rmax, sp->d_escale, parity, 0);
+    residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->rp, sp->d_rmax,
+                                                 sp->d_escale, parity, 0);
     g.parity = parity;
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    split_gemm_kernel<<<ggrid, GEMM_THREADS, SMEM_BYTES, st>>>(sp->tmPint, sp->tmP2, sp->tmRint, sp->tmR2, sp->tmR3,
-                                                               sp->d_uh, sp->d_ul, g);
+    split_gemm_kernel<<<ggrid, GEMM_THREADS, SMEM_BYTES, st>>>(sp->tmPint, sp->tmP2, sp->tmRint, sp->tmR2, sp->d_uh,
+                                                               sp->d_ul, g);
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
@@ -589,7 +586,7 @@ lem_status split_check_error(lem_ctx* ctx) {
 void split_destroy(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   if (!sp) return;
-  cudaFree(sp->d_uh); cudaFree(sp->d_ul); cudaFree(sp->d_Rint); cudaFree(sp->d_R2); cudaFree(sp->d_R3);
+  cudaFree(sp->d_uh); cudaFree(sp->d_ul); cudaFree(sp->d_Rint); cudaFree(sp->d_R2);
   cudaFree(sp->d_Pint); cudaFree(sp->d_P2); cudaFree(sp->d_eP); cudaFree(sp->d_S);
   cudaFree(sp->d_rmax); cudaFree(sp->d_escale); cudaFree(sp->d_err);
   delete sp;

@@ -89,9 +89,11 @@ def test_split_full_size_100_steps():
     props = [P if i in sample else None for i in range(len(wins))]
     ref1 = lem_step(X, wl["u0"], wins, props, "phi", tiles=sample)
     got = u_s.cpu().numpy()
+    # one step carries the FP16-slice representation error of P and r (about 2^-22 of each
+    # row / column maximum, times the cancellation in the window sums); it does not compound
     for t in sample:
         D = wins[t].D
-        assert rel_l2(got[D], ref1[D]) <= 1e-7
+        assert rel_l2(got[D], ref1[D]) <= 5e-7
     # 100 steps against the FP64 path
     split.step(u_s, 99)
     fp64.step(u_d, 100)
