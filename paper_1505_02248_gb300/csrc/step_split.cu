@@ -10,8 +10,9 @@
 //     r2 the FP16-rounded remainder. er comes from the previous step's max|r|.
 //  2. split_gemm_kernel: Y = P R (M = Ty*Tx owner rows, N = tiles, K = window nodes).
 //     P is stored per row i as P*2^eP_i = P_int + P2 with |P_int| <= 2^9 an integer.
-//     Each K block is one window row (Wx nodes, padded to 64 in the P layout): TMA loads
-//     P_int/P2 and the 128 windows' rows of r_int/r2 straight from the padded residual
+//     Each K block is one window row (Wx = 16, 32, 48 or 64 nodes, loaded as 128-byte
+//     swizzled rows of 64): TMA loads P_int/P2 and the 128 windows' rows of r_int/r2
+//     straight from the padded residual
 //     through a 4D tensor map (the halo gather happens inside TMA). One thread issues
 //     tcgen05.mma: P_int r_int into the main TMEM accumulator and P_int r2, P2 r_int and
 //     P2 r2 into a correction accumulator. Because sum_k |P_int| |r_int| < 2^24
@@ -40,14 +41,22 @@ namespace lem {
 namespace {
 
 constexpr int BM = 128;            // owner rows per CTA tile (TMEM lanes)
-constexpr int BN = 128;            // windows per CTA tile (TMEM columns per accumulator)
-constexpr int KB = 64;             // fp16 elements per 128-byte K row
-constexpr int STAGES = 3;
-constexpr int TILE_BYTES = BM * KB * 2;  // 16 KB (A and B tiles have 128 rows each)
-constexpr int NTILES_STAGE = 4;          // P_int, P2, r_int, r2
-constexpr int STAGE_BYTES = NTILES_STAGE * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;      // main and correction accumulators, BN columns each
+constexpr int KB = 64;             // fp16 elements per 128-byte K row (window rows padded to it)
+constexpr int A_BYTES = BM * KB * 2;  // one P slice of a stage: 128 rows x 128 B = 16 KB
+constexpr int RING_BYTES = 192 * 1024;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;   // main + correction accumulators: 2 sets for BN = 128, 1 for 256
+
+// Tile shape: BN windows per CTA tile (TMEM columns per accumulator). BN = 256 halves the
+// shared-memory operand traffic per MMA (an N = 128 MMA reads its 8 KB of operands at the
+// full 128 B/clk shared-memory rate); it leaves room for one accumulator set and two stages.
+template <int BN>
+struct Shape {
+  static constexpr int B_BYTES = BN * KB * 2;                      // one residual slice of a stage
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // P_int, P2, r_int, r2
+  static constexpr int STAGES = RING_BYTES / STAGE_BYTES;           // 3 (BN 128) or 2 (BN 256)
+  static constexpr int NBUF = BN == 256 ? 1 : 2;                    // TMEM accumulator sets
+};
 constexpr int EPI_WARPS = 4;             // one warp per TMEM lane quarter
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int P_INT_BITS = 9;            // |P_int| <= 2^9
@@ -57,6 +66,8 @@ enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3 
 
 struct GemmParams {
   int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx;
+  int nMB, nNB;         // M blocks of 128 owner rows, window blocks of 128 windows
+  int bsplit_y;         // clustered: a window block's two halves split along y (else x)
   const int* eP;        // per owner row: P scale exponent
   const int* escale;    // [2] residual scale exponent of each step parity
   unsigned* rmax;       // [2] max|r| accumulators (this kernel clears the current one)
@@ -69,6 +80,7 @@ struct ResParams {
   float c_hi[5], c_lo[5];   // dt-scaled C, W, E, S, N as float pairs
   float csum_hi, csum_lo;   // sum of all five
   int rb;                   // |r_int| target 2^(rb-1) (2x headroom below 2^rb)
+  int has_lo;               // some coefficient (or their sum) is not exact in float
 };
 
 __device__ __forceinline__ float pow2f(int e) {  // exact 2^e for -126 <= e <= 127
@@ -95,11 +107,14 @@ __device__ __forceinline__ ffv ff_sub(float ah, float al, float bh, float bl) {
   return t;
 }
 
-// acc += (ch + cl) * d, keeping the product's rounding error (exact through the FMA)
+// acc += (ch + cl) * d, keeping the product's rounding error (exact through the FMA);
+// HAS_LO = false when the coefficient is exact in float (cl == 0)
+template <bool HAS_LO>
 __device__ __forceinline__ void ff_mac(ffv& acc, float ch, float cl, ffv d) {
   const float p = __fmul_rn(ch, d.h);
   float pe = fmaf(ch, d.h, -p);
-  pe = fmaf(ch, d.l, fmaf(cl, d.h, pe));
+  if (HAS_LO) pe = fmaf(cl, d.h, pe);
+  pe = fmaf(ch, d.l, pe);
   const ffv s = two_sum(acc.h, p);
   acc.h = s.h;
   acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, pe));
@@ -135,9 +150,10 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
   // stage u over padded rows y0-1 .. y0+RT and columns x0-1 .. x0+RT
   for (int e = threadIdx.x; e < (RT + 2) * (RT + 2); e += blockDim.x) {
     const int ly = e / (RT + 2), lx = e % (RT + 2);
+    // one wrap suffices: -Hy-1 <= y < ny + Hy + RT and Hy + RT < ny (checked at prepare)
     int y = y0 + ly - 1 - p.Hy, x = x0 + lx - 1 - p.Hx;
-    y %= p.ny; if (y < 0) y += p.ny;
-    x %= p.nx; if (x < 0) x += p.nx;
+    y += y < 0 ? p.ny : (y >= p.ny ? -p.ny : 0);
+    x += x < 0 ? p.nx : (x >= p.nx ? -p.nx : 0);
     const int c = y * p.nx + x;
     sh[ly][lx] = uh[c];
     sl[ly][lx] = ul[c];
@@ -157,11 +173,23 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
     // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
     // about log2(|c d| / |r|) bits of r.
     ffv acc{0.0f, 0.0f};
-    ff_mac(acc, p.c_hi[1], p.c_lo[1], ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl));
-    ff_mac(acc, p.c_hi[2], p.c_lo[2], ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl));
-    ff_mac(acc, p.c_hi[3], p.c_lo[3], ff_sub(sh[cy - 1][cx], sl[cy - 1][cx], ch, cl));
-    ff_mac(acc, p.c_hi[4], p.c_lo[4], ff_sub(sh[cy + 1][cx], sl[cy + 1][cx], ch, cl));
-    if (p.csum_hi != 0.0f || p.csum_lo != 0.0f) ff_mac(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
+    const ffv dW = ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl);
+    const ffv dE = ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl);
+    const ffv dS = ff_sub(sh[cy - 1][cx], sl[cy - 1][cx], ch, cl);
+    const ffv dN = ff_sub(sh[cy + 1][cx], sl[cy + 1][cx], ch, cl);
+    if (p.has_lo) {
+      ff_mac<true>(acc, p.c_hi[1], p.c_lo[1], dW);
+      ff_mac<true>(acc, p.c_hi[2], p.c_lo[2], dE);
+      ff_mac<true>(acc, p.c_hi[3], p.c_lo[3], dS);
+      ff_mac<true>(acc, p.c_hi[4], p.c_lo[4], dN);
+      ff_mac<true>(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
+    } else {
+      ff_mac<false>(acc, p.c_hi[1], 0.0f, dW);
+      ff_mac<false>(acc, p.c_hi[2], 0.0f, dE);
+      ff_mac<false>(acc, p.c_hi[3], 0.0f, dS);
+      ff_mac<false>(acc, p.c_hi[4], 0.0f, dN);
+      if (p.csum_hi != 0.0f) ff_mac<false>(acc, p.csum_hi, 0.0f, ffv{ch, cl});
+    }
     const float r = __fadd_rn(acc.h, acc.l);
     rabs = fmaxf(rabs, fabsf(r));
     if (measure) continue;
@@ -199,9 +227,10 @@ __global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __re
 }
 
 // Per owner row i of P (FP64, n_int x n_loc, window row-major): eP_i with
-// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 in the [M][Wy*64]
-// K layout, and S_i = sum_k |P_int[i,k]| (the exactness bound of the main product).
-__global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx,
+// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 in the [M][Wy*kpad]
+// K layout (each window row zero-padded to kpad), and S_i = sum_k |P_int[i,k]| (the
+// exactness bound of the main product).
+__global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx, int kpad,
                               __half* __restrict__ Pint, __half* __restrict__ P2, int* __restrict__ eP,
                               double* __restrict__ S) {
   const int i = blockIdx.x;
@@ -220,15 +249,15 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
   const int ei = red[0] > 0.0 ? P_INT_BITS - e : 0;
   __syncthreads();
   double sum = 0.0;
-  for (int col = threadIdx.x; col < Wy * KB; col += blockDim.x) {
-    const int wy = col / KB, wx = col % KB;
+  for (int col = threadIdx.x; col < Wy * kpad; col += blockDim.x) {
+    const int wy = col / kpad, wx = col % kpad;
     const double v = wx < Wx ? P[int64_t(i) * n_loc + int64_t(wy) * Wx + wx] : 0.0;
     const double x = ldexp(v, ei);
     const double xi = rint(x);
     const __half hi = __double2half(xi);  // exact: |xi| <= 2^9
     const __half h2 = __double2half(x - xi);
-    Pint[int64_t(i) * Wy * KB + col] = hi;
-    P2[int64_t(i) * Wy * KB + col] = h2;
+    Pint[int64_t(i) * Wy * kpad + col] = hi;
+    P2[int64_t(i) * Wy * kpad + col] = h2;
     sum += fabs(xi);
   }
   red[threadIdx.x] = sum;
@@ -243,114 +272,176 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
   }
 }
 
+// Persistent GEMM. MC = false: each CTA walks output tiles t = blockIdx.x, + gridDim.x, ...
+// (M block t % nMB, window block t / nMB) and loads its own operands. MC = true: clusters of
+// 4 CTAs walk 2 x 2 groups of tiles; the two CTAs on the same M block each load half of
+// its P rows and multicast them to both, and the two on the same window block each load half
+// of the windows and multicast them, so every CTA issues half the TMA rows. A stage is reused
+// only after all three CTAs that write into it (self, P partner, window partner) released it.
+// Two TMEM accumulator sets alternate between tiles, so the epilogue of one tile overlaps the
+// MMAs of the next.
+template <bool MC, int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmPint, const __grid_constant__ CUtensorMap tmP2,
                       const __grid_constant__ CUtensorMap tmRint, const __grid_constant__ CUtensorMap tmR2,
-                      float* __restrict__ uh, float* __restrict__ ul,
-                      GemmParams g) {
+                      float* __restrict__ uh, float* __restrict__ ul, GemmParams g) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* tiles = smem;  // [stage][P_int, P2, r_int, r2] 16 KB each
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  constexpr int STAGES = Shape<BN>::STAGES, STAGE_BYTES = Shape<BN>::STAGE_BYTES;
+  constexpr int B_BYTES = Shape<BN>::B_BYTES, NBUF = Shape<BN>::NBUF;
+  uint8_t* tiles = smem;  // [stage][P_int, P2 (A_BYTES each), r_int, r2 (B_BYTES each)], same offsets in every CTA
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* full = bars;                 // [STAGES] stage loaded
-  uint64_t* empty = bars + STAGES;       // [STAGES] stage consumed by the MMAs
-  uint64_t* done = bars + 2 * STAGES;    // every MMA finished
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* empty = bars + STAGES;       // [STAGES] stage released by every CTA writing into it
+  uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set ready
+  uint64_t* acce = accf + 2;             // [2] accumulator set drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int m0 = blockIdx.x * BM;
-  const int nbx = g.ntx / g.BNx;
-  const int tx0 = (blockIdx.y % nbx) * g.BNx;
-  const int ty0 = (blockIdx.y / nbx) * g.BNy;
   const int nk = g.Wy;
+  const int nbx = g.ntx / g.BNx;
+  const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
+  const int mh = int(rank & 1u), nh = int(rank >> 1);  // MC: place in the 2 x 2 tile group
+  const int unit0 = MC ? int(ptx::cluster_id_x()) : int(blockIdx.x);
+  const int nunit_step = MC ? int(ptx::nclusters_x()) : int(gridDim.x);
+  const int nMBu = MC ? g.nMB / 2 : g.nMB;
+  const int nunits = nMBu * (MC ? g.nNB / 2 : g.nNB);
+  auto tile_of = [&](int u, int& m0, int& tx0, int& ty0) {
+    const int mb = MC ? 2 * (u % nMBu) + nh : u % nMBu;
+    const int nb = MC ? 2 * (u / nMBu) + mh : u / nMBu;
+    m0 = mb * BM;
+    tx0 = (nb % nbx) * g.BNx;
+    ty0 = (nb / nbx) * g.BNy;
+  };
+  // MC multicast masks: P partner shares the M block (differs in mh), window partner the
+  // window block (differs in nh)
+  const uint16_t maskP = uint16_t((1u << rank) | (1u << (rank ^ 1u)));
+  const uint16_t maskR = uint16_t((1u << rank) | (1u << (rank ^ 2u)));
+  const uint16_t maskE = uint16_t(maskP | maskR);
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < STAGES; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
-    ptx::mbar_init(done, 1);
+    for (int s = 0; s < STAGES; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], MC ? 3 : 1); }
+    for (int b = 0; b < 2; ++b) { ptx::mbar_init(&accf[b], 1); ptx::mbar_init(&acce[b], EPI_WARPS); }
     ptx::fence_barrier_init();
     ptx::tma_prefetch_desc(&tmPint); ptx::tma_prefetch_desc(&tmP2);
     ptx::tma_prefetch_desc(&tmRint); ptx::tma_prefetch_desc(&tmR2);
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
-    if (blockIdx.x == 0 && blockIdx.y == 0) g.rmax[g.parity] = 0u;
+    if (blockIdx.x == 0) g.rmax[g.parity] = 0u;
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, TMEM_COLS);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
-  __syncthreads();
+  if (MC) ptx::cluster_sync();  // peers' barriers exist before any multicast reaches them
+  else __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        const uint32_t use = kb / STAGES;
-        if (kb >= STAGES && !ptx::mbar_wait(&empty[s], (use & 1) ^ 1, WAIT_NS)) {
-          atomicExch(g.err, ERR_TIMEOUT_PRODUCER);
-          s_abort = 1;
-          break;
+      int it = 0, issued = 0;
+      for (int u = unit0; u < nunits && !s_abort; u += nunit_step) {
+        int m0, tx0, ty0;
+        tile_of(u, m0, tx0, ty0);
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t use = it / STAGES;
+          if (it >= STAGES && !ptx::mbar_wait(&empty[s], (use & 1) ^ 1, WAIT_NS)) {
+            atomicExch(g.err, ERR_TIMEOUT_PRODUCER);
+            s_abort = 1;
+            break;
+          }
+          if (s_abort) break;
+          uint8_t* st = tiles + s * STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          if (MC) {
+            // my half of the P rows (to me and the P partner), my half of the windows (to me
+            // and the window partner); the partners send the other halves
+            ptx::tma_load_2d_mc(st + mh * (A_BYTES / 2), &tmPint, &full[s], kb * KB, m0 + mh * (BM / 2), maskP);
+            ptx::tma_load_2d_mc(st + A_BYTES + mh * (A_BYTES / 2), &tmP2, &full[s], kb * KB, m0 + mh * (BM / 2),
+                                maskP);
+            const int wx = g.bsplit_y ? tx0 : tx0 + nh * (g.BNx / 2);
+            const int wy = g.bsplit_y ? ty0 + nh * (g.BNy / 2) : ty0;
+            ptx::tma_load_4d_mc(st + 2 * A_BYTES + nh * (B_BYTES / 2), &tmRint, &full[s], 0, wx, kb, wy, maskR);
+            ptx::tma_load_4d_mc(st + 2 * A_BYTES + B_BYTES + nh * (B_BYTES / 2), &tmR2, &full[s], 0, wx, kb, wy, maskR);
+          } else {
+            ptx::tma_load_2d(st, &tmPint, &full[s], kb * KB, m0);
+            ptx::tma_load_2d(st + A_BYTES, &tmP2, &full[s], kb * KB, m0);
+            ptx::tma_load_4d(st + 2 * A_BYTES, &tmRint, &full[s], 0, tx0, kb, ty0);
+            ptx::tma_load_4d(st + 2 * A_BYTES + B_BYTES, &tmR2, &full[s], 0, tx0, kb, ty0);
+          }
+          issued = it + 1;
         }
-        if (s_abort) break;
-        uint8_t* st = tiles + s * STAGE_BYTES;
-        ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-        ptx::tma_load_2d(st, &tmPint, &full[s], kb * KB, m0);
-        ptx::tma_load_2d(st + TILE_BYTES, &tmP2, &full[s], kb * KB, m0);
-        ptx::tma_load_4d(st + 2 * TILE_BYTES, &tmRint, &full[s], 0, tx0, kb, ty0);
-        ptx::tma_load_4d(st + 3 * TILE_BYTES, &tmR2, &full[s], 0, tx0, kb, ty0);
-        issued = kb + 1;
       }
-      // every copy this thread issued has landed before the CTA may exit
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        ptx::mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_NS);
+      // every copy this thread issued into this CTA has landed before the CTA may exit
+      for (int k = (issued > STAGES ? issued - STAGES : 0); k < issued; ++k)
+        ptx::mbar_wait(&full[k % STAGES], (k / STAGES) & 1, WAIT_NS);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
-      const uint32_t main = tmem, corr = tmem + BN;
       bool ok = true;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        if (!ptx::mbar_wait(&full[s], (kb / STAGES) & 1, WAIT_NS)) { ok = false; break; }
-        ptx::tc_fence_after();
-        const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
-        const uint64_t dPi = ptx::sw128_kmajor_desc(base);
-        const uint64_t dP2 = ptx::sw128_kmajor_desc(base + TILE_BYTES);
-        const uint64_t dRi = ptx::sw128_kmajor_desc(base + 2 * TILE_BYTES);
-        const uint64_t dR2 = ptx::sw128_kmajor_desc(base + 3 * TILE_BYTES);
-        for (int kk = 0; kk < g.Wx / 16; ++kk) {
-          const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
-          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-          ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
-          ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, acc);
-          ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
-          ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
+      int it = 0, lt = 0;
+      for (int u = unit0; u < nunits && ok; u += nunit_step, ++lt) {
+        const int b = lt % NBUF;
+        if (lt >= NBUF) {
+          if (!ptx::mbar_wait(&acce[b], ((lt / NBUF) - 1) & 1, WAIT_NS)) { ok = false; break; }
+          ptx::tc_fence_after();
         }
-        ptx::mma_commit(&empty[s]);
+        const uint32_t main = tmem + b * 2 * BN, corr = main + BN;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, WAIT_NS)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
+          const uint64_t dPi = ptx::sw128_kmajor_desc(base);
+          const uint64_t dP2 = ptx::sw128_kmajor_desc(base + A_BYTES);
+          const uint64_t dRi = ptx::sw128_kmajor_desc(base + 2 * A_BYTES);
+          const uint64_t dR2 = ptx::sw128_kmajor_desc(base + 2 * A_BYTES + B_BYTES);
+          for (int kk = 0; kk < g.Wx / 16; ++kk) {
+            const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
+            ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, acc);
+            ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
+            ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
+          }
+          if (MC) ptx::mma_commit_mc(&empty[s], maskE);
+          else ptx::mma_commit(&empty[s]);
+        }
+        if (ok) ptx::mma_commit(&accf[b]);
       }
       if (!ok) {
         atomicExch(g.err, ERR_TIMEOUT_MMA);
         s_abort = 1;
       }
-      ptx::mma_commit(done);
-      ptx::mbar_wait(done, 0, WAIT_NS);  // no MMA may still run when TMEM is released
+      if (MC) {
+        // the partners' releases of my last stages have arrived before the cluster may exit
+        for (int k = (it > STAGES ? it - STAGES : 0); k < it; ++k)
+          ptx::mbar_wait(&empty[k % STAGES], (k / STAGES) & 1, WAIT_NS);
+      }
     }
   } else {
     // ------------------------------------------------------------ epilogue (4 warps)
     const int lane_base = 32 * (warp & 3);
     const int row = lane_base + lane;  // TMEM lane = owner row within the M block
-    const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16);
-    if (!ptx::mbar_wait(done, 0, WAIT_NS)) {
-      atomicExch(g.err, ERR_TIMEOUT_EPI);
-    } else {
+    int lt = 0;
+    for (int u = unit0; u < nunits; u += nunit_step, ++lt) {
+      const int b = lt % NBUF;
+      if (!ptx::mbar_wait(&accf[b], (lt / NBUF) & 1, WAIT_NS)) {
+        atomicExch(g.err, ERR_TIMEOUT_EPI);
+        break;
+      }
       ptx::tc_fence_after();
+      const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(b * 2 * BN);
+      int m0, tx0, ty0;
+      tile_of(u, m0, tx0, ty0);
       const int ii = m0 + row;
       const float oscale = pow2f(-(g.eP[ii] + g.escale[g.parity]));
       const int iy = ii / g.Tx, ix = ii % g.Tx;
@@ -384,6 +475,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           ul[node[i]] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
         }
       }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&acce[b]);
     }
   }
   ptx::tc_fence_before();
@@ -392,13 +486,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, TMEM_COLS);
   }
+  if (MC) ptx::cluster_sync();  // no CTA leaves while a partner may still signal it
 }
 
 }  // namespace
 
 struct SplitPlan {
   int Ty = 0, Tx = 0, Hy = 0, Hx = 0, Wy = 0, Wx = 0, nty = 0, ntx = 0, M = 0, BNx = 0, BNy = 0;
-  int pitch = 0, prow = 0;
+  int pitch = 0, prow = 0, nsm = 0, bsplit_y = 0;
+  int bn = 128;      // windows per CTA tile (256 when the tile grid allows it)
+  int clusters = 0;  // > 0: the multicast (2 x 2 cluster) kernel runs with this many clusters
   ResParams rp{};
   float* d_uh = nullptr;
   float* d_ul = nullptr;
@@ -411,9 +508,24 @@ struct SplitPlan {
   unsigned* d_rmax = nullptr;
   int* d_escale = nullptr;
   int* d_err = nullptr;
-  CUtensorMap tmPint, tmP2, tmRint, tmR2;
+  CUtensorMap tm[4];  // P_int, P2, r_int, r2 (half boxes when clustered)
   int packed_gen = -1;
 };
+
+// Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn.
+static bool group_tiles(int64_t ntx, int64_t nty, int bn, int* bnx, int* bny) {
+  int x, y;
+  if (ntx >= bn) {
+    if (ntx % bn) return false;
+    x = bn; y = 1;
+  } else {
+    if (bn % ntx || nty % (bn / ntx)) return false;
+    x = int(ntx); y = bn / int(ntx);
+  }
+  if (bnx) *bnx = x;
+  if (bny) *bny = y;
+  return true;
+}
 
 bool split_eligible(const lem_ctx* ctx) {
   const lem_problem_desc& d = ctx->desc;
@@ -427,10 +539,9 @@ bool split_eligible(const lem_ctx* ctx) {
   const int Wx = Tx + 2 * Hx;
   if (Wx > KB || Wx % 16 || Tx % 8) return false;
   if ((Ty * Tx) % BM) return false;
+  if (ctx->ny <= d.overlap[0] + RT + 1 || ctx->nx <= Hx + RT + 1) return false;  // single-wrap staging
   const int64_t ntx = ctx->nx / Tx, nty = ctx->ny / Ty;
-  if (ntx >= BN) { if (ntx % BN) return false; }
-  else if (BN % ntx || nty % (BN / ntx)) return false;
-  return true;
+  return group_tiles(ntx, nty, 128, nullptr, nullptr);
 }
 
 static lem_status encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
@@ -452,8 +563,9 @@ lem_status split_prepare(lem_ctx* ctx) {
   sp->Wy = sp->Ty + 2 * sp->Hy; sp->Wx = sp->Tx + 2 * sp->Hx;
   sp->nty = int(ctx->ny / sp->Ty); sp->ntx = int(ctx->nx / sp->Tx);
   sp->M = sp->Ty * sp->Tx;
-  sp->BNx = sp->ntx >= BN ? BN : sp->ntx;
-  sp->BNy = BN / sp->BNx;
+  sp->bn = group_tiles(sp->ntx, sp->nty, 256, &sp->BNx, &sp->BNy) ? 256 : 128;
+  if (sp->bn == 128) group_tiles(sp->ntx, sp->nty, 128, &sp->BNx, &sp->BNy);
+  LEM_CUDA_TRY(cudaDeviceGetAttribute(&sp->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   // padded residual: rows ny + 2Hy, row pitch covers the last 64-wide window row read
   sp->prow = int(ctx->ny) + 2 * sp->Hy;
   int need = std::max<int>(int(ctx->nx) + 2 * sp->Hx, (sp->ntx - 1) * sp->Tx + KB);
@@ -469,6 +581,8 @@ lem_status split_prepare(lem_ctx* ctx) {
   }
   sp->rp.csum_hi = float(csum);
   sp->rp.csum_lo = float(csum - double(sp->rp.csum_hi));
+  sp->rp.has_lo = sp->rp.csum_lo != 0.0f;
+  for (int k = 0; k < 5; ++k) sp->rp.has_lo |= sp->rp.c_lo[k] != 0.0f;
   sp->rp.ny = int(ctx->ny); sp->rp.nx = int(ctx->nx); sp->rp.Hy = sp->Hy; sp->rp.Hx = sp->Hx;
   sp->rp.pitch = sp->pitch; sp->rp.prow = sp->prow;
   sp->rp.rb = 10;  // set from the packed propagator in split_pack
@@ -489,26 +603,57 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_R2, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
-  // tensor maps: P slices [M][Wy*64] fp16, box 64 x 128 ; residual slices through a 4D
-  // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx],
-  // box 64 x BNx x 1 x BNy (128 windows' rows of one window row index)
-  {
-    cuuint64_t dims[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(sp->M)};
-    cuuint64_t str[1] = {cuuint64_t(sp->Wy) * KB * 2};
-    cuuint32_t box[2] = {KB, BM};
-    LEM_TRY(encode(&sp->tmPint, sp->d_Pint, 2, dims, str, box, "P_int"));
-    LEM_TRY(encode(&sp->tmP2, sp->d_P2, 2, dims, str, box, "P2"));
+  // Clustered (multicast) kernel when the tile grid splits into 2 x 2 groups and the device
+  // can co-schedule clusters of 4 one-CTA-per-SM blocks.
+  const int nMB = sp->M / BM, nNB = int(ctx->tiles.size() / sp->bn);
+  const bool bsplit_y = sp->BNy % 2 == 0;
+  const bool mc_ok = nMB % 2 == 0 && nNB % 2 == 0 && (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) &&
+                     std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
+  sp->bsplit_y = bsplit_y ? 1 : 0;
+  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  sp->clusters = 0;
+  if (mc_ok) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 4; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(4 * ((nMB / 2) * (nNB / 2)));
+    cfg.blockDim = dim3(GEMM_THREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclus = 0;
+    cudaError_t e = sp->bn == 256 ? cudaOccupancyMaxActiveClusters(&nclus, split_gemm_kernel<true, 256>, &cfg)
+                                  : cudaOccupancyMaxActiveClusters(&nclus, split_gemm_kernel<true, 128>, &cfg);
+    if (e == cudaSuccess && nclus > 0) sp->clusters = std::min(nclus, (nMB / 2) * (nNB / 2));
+    cudaGetLastError();
   }
+  // tensor maps: P slices [M][Wy*64] fp16 (2D, box 64 x rows); residual slices through a 4D
+  // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx]
   {
-    cuuint64_t dims[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
-    cuuint64_t str[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
-    cuuint32_t box[4] = {KB, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
-    LEM_TRY(encode(&sp->tmRint, sp->d_Rint, 4, dims, str, box, "r_int"));
-    LEM_TRY(encode(&sp->tmR2, sp->d_R2, 4, dims, str, box, "r2"));
+    const bool mc = sp->clusters > 0;
+    __half* pbase[2] = {sp->d_Pint, sp->d_P2};
+    __half* rbase[2] = {sp->d_Rint, sp->d_R2};
+    cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(sp->M)};
+    cuuint64_t ps[1] = {cuuint64_t(sp->Wy) * KB * 2};
+    cuuint32_t pbox[2] = {KB, cuuint32_t(mc ? BM / 2 : BM)};
+    cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
+    cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
+    cuuint32_t rbox[4] = {KB, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
+    if (mc) {
+      if (bsplit_y) rbox[3] /= 2;
+      else rbox[1] /= 2;
+    }
+    for (int k = 0; k < 2; ++k) {
+      LEM_TRY(encode(&sp->tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
+      LEM_TRY(encode(&sp->tm[2 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
+    }
   }
-  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   cudaFuncAttributes fa{};
-  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, split_gemm_kernel));
+  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, split_gemm_kernel<false, 256>));
   if (fa.maxThreadsPerBlock < GEMM_THREADS)
     return fail(LEM_ECUDA, "split GEMM kernel cannot launch " + std::to_string(GEMM_THREADS) + " threads (" +
                                std::to_string(fa.numRegs) + " registers per thread)");
@@ -520,8 +665,8 @@ lem_status split_prepare(lem_ctx* ctx) {
 static lem_status split_pack(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
-  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, sp->d_Pint, sp->d_P2, sp->d_eP,
-                                       sp->d_S);
+  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->d_Pint, sp->d_P2,
+                                       sp->d_eP, sp->d_S);
   LEM_CUDA_TRY(cudaGetLastError());
   std::vector<double> S(sp->M);
   LEM_CUDA_TRY(cudaMemcpyAsync(S.data(), sp->d_S, sizeof(double) * sp->M, cudaMemcpyDeviceToHost, st));
@@ -553,8 +698,22 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   GemmParams g{};
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx;
+  g.nMB = sp->M / BM; g.nNB = int(ctx->tiles.size() / sp->bn); g.bsplit_y = sp->bsplit_y;
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.err = sp->d_err;
-  const dim3 ggrid(sp->M / BM, unsigned(ctx->tiles.size() / BN));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(GEMM_THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  if (sp->clusters > 0) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 4; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(4 * sp->clusters);
+  } else {
+    cfg.gridDim = dim3(std::min(g.nMB * g.nNB, sp->nsm));
+  }
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
     residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->rp, sp->d_rmax,
@@ -562,8 +721,9 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
     g.parity = parity;
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    split_gemm_kernel<<<ggrid, GEMM_THREADS, SMEM_BYTES, st>>>(sp->tmPint, sp->tmP2, sp->tmRint, sp->tmR2, sp->d_uh,
-                                                               sp->d_ul, g);
+    auto kern = sp->clusters > 0 ? (sp->bn == 256 ? split_gemm_kernel<true, 256> : split_gemm_kernel<true, 128>)
+                                 : (sp->bn == 256 ? split_gemm_kernel<false, 256> : split_gemm_kernel<false, 128>);
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, sp->tm[0], sp->tm[1], sp->tm[2], sp->tm[3], sp->d_uh, sp->d_ul, g));
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
