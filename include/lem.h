@@ -175,6 +175,54 @@ lem_status lem_sync(lem_ctx* ctx);
 
 void lem_destroy(lem_ctx* ctx);
 
+/* ------------------------------------------------------------------ serving
+ * A server advances many independent LEM problems on one device with continuous batching:
+ * requests are admitted while their device memory fits the budget (otherwise they wait in
+ * the queue; they are not failed), every admitted request advances a few LEM steps at a time
+ * on the stream of its context, and requests that arrive while others run join between those
+ * chunks, so their work overlaps on the device. Problems with identical descriptors and
+ * precision share one context (one set of propagators), kept cached while the budget allows.
+ * The precision follows the tolerance tier: tol >= 1e-6 selects LEM_PREC_SPLIT when the
+ * problem is eligible for it, anything tighter (or an ineligible problem) LEM_PREC_FP64.
+ * The paper has no serving layer; Sec. 3's independent local problems are what makes the
+ * requests independent. A server is thread-safe. */
+typedef struct lem_server lem_server;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int64_t queued, active;       /* at the time of the call */
+  int64_t dof_steps;            /* owner nodes x LEM steps of completed requests */
+  double p50_ms, p99_ms;        /* submit-to-result latency of completed requests */
+  double first_admit_to_last_done_s;
+  int64_t device_bytes;         /* states, scratch and cached contexts held now */
+  int64_t ctx_hits, ctx_misses; /* context (propagator) cache */
+} lem_server_stats;
+
+/* Create a server on `device` with a device-memory budget in bytes (states, scratch and cached
+ * propagators; 0 = 80 GiB). Starts one worker thread. Errors: LEM_EINVAL, LEM_ECUDA. */
+lem_status lem_server_create(size_t hbm_budget_bytes, int device, lem_server** out);
+
+/* Queue a request to advance the host state h_state (FP64, row-major, in/out; it must stay
+ * valid and untouched until the request is done) by nsteps LEM steps of the problem `desc`
+ * (copied) within relative tolerance tier `tol`. Returns at once with a ticket.
+ * Errors: LEM_EINVAL (descriptor, nsteps < 0, NULL pointers), LEM_EBUSY (server stopping). */
+lem_status lem_submit(lem_server* srv, const lem_problem_desc* desc, double tol, double* h_state,
+                      int nsteps, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the result is back in h_state. Returns the request's error
+ * status if it failed (then *done = 1), LEM_EINVAL for an unknown ticket, else LEM_OK. */
+lem_status lem_poll(lem_server* srv, uint64_t ticket, int* done);
+
+/* Block until the request is done or `timeout_s` seconds pass (LEM_ETIMEOUT; the request
+ * keeps running). Returns the request's own status when done. */
+lem_status lem_wait(lem_server* srv, uint64_t ticket, double timeout_s);
+
+lem_status lem_server_get_stats(lem_server* srv, lem_server_stats* out);
+
+/* Stop the worker after the admitted requests finish (queued ones are failed with LEM_EBUSY),
+ * free everything. */
+void lem_server_destroy(lem_server* srv);
+
 const char* lem_status_str(lem_status s);
 const char* lem_last_error(void);
 

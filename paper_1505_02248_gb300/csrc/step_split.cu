@@ -65,7 +65,8 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
 enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3 };
 
 struct GemmParams {
-  int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx;
+  int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx, nty;
+  int nbx;              // window blocks per row of the tile grid
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of 128 windows
   int bsplit_y;         // clustered: a window block's two halves split along y (else x)
   const int* eP;        // per owner row: P scale exponent
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = g.Wy;
-  const int nbx = g.ntx / g.BNx;
+  const int nbx = g.nbx;
   const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
   const int mh = int(rank & 1u), nh = int(rank >> 1);  // MC: place in the 2 x 2 tile group
   const int unit0 = MC ? int(ptx::cluster_id_x()) : int(blockIdx.x);
@@ -455,11 +456,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // the same pointers, so the compiler would otherwise keep them in program order)
         int node[32];
         float a[32], al[32];
+        uint32_t inside = 0;  // windows of this batch that exist (blocks may overhang the grid)
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int n = q * 32 + i;
           const int ty = ty0 + n / g.BNx, tx = tx0 + n % g.BNx;
-          node[i] = (ty * g.Ty) * g.nx + tx * g.Tx + rowbase;
+          const bool in = ty < g.nty && tx < g.ntx;
+          inside |= uint32_t(in) << i;
+          node[i] = in ? (ty * g.Ty) * g.nx + tx * g.Tx + rowbase : rowbase;
           a[i] = uh[node[i]];
           al[i] = ul[node[i]];
         }
@@ -471,8 +475,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const ffv s = two_sum(a[i], y);
           const float lo = __fadd_rn(al[i], s.l);
           const float hi2 = __fadd_rn(s.h, lo);
-          uh[node[i]] = hi2;
-          ul[node[i]] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
+          if (inside >> i & 1u) {
+            uh[node[i]] = hi2;
+            ul[node[i]] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
+          }
         }
       }
       ptx::tc_fence_before();
@@ -494,7 +500,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 struct SplitPlan {
   int Ty = 0, Tx = 0, Hy = 0, Hx = 0, Wy = 0, Wx = 0, nty = 0, ntx = 0, M = 0, BNx = 0, BNy = 0;
   int pitch = 0, prow = 0, nsm = 0, bsplit_y = 0;
-  int bn = 128;      // windows per CTA tile (256 when the tile grid allows it)
+  int bn = 128;      // windows per CTA tile (256 for large tile grids)
+  int nbx = 0, nby = 0;  // window blocks per grid row / column (the last ones may overhang)
   int clusters = 0;  // > 0: the multicast (2 x 2 cluster) kernel runs with this many clusters
   ResParams rp{};
   float* d_uh = nullptr;
@@ -512,19 +519,14 @@ struct SplitPlan {
   int packed_gen = -1;
 };
 
-// Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn.
-static bool group_tiles(int64_t ntx, int64_t nty, int bn, int* bnx, int* bny) {
-  int x, y;
-  if (ntx >= bn) {
-    if (ntx % bn) return false;
-    x = bn; y = 1;
-  } else {
-    if (bn % ntx || nty % (bn / ntx)) return false;
-    x = int(ntx); y = bn / int(ntx);
-  }
-  if (bnx) *bnx = x;
-  if (bny) *bny = y;
-  return true;
+// Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn and
+// BNx a power of two no wider than the grid; blocks may overhang the grid at its right and
+// bottom edges (TMA zero-fills those windows and the epilogue skips them).
+static void group_tiles(int64_t ntx, int bn, int* bnx, int* bny) {
+  int x = 1;
+  while (x * 2 <= bn && x * 2 <= ntx) x *= 2;
+  *bnx = x;
+  *bny = bn / x;
 }
 
 bool split_eligible(const lem_ctx* ctx) {
@@ -540,14 +542,33 @@ bool split_eligible(const lem_ctx* ctx) {
   if (Wx > KB || Wx % 16 || Tx % 8) return false;
   if ((Ty * Tx) % BM) return false;
   if (ctx->ny <= d.overlap[0] + RT + 1 || ctx->nx <= Hx + RT + 1) return false;  // single-wrap staging
-  const int64_t ntx = ctx->nx / Tx, nty = ctx->ny / Ty;
-  return group_tiles(ntx, nty, 128, nullptr, nullptr);
+  return true;
+}
+
+// cuTensorMapEncodeTiled, resolved through the runtime so that liblem.so does not link
+// the driver library (it loads on machines without a GPU driver, e.g. for the host planner).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
 }
 
 static lem_status encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
                          const cuuint32_t* box, const char* what) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(LEM_ECUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, cuuint32_t(rank), base, dims, strides, box, es,
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, cuuint32_t(rank), base, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(LEM_ECUDA, std::string("cuTensorMapEncodeTiled failed for ") + what +
@@ -563,8 +584,11 @@ lem_status split_prepare(lem_ctx* ctx) {
   sp->Wy = sp->Ty + 2 * sp->Hy; sp->Wx = sp->Tx + 2 * sp->Hx;
   sp->nty = int(ctx->ny / sp->Ty); sp->ntx = int(ctx->nx / sp->Tx);
   sp->M = sp->Ty * sp->Tx;
-  sp->bn = group_tiles(sp->ntx, sp->nty, 256, &sp->BNx, &sp->BNy) ? 256 : 128;
-  if (sp->bn == 128) group_tiles(sp->ntx, sp->nty, 128, &sp->BNx, &sp->BNy);
+  // 256-wide tiles when they do not waste more than they save on mostly-empty edge blocks
+  sp->bn = int64_t(sp->ntx) * sp->nty >= 1024 ? 256 : 128;
+  group_tiles(sp->ntx, sp->bn, &sp->BNx, &sp->BNy);
+  sp->nbx = int((sp->ntx + sp->BNx - 1) / sp->BNx);
+  sp->nby = int((sp->nty + sp->BNy - 1) / sp->BNy);
   LEM_CUDA_TRY(cudaDeviceGetAttribute(&sp->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   // padded residual: rows ny + 2Hy, row pitch covers the last 64-wide window row read
   sp->prow = int(ctx->ny) + 2 * sp->Hy;
@@ -605,7 +629,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
   // Clustered (multicast) kernel when the tile grid splits into 2 x 2 groups and the device
   // can co-schedule clusters of 4 one-CTA-per-SM blocks.
-  const int nMB = sp->M / BM, nNB = int(ctx->tiles.size() / sp->bn);
+  const int nMB = sp->M / BM, nNB = sp->nbx * sp->nby;
   const bool bsplit_y = sp->BNy % 2 == 0;
   const bool mc_ok = nMB % 2 == 0 && nNB % 2 == 0 && (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) &&
                      std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
@@ -698,7 +722,8 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   GemmParams g{};
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx;
-  g.nMB = sp->M / BM; g.nNB = int(ctx->tiles.size() / sp->bn); g.bsplit_y = sp->bsplit_y;
+  g.nMB = sp->M / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
+  g.nty = sp->nty; g.nbx = sp->nbx;
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.err = sp->d_err;
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];

@@ -52,6 +52,15 @@ class Info(C.Structure):
     ]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+        ("queued", C.c_int64), ("active", C.c_int64), ("dof_steps", C.c_int64),
+        ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("first_admit_to_last_done_s", C.c_double),
+        ("device_bytes", C.c_int64), ("ctx_hits", C.c_int64), ("ctx_misses", C.c_int64),
+    ]
+
+
 _lib = None
 
 # (name, restype, argtypes) for every entry point of include/lem.h
@@ -71,6 +80,13 @@ SIGNATURES = [
     ("lem_get_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     ("lem_sync", C.c_int, [C.c_void_p]),
     ("lem_destroy", None, [C.c_void_p]),
+    ("lem_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    ("lem_submit", C.c_int, [C.c_void_p, C.POINTER(ProblemDesc), C.c_double, C.c_void_p, C.c_int,
+                             C.POINTER(C.c_uint64)]),
+    ("lem_poll", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]),
+    ("lem_wait", C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    ("lem_server_get_stats", C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    ("lem_server_destroy", None, [C.c_void_p]),
     ("lem_status_str", C.c_char_p, [C.c_int]),
     ("lem_last_error", C.c_char_p, []),
 ]
@@ -233,3 +249,54 @@ class Lem:
 
     def sync(self):
         check(self._lib.lem_sync(self._h), "lem_sync")
+
+
+class Server:
+    """lem_server: continuous batching of independent LEM requests on one device."""
+
+    def __init__(self, budget_bytes: int = 0, device: int = 0):
+        lib = load()
+        self._lib = lib
+        h = C.c_void_p()
+        check(lib.lem_server_create(C.c_size_t(int(budget_bytes)), int(device), C.byref(h)), "lem_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, shape, bc, coef, dt, tile, overlap, state: np.ndarray, nsteps: int, tol: float = 1e-6,
+               mode="phi", reaction=False, refresh=0) -> int:
+        """Queue `state` (float64, C-contiguous, updated in place when done); returns a ticket."""
+        assert state.dtype == np.float64 and state.flags.c_contiguous
+        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, "fp64", reaction, refresh)
+        t = C.c_uint64()
+        check(self._lib.lem_submit(self._h, C.byref(d), float(tol), state.ctypes.data_as(C.c_void_p), int(nsteps),
+                                   C.byref(t)), "lem_submit")
+        self._keep[t.value] = state  # the server writes into it until done
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        done = C.c_int()
+        check(self._lib.lem_poll(self._h, C.c_uint64(ticket), C.byref(done)), "lem_poll")
+        return bool(done.value)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        check(self._lib.lem_wait(self._h, C.c_uint64(ticket), float(timeout_s)), "lem_wait")
+
+    def status(self, ticket: int) -> int:
+        done = C.c_int()
+        return int(self._lib.lem_poll(self._h, C.c_uint64(ticket), C.byref(done)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(self._lib.lem_server_get_stats(self._h, C.byref(st)), "lem_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lem_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

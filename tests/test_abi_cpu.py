@@ -115,3 +115,12 @@ def test_constant_coefficient_classes(lib):
     q3 = L.plan_query((64, 64), ("dirichlet", "dirichlet"), W.stencil_vardiff_2d(kfield, 1.0),
                       1.0, (16, 16), (6, 6))
     assert q3["nclasses"] == q3["ntiles"] == 16  # variable coefficients: one class per tile
+
+
+def test_server_create_without_device_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = L.C.c_void_p()
+    st = lib.lem_server_create(0, 0, L.C.byref(h))
+    assert st in (L.LEM_ECUDA, L.LEM_EINVAL) and not h.value
