@@ -54,10 +54,23 @@ typedef enum {
 typedef enum { LEM_BC_DIRICHLET0 = 0, LEM_BC_PERIODIC = 1 } lem_bc;
 typedef enum { LEM_MODE_PHI = 0, LEM_MODE_EXP = 1 } lem_mode;
 /* LEM_PREC_FP64: propagators, residual and apply in IEEE binary64.
- * LEM_PREC_SPLIT: propagators built in FP64, stored as a scaled FP16 hi + FP16 lo pair and
- * applied on the tcgen05 tensor cores (three products, FP32 accumulation); the residual
- * and the state update run in float-float (about 48-bit) arithmetic. */
+ * LEM_PREC_SPLIT: propagators built in FP64, then applied in reduced precision with a
+ * stated error: when every window shares one propagator (2D periodic, constant
+ * coefficients, tile_y*tile_x a multiple of 128, tile_x a multiple of 8, window width a
+ * multiple of 16 up to 64) on the tcgen05 tensor cores -- P = P_int + P2 per row scale,
+ * r = r_int + r2 with one scale, the P_int r_int product exact in FP32, three correction
+ * products, float-float state and residual; otherwise (PHI mode) as FP32 propagators in a
+ * batched GEMV with float-float accumulation. EXP mode with LEM_PREC_SPLIT on a problem
+ * without a shared propagator runs the FP64 path. lem_get_info reports the path taken. */
 typedef enum { LEM_PREC_FP64 = 0, LEM_PREC_SPLIT = 1 } lem_prec;
+
+/* How lem_step applies the propagators (lem_info.apply_path). */
+typedef enum {
+  LEM_APPLY_FP64_GEMM = 0,   /* FP64, one gathered GEMM per class of tiles */
+  LEM_APPLY_FP64_GEMV = 1,   /* FP64, one batched GEMV over all tiles (many classes) */
+  LEM_APPLY_F32_GEMV = 2,    /* FP32 propagators, float-float accumulation */
+  LEM_APPLY_TC_SPLIT = 3     /* shared propagator on the tcgen05 tensor cores */
+} lem_apply_path;
 
 typedef struct {
   int ndim;               /* 1 or 2 */
@@ -89,6 +102,7 @@ typedef struct {
   int built;              /* 1 once propagators exist */
   int split_path;         /* 1 if lem_step runs the tcgen05 split-precision kernel */
   int64_t device_bytes;   /* device memory held by the context */
+  int apply_path;         /* lem_apply_path */
 } lem_info;
 
 /* Create a context on CUDA device `device`, enqueueing its work on `cuda_stream`

@@ -99,6 +99,7 @@ void free_ctx(lem_ctx* c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_class_order);
   cudaFree(c->d_P);
+  cudaFree(c->d_P32);
   cudaFree(c->d_r);
   cudaFree(c->d_U);
   cudaFree(c->d_Y);
@@ -200,15 +201,20 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   if (e == cudaSuccess) e = cudaMemcpy(c->d_class_order, c->class_order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "lem_create upload"); }
-  if (desc->prec == LEM_PREC_SPLIT) {
-    if (!split_eligible(c)) {
-      free_ctx(c);
-      return fail(LEM_EINVAL, "LEM_PREC_SPLIT needs a 2D periodic mesh with constant coefficients, "
-                              "LEM_MODE_PHI, tiles dividing the mesh, tile_y*tile_x a multiple of 128, "
-                              "tile_x a multiple of 8, window width tile_x + 2*overlap_x a multiple "
-                              "of 16 and at most 64, and a tile grid that groups into 128 windows");
-    }
+  // apply path: tensor-core split for a shared propagator, else a batched GEMV when tiles
+  // have (mostly) their own propagators or FP32 propagators are asked for, else grouped GEMMs
+  const bool many_classes = c->classes.size() * 8 > c->tiles.size();
+  if (desc->prec == LEM_PREC_SPLIT && split_eligible(c)) {
+    c->apply_path = LEM_APPLY_TC_SPLIT;
     s = split_prepare(c);
+    if (s != LEM_OK) { free_ctx(c); return s; }
+  } else if (desc->prec == LEM_PREC_SPLIT && desc->mode == LEM_MODE_PHI) {
+    c->apply_path = LEM_APPLY_F32_GEMV;
+  } else {
+    c->apply_path = many_classes ? LEM_APPLY_FP64_GEMV : LEM_APPLY_FP64_GEMM;
+  }
+  if (c->apply_path == LEM_APPLY_F32_GEMV || c->apply_path == LEM_APPLY_FP64_GEMV) {
+    s = gemv_set_smem(c);
     if (s != LEM_OK) { free_ctx(c); return s; }
   }
   *out = c;
@@ -233,7 +239,8 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
   for (int k = 0; k < nsteps; ++k) {
     if (ctx->desc.reaction && ctx->desc.refresh > 0 && ctx->steps_since_build >= ctx->desc.refresh)
       LEM_TRY(build_propagators(ctx, d_state));
-    LEM_TRY(step_fp64(ctx, d_state));
+    if (ctx->apply_path == LEM_APPLY_FP64_GEMM) LEM_TRY(step_fp64(ctx, d_state));
+    else LEM_TRY(step_gemv(ctx, d_state, ctx->apply_path == LEM_APPLY_F32_GEMV));
     ctx->steps_since_build++;
   }
   return LEM_OK;
@@ -286,6 +293,7 @@ lem_status lem_get_info(const lem_ctx* ctx, lem_info* out) {
   out->built = ctx->built ? 1 : 0;
   out->split_path = ctx->split ? 1 : 0;
   out->device_bytes = ctx->device_bytes;
+  out->apply_path = ctx->apply_path;
   return LEM_OK;
 }
 

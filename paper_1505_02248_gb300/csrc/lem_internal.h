@@ -82,6 +82,9 @@ struct lem_ctx {
   lem::TileDesc* d_tiles = nullptr;
   int32_t* d_class_order = nullptr;
   double* d_P = nullptr;               // nclasses * n_int * n_loc
+  float* d_P32 = nullptr;              // FP32 copy for the reduced-precision GEMV
+  int p32_gen = -1;                    // build_gen the FP32 copy was made from
+  int apply_path = 0;                  // lem_apply_path: how lem_step applies the propagators
   double* d_r = nullptr;               // npts (residual)
   double* d_U = nullptr;               // ntiles * n_loc (gathered windows)
   double* d_Y = nullptr;               // ntiles * n_int (local results)
@@ -106,6 +109,9 @@ lem_status make_plan(lem_ctx* ctx);
 lem_status build_propagators(lem_ctx* ctx, const double* d_state);
 // step_fp64.cu
 lem_status step_fp64(lem_ctx* ctx, double* d_u);
+// step_gemv.cu
+lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32);
+lem_status gemv_set_smem(lem_ctx* ctx);
 // step_split.cu
 lem_status split_prepare(lem_ctx* ctx);
 lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);

@@ -48,8 +48,11 @@ class Info(C.Structure):
     _fields_ = [
         ("ntiles", C.c_int64), ("nclasses", C.c_int64), ("n_loc", C.c_int64), ("n_int", C.c_int64),
         ("squarings_max", C.c_int), ("built", C.c_int), ("split_path", C.c_int),
-        ("device_bytes", C.c_int64),
+        ("device_bytes", C.c_int64), ("apply_path", C.c_int),
     ]
+
+
+APPLY_PATHS = {0: "fp64_gemm", 1: "fp64_gemv", 2: "f32_gemv", 3: "tc_split"}
 
 
 class ServerStats(C.Structure):

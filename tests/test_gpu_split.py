@@ -103,11 +103,19 @@ def test_split_full_size_100_steps():
     assert err <= TOL_SPLIT_100
 
 
-def test_split_rejects_ineligible_problems():
+def test_split_without_shared_propagator_uses_f32_gemv():
+    """1D heat has three propagator classes: LEM_PREC_SPLIT applies FP32 propagators with a
+    float-float GEMV there; 100 steps stay within the split bar of the oracle."""
     wl = W.heat1d()
-    with pytest.raises(L.LemError) as e:
-        L.Lem.from_workload(wl, prec="split")
-    assert e.value.status == L.LEM_EINVAL
+    X = assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    wins = decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
+    ctx = L.Lem.from_workload(wl, prec="split")
+    assert L.APPLY_PATHS[ctx.info()["apply_path"]] == "f32_gemv"
+    u = torch.tensor(wl["u0"], device="cuda")
+    ctx.step(u, 100)
+    ctx.sync()
+    from oracle import lem_run
+    assert rel_l2(u.cpu().numpy(), lem_run(X, wl["u0"], wins, 100)) <= TOL_SPLIT_100
 
 
 @pytest.fixture(scope="module")
