@@ -204,11 +204,12 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   // apply path: tensor-core split for a shared propagator, else a batched GEMV when tiles
   // have (mostly) their own propagators or FP32 propagators are asked for, else grouped GEMMs
   const bool many_classes = c->classes.size() * 8 > c->tiles.size();
-  if (desc->prec == LEM_PREC_SPLIT && split_eligible(c)) {
+  const bool split_tier = desc->prec == LEM_PREC_SPLIT || desc->prec == LEM_PREC_SPLIT_FAST;
+  if (split_tier && split_eligible(c)) {
     c->apply_path = LEM_APPLY_TC_SPLIT;
     s = split_prepare(c);
     if (s != LEM_OK) { free_ctx(c); return s; }
-  } else if (desc->prec == LEM_PREC_SPLIT && desc->mode == LEM_MODE_PHI) {
+  } else if (desc->prec == LEM_PREC_SPLIT_FAST && desc->mode == LEM_MODE_PHI) {
     c->apply_path = LEM_APPLY_F32_GEMV;
   } else {
     c->apply_path = many_classes ? LEM_APPLY_FP64_GEMV : LEM_APPLY_FP64_GEMM;

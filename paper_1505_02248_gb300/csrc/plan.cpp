@@ -25,7 +25,8 @@ lem_status validate(const lem_problem_desc* d) {
   for (int k = 0; k < ncoef; ++k)
     if (!d->coef[k]) return fail(LEM_EINVAL, "missing stencil coefficient pointer");
   if (d->mode != LEM_MODE_PHI && d->mode != LEM_MODE_EXP) return fail(LEM_EINVAL, "bad mode");
-  if (d->prec != LEM_PREC_FP64 && d->prec != LEM_PREC_SPLIT) return fail(LEM_EINVAL, "bad prec");
+  if (d->prec != LEM_PREC_FP64 && d->prec != LEM_PREC_SPLIT && d->prec != LEM_PREC_SPLIT_FAST)
+    return fail(LEM_EINVAL, "bad prec");
   if (d->reaction != 0 && d->reaction != 1) return fail(LEM_EINVAL, "reaction must be 0 or 1");
   if (d->reaction && d->mode != LEM_MODE_PHI) return fail(LEM_EINVAL, "the reaction needs LEM_MODE_PHI");
   if (d->refresh < 0) return fail(LEM_EINVAL, "refresh must be >= 0");

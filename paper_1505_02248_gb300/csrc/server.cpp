@@ -143,8 +143,8 @@ int64_t ctx_bytes_estimate(const lem_problem_desc& d) {
   if (lem_plan_query(&d, &nt, &nc, &nl, &ni, nullptr) != LEM_OK) return -1;
   const int64_t npts = d.ndim == 1 ? d.n[0] : d.n[0] * d.n[1];
   int64_t b = 8 * (nc * ni * nl + 2 * npts + nt * (nl + ni)) + 5 * 8 * (d.coef_stride ? npts : 1);
-  if (d.prec == LEM_PREC_SPLIT) b += 4 * 2 * npts + 2 * 2 * (npts + 8 * int64_t(std::sqrt(double(npts))) * 64) +
-                                     2 * 2 * ni * nl * 2;
+  if (d.prec == LEM_PREC_SPLIT) b += 4 * 2 * npts + 3 * 2 * (npts + 8 * int64_t(std::sqrt(double(npts))) * 64) +
+                                     3 * 2 * ni * nl * 2;
   // transient builder scratch (freed after the build): 19 n_loc^2 doubles per class batch
   const int64_t per = 19 * nl * nl * 8;
   const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nc, (int64_t(8) << 30) / std::max<int64_t>(per, 1)));

@@ -7,7 +7,8 @@
 //     power of two 2^er and written as two FP16 slices r*2^er = r_int + r2 into a
 //     ghost-padded [ny + 2Hy][pitch] array (the periodic halo is materialised here, so
 //     every window is a plain rectangle of it). r_int is an integer (|r_int| <= 2^rb),
-//     r2 the FP16-rounded remainder. er comes from the previous step's max|r|.
+//     r2 the FP16-rounded remainder (with three pieces, r3 the FP16-rounded remainder of
+//     that). er comes from the previous step's max|r|.
 //  2. split_gemm_kernel: Y = P R (M = Ty*Tx owner rows, N = tiles, K = window nodes).
 //     P is stored per row i as P*2^eP_i = P_int + P2 with |P_int| <= 2^9 an integer.
 //     Each K block is one window row (Wx = 16, 32, 48 or 64 nodes, loaded as 128-byte
@@ -47,17 +48,26 @@ constexpr int RING_BYTES = 192 * 1024;
 constexpr int SMEM_BYTES = RING_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;   // main + correction accumulators: 2 sets for BN = 128, 1 for 256
 
-// Tile shape: BN windows per CTA tile (TMEM columns per accumulator). BN = 256 halves the
-// shared-memory operand traffic per MMA (an N = 128 MMA reads its 8 KB of operands at the
-// full 128 B/clk shared-memory rate); it leaves room for one accumulator set and two stages.
-template <int BN>
+// Tile shape: BN windows per CTA tile (TMEM columns per accumulator), NP pieces of each
+// operand (2: P_int + P2 and r_int + r2, four products; 3: a third FP16 piece of each, six
+// products). BN = 256 halves the shared-memory operand traffic per MMA (an N = 128 MMA reads
+// its 8 KB of operands at the full 128 B/clk shared-memory rate); it leaves room for one
+// accumulator set and two stages of two pieces.
+template <int BN, int NP>
 struct Shape {
   static constexpr int B_BYTES = BN * KB * 2;                      // one residual slice of a stage
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // P_int, P2, r_int, r2
-  static constexpr int STAGES = RING_BYTES / STAGE_BYTES;           // 3 (BN 128) or 2 (BN 256)
+  static constexpr int STAGE_BYTES = NP * (A_BYTES + B_BYTES);      // P pieces, then r pieces
+  static constexpr int STAGES = RING_BYTES / STAGE_BYTES;           // 3 (BN 128, NP 2) or 2
   static constexpr int NBUF = BN == 256 ? 1 : 2;                    // TMEM accumulator sets
+  static_assert(STAGES >= 2, "at least two stages");
 };
-constexpr int EPI_WARPS = 4;             // one warp per TMEM lane quarter
+// Thread roles: warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 the epilogue (one per
+// TMEM lane quarter). With two pieces the epilogue reads the accumulators once per tile. With
+// three pieces (DRAIN) it also drains the correction accumulator into registers after every
+// window row: the tensor pipe's FP32 accumulation of the correction then spans only
+// 5 * ceil(Wx/16) MMAs, and the sum over window rows is a correctly rounded FP32 add. (Six
+// warps keep the 255-register limit: an SM sub-partition holds at most two of them.)
+constexpr int EPI_WARPS = 4;
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int P_INT_BITS = 9;            // |P_int| <= 2^9
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
@@ -66,6 +76,7 @@ enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3 
 
 struct GemmParams {
   int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx, nty;
+  int M;                // owner rows (Ty * Tx); M blocks past it are masked
   int nbx;              // window blocks per row of the tile grid
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of 128 windows
   int bsplit_y;         // clustered: a window block's two halves split along y (else x)
@@ -137,7 +148,8 @@ constexpr int RT = 32;  // residual output tile (padded coordinates), RT x RT pe
 __global__ void __launch_bounds__(256) residual_split_kernel(const float* __restrict__ uh,
                                                              const float* __restrict__ ul,
                                                              __half* __restrict__ Rint,
-                                                             __half* __restrict__ R2, ResParams p,
+                                                             __half* __restrict__ R2,
+                                                             __half* __restrict__ R3, ResParams p,
                                                              unsigned* rmax, int* escale, int parity,
                                                              int measure) {
   __shared__ float sh[RT + 2][RT + 3], sl[RT + 2][RT + 3];
@@ -191,15 +203,21 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
       ff_mac<false>(acc, p.c_hi[4], 0.0f, dN);
       if (p.csum_hi != 0.0f) ff_mac<false>(acc, p.csum_hi, 0.0f, ffv{ch, cl});
     }
-    const float r = __fadd_rn(acc.h, acc.l);
-    rabs = fmaxf(rabs, fabsf(r));
+    const ffv r = two_sum(acc.h, acc.l);  // normalised: |r.l| <= ulp(r.h) / 2
+    rabs = fmaxf(rabs, fabsf(r.h));
     if (measure) continue;
-    // r 2^er = r_int + r2 (r_int an integer; the remainder is exact in float)
-    const float rs = __fmul_rn(r, scale);
-    const __half hi = __float2half_rn(rintf(rs));
+    // r 2^er = r_int + r2 (+ r3), split from the float-float value: r_int an integer, the
+    // remainder t + l (t exact in float) rounded to FP16 twice. Three pieces carry about
+    // rb + 22 bits, more than one float holds, so the low word takes part.
+    const float rh = __fmul_rn(r.h, scale), rl = __fmul_rn(r.l, scale);  // exact (powers of two)
+    const float ri = rintf(rh);
+    const __half hi = __float2half_rn(ri);
     const int o = yp * p.pitch + xp;
     Rint[o] = hi;
-    R2[o] = __float2half_rn(__fsub_rn(rs, __half2float(hi)));
+    const float t = __fsub_rn(rh, __half2float(hi));  // exact (r_int may round in FP16 past 2048)
+    const __half h2 = __float2half_rn(__fadd_rn(t, rl));
+    R2[o] = h2;
+    if (R3) R3[o] = __float2half_rn(__fadd_rn(__fsub_rn(t, __half2float(h2)), rl));  // t - r2 exact
   }
   for (int o = 16; o > 0; o >>= 1) rabs = fmaxf(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = rabs;
@@ -228,11 +246,12 @@ __global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __re
 }
 
 // Per owner row i of P (FP64, n_int x n_loc, window row-major): eP_i with
-// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 in the [M][Wy*kpad]
+// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 (+ P3) in the [M][Wy*kpad]
 // K layout (each window row zero-padded to kpad), and S_i = sum_k |P_int[i,k]| (the
 // exactness bound of the main product).
 __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx, int kpad,
-                              __half* __restrict__ Pint, __half* __restrict__ P2, int* __restrict__ eP,
+                              __half* __restrict__ Pint, __half* __restrict__ P2, __half* __restrict__ P3,
+                              int* __restrict__ eP,
                               double* __restrict__ S) {
   const int i = blockIdx.x;
   if (i >= M) return;
@@ -259,6 +278,7 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
     const __half h2 = __double2half(x - xi);
     Pint[int64_t(i) * Wy * kpad + col] = hi;
     P2[int64_t(i) * Wy * kpad + col] = h2;
+    if (P3) P3[int64_t(i) * Wy * kpad + col] = __double2half(x - xi - double(__half2float(h2)));
     sum += fabs(xi);
   }
   red[threadIdx.x] = sum;
@@ -281,22 +301,29 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
 // only after all three CTAs that write into it (self, P partner, window partner) released it.
 // Two TMEM accumulator sets alternate between tiles, so the epilogue of one tile overlaps the
 // MMAs of the next.
-template <bool MC, int BN>
+template <bool MC, int BN, int NP>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmPint, const __grid_constant__ CUtensorMap tmP2,
-                      const __grid_constant__ CUtensorMap tmRint, const __grid_constant__ CUtensorMap tmR2,
+                      const __grid_constant__ CUtensorMap tmP3, const __grid_constant__ CUtensorMap tmRint,
+                      const __grid_constant__ CUtensorMap tmR2, const __grid_constant__ CUtensorMap tmR3,
                       float* __restrict__ uh, float* __restrict__ ul, GemmParams g) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  constexpr int STAGES = Shape<BN>::STAGES, STAGE_BYTES = Shape<BN>::STAGE_BYTES;
-  constexpr int B_BYTES = Shape<BN>::B_BYTES, NBUF = Shape<BN>::NBUF;
-  uint8_t* tiles = smem;  // [stage][P_int, P2 (A_BYTES each), r_int, r2 (B_BYTES each)], same offsets in every CTA
+  constexpr int STAGES = Shape<BN, NP>::STAGES, STAGE_BYTES = Shape<BN, NP>::STAGE_BYTES;
+  constexpr int B_BYTES = Shape<BN, NP>::B_BYTES, NBUF = Shape<BN, NP>::NBUF;
+  constexpr int R_OFF = NP * A_BYTES;  // r pieces follow the P pieces in a stage
+  // [stage][P_int, P2, (P3) (A_BYTES each), r_int, r2, (r3) (B_BYTES each)], same offsets in every CTA
+  uint8_t* tiles = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* full = bars;                 // [STAGES] stage loaded
   uint64_t* empty = bars + STAGES;       // [STAGES] stage released by every CTA writing into it
-  uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set ready
-  uint64_t* acce = accf + 2;             // [2] accumulator set drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  constexpr bool DRAIN = NP == 3;
+  static_assert(!DRAIN || BN == 128, "drained correction: main[2] + corr[2] of 128 columns fill TMEM");
+  uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set (main) ready
+  uint64_t* acce = accf + 2;             // [2] accumulator set (main) drained
+  uint64_t* cf = acce + 2;               // DRAIN: [2] correction of one window row ready
+  uint64_t* ce = cf + 2;                 // DRAIN: [2] correction drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ce + 2);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -324,10 +351,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (threadIdx.x == 0) {
     s_abort = 0;
     for (int s = 0; s < STAGES; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], MC ? 3 : 1); }
-    for (int b = 0; b < 2; ++b) { ptx::mbar_init(&accf[b], 1); ptx::mbar_init(&acce[b], EPI_WARPS); }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&accf[b], 1);
+      ptx::mbar_init(&acce[b], EPI_WARPS);
+      ptx::mbar_init(&cf[b], 1);
+      ptx::mbar_init(&ce[b], EPI_WARPS);
+    }
     ptx::fence_barrier_init();
     ptx::tma_prefetch_desc(&tmPint); ptx::tma_prefetch_desc(&tmP2);
     ptx::tma_prefetch_desc(&tmRint); ptx::tma_prefetch_desc(&tmR2);
+    if (NP == 3) { ptx::tma_prefetch_desc(&tmP3); ptx::tma_prefetch_desc(&tmR3); }
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
     if (blockIdx.x == 0) g.rmax[g.parity] = 0u;
@@ -363,18 +396,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (MC) {
             // my half of the P rows (to me and the P partner), my half of the windows (to me
             // and the window partner); the partners send the other halves
-            ptx::tma_load_2d_mc(st + mh * (A_BYTES / 2), &tmPint, &full[s], kb * KB, m0 + mh * (BM / 2), maskP);
-            ptx::tma_load_2d_mc(st + A_BYTES + mh * (A_BYTES / 2), &tmP2, &full[s], kb * KB, m0 + mh * (BM / 2),
-                                maskP);
+            const CUtensorMap* tp[3] = {&tmPint, &tmP2, &tmP3};
+            const CUtensorMap* tr[3] = {&tmRint, &tmR2, &tmR3};
             const int wx = g.bsplit_y ? tx0 : tx0 + nh * (g.BNx / 2);
             const int wy = g.bsplit_y ? ty0 + nh * (g.BNy / 2) : ty0;
-            ptx::tma_load_4d_mc(st + 2 * A_BYTES + nh * (B_BYTES / 2), &tmRint, &full[s], 0, wx, kb, wy, maskR);
-            ptx::tma_load_4d_mc(st + 2 * A_BYTES + B_BYTES + nh * (B_BYTES / 2), &tmR2, &full[s], 0, wx, kb, wy, maskR);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              ptx::tma_load_2d_mc(st + q * A_BYTES + mh * (A_BYTES / 2), tp[q], &full[s], kb * KB,
+                                  m0 + mh * (BM / 2), maskP);
+              ptx::tma_load_4d_mc(st + R_OFF + q * B_BYTES + nh * (B_BYTES / 2), tr[q], &full[s], 0, wx, kb, wy,
+                                  maskR);
+            }
           } else {
-            ptx::tma_load_2d(st, &tmPint, &full[s], kb * KB, m0);
-            ptx::tma_load_2d(st + A_BYTES, &tmP2, &full[s], kb * KB, m0);
-            ptx::tma_load_4d(st + 2 * A_BYTES, &tmRint, &full[s], 0, tx0, kb, ty0);
-            ptx::tma_load_4d(st + 2 * A_BYTES + B_BYTES, &tmR2, &full[s], 0, tx0, kb, ty0);
+            const CUtensorMap* tp[3] = {&tmPint, &tmP2, &tmP3};
+            const CUtensorMap* tr[3] = {&tmRint, &tmR2, &tmR3};
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+              ptx::tma_load_2d(st + q * A_BYTES, tp[q], &full[s], kb * KB, m0);
+              ptx::tma_load_4d(st + R_OFF + q * B_BYTES, tr[q], &full[s], 0, tx0, kb, ty0);
+            }
           }
           issued = it + 1;
         }
@@ -385,36 +425,55 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // TMEM columns: without DRAIN, set b = [main | corr] at b * 2BN; with DRAIN, main b at
+    // b * BN and the two correction buffers at 2BN and 3BN.
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
       bool ok = true;
-      int it = 0, lt = 0;
+      int it = 0, lt = 0, kc = 0;
       for (int u = unit0; u < nunits && ok; u += nunit_step, ++lt) {
         const int b = lt % NBUF;
         if (lt >= NBUF) {
           if (!ptx::mbar_wait(&acce[b], ((lt / NBUF) - 1) & 1, WAIT_NS)) { ok = false; break; }
           ptx::tc_fence_after();
         }
-        const uint32_t main = tmem + b * 2 * BN, corr = main + BN;
+        const uint32_t main = DRAIN ? tmem + b * BN : tmem + b * 2 * BN;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, WAIT_NS)) { ok = false; break; }
+          uint32_t corr = main + BN;
+          if (DRAIN) {
+            const int j = kc & 1;
+            if (kc >= 2 && !ptx::mbar_wait(&ce[j], ((kc >> 1) - 1) & 1, WAIT_NS)) { ok = false; break; }
+            corr = tmem + (2 + j) * BN;
+          }
           ptx::tc_fence_after();
           const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
           const uint64_t dPi = ptx::sw128_kmajor_desc(base);
           const uint64_t dP2 = ptx::sw128_kmajor_desc(base + A_BYTES);
-          const uint64_t dRi = ptx::sw128_kmajor_desc(base + 2 * A_BYTES);
-          const uint64_t dR2 = ptx::sw128_kmajor_desc(base + 2 * A_BYTES + B_BYTES);
-          for (int kk = 0; kk < g.Wx / 16; ++kk) {
+          const uint64_t dRi = ptx::sw128_kmajor_desc(base + R_OFF);
+          const uint64_t dR2 = ptx::sw128_kmajor_desc(base + R_OFF + B_BYTES);
+          const uint64_t dP3 = ptx::sw128_kmajor_desc(base + 2 * A_BYTES);       // NP == 3 only
+          const uint64_t dR3 = ptx::sw128_kmajor_desc(base + R_OFF + 2 * B_BYTES);  // NP == 3 only
+          // ceil(Wx / 16) K steps: P is zero beyond Wx in each padded window row
+          for (int kk = 0; kk < (g.Wx + 15) / 16; ++kk) {
             const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            // DRAIN: each window row starts a fresh correction sum
+            const uint32_t cacc = DRAIN ? (kk > 0 ? 1u : 0u) : acc;
             ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
-            ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, acc);
+            ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, cacc);
             ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
             ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
+            if (NP == 3) {
+              ptx::mma_f16(corr, dPi + adv, dR3 + adv, idesc, 1u);
+              ptx::mma_f16(corr, dP3 + adv, dRi + adv, idesc, 1u);
+            }
           }
           if (MC) ptx::mma_commit_mc(&empty[s], maskE);
           else ptx::mma_commit(&empty[s]);
+          if (DRAIN) ptx::mma_commit(&cf[kc & 1]);
+          ++kc;
         }
         if (ok) ptx::mma_commit(&accf[b]);
       }
@@ -429,48 +488,72 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue (4 warps)
-    const int lane_base = 32 * (warp & 3);
-    const int row = lane_base + lane;  // TMEM lane = owner row within the M block
-    int lt = 0;
+    // ------------------------------------------------------------ epilogue
+    const int lane_base = 32 * (warp & 3);  // tcgen05.ld: a warp reaches lane quarter warp % 4
+    const int row = lane_base + lane;       // TMEM lane = owner row within the M block
+    int lt = 0, kc = 0;
     for (int u = unit0; u < nunits; u += nunit_step, ++lt) {
       const int b = lt % NBUF;
+      float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over window rows
+      if constexpr (DRAIN) {
+#pragma unroll
+        for (int i = 0; i < BN; ++i) cs[i] = 0.0f;
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++kc) {
+          const int j = kc & 1;
+          if (s_abort || !ptx::mbar_wait(&cf[j], (kc >> 1) & 1, WAIT_NS)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t tc = tmem + (uint32_t(lane_base) << 16) + uint32_t((2 + j) * BN);
+#pragma unroll
+          for (int h = 0; h < BN / 32; ++h) {
+            uint32_t r[32];
+            ptx::tmem_ld_32x32b_x32_nowait(tc + h * 32, r);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) cs[h * 32 + i] = __fadd_rn(cs[h * 32 + i], __uint_as_float(r[i]));
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&ce[j]);
+        }
+        if (!ok) {
+          atomicExch(g.err, ERR_TIMEOUT_EPI);
+          break;
+        }
+      }
       if (!ptx::mbar_wait(&accf[b], (lt / NBUF) & 1, WAIT_NS)) {
         atomicExch(g.err, ERR_TIMEOUT_EPI);
         break;
       }
       ptx::tc_fence_after();
-      const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(b * 2 * BN);
+      const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(DRAIN ? b * BN : b * 2 * BN);
       int m0, tx0, ty0;
       tile_of(u, m0, tx0, ty0);
       const int ii = m0 + row;
-      const float oscale = pow2f(-(g.eP[ii] + g.escale[g.parity]));
-      const int iy = ii / g.Tx, ix = ii % g.Tx;
+      const bool row_in = ii < g.M;  // the last M block may extend past the owner rows
+      const float oscale = pow2f(-((row_in ? g.eP[ii] : 0) + g.escale[g.parity]));
+      const int iy = row_in ? ii / g.Tx : 0, ix = row_in ? ii % g.Tx : 0;
       const int rowbase = iy * g.nx + ix;
-#pragma unroll 1
-      for (int q = 0; q < BN / 32; ++q) {
-        uint32_t vm[32], vc[32];
-        ptx::tmem_ld_32x32b_x32_nowait(t_lane + q * 32, vm);
-        ptx::tmem_ld_32x32b_x32_nowait(t_lane + BN + q * 32, vc);
-        // all 64 state loads of this batch go out before any store (the stores go through
+      // one batch of 16 windows: y = (main + corr) 2^-(eP_i + er) added into the owner nodes
+      auto batch = [&](int q, const float (&vm)[16], const float (&vc)[16]) {
+        // all 32 state loads of this batch go out before any store (the stores go through
         // the same pointers, so the compiler would otherwise keep them in program order)
-        int node[32];
-        float a[32], al[32];
+        int node[16];
+        float a[16], al[16];
         uint32_t inside = 0;  // windows of this batch that exist (blocks may overhang the grid)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int n = q * 32 + i;
+        for (int i = 0; i < 16; ++i) {
+          const int n = q * 16 + i;
           const int ty = ty0 + n / g.BNx, tx = tx0 + n % g.BNx;
-          const bool in = ty < g.nty && tx < g.ntx;
+          const bool in = row_in && ty < g.nty && tx < g.ntx;
           inside |= uint32_t(in) << i;
           node[i] = in ? (ty * g.Ty) * g.nx + tx * g.Tx + rowbase : rowbase;
           a[i] = uh[node[i]];
           al[i] = ul[node[i]];
         }
-        ptx::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float y = __fmul_rn(__fadd_rn(__uint_as_float(vm[i]), __uint_as_float(vc[i])), oscale);
+        for (int i = 0; i < 16; ++i) {
+          const float y = __fmul_rn(__fadd_rn(vm[i], vc[i]), oscale);
           // (u_hi, u_lo) += y in float-float
           const ffv s = two_sum(a[i], y);
           const float lo = __fadd_rn(al[i], s.l);
@@ -479,6 +562,34 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             uh[node[i]] = hi2;
             ul[node[i]] = __fsub_rn(lo, __fsub_rn(hi2, s.h));
           }
+        }
+      };
+      if constexpr (DRAIN) {
+        // fold the correction into the main accumulator (main + corr in FP32, as without the
+        // drain), so the scatter below holds no correction registers
+#pragma unroll
+        for (int q = 0; q < BN / 16; ++q) {  // unrolled: cs is indexed statically
+          float vm[16];
+          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
+          ptx::tmem_st_32x32b_x16(t_lane + q * 16, vm);
+        }
+        ptx::tmem_wait_st();
+        const float zero[16] = {};
+#pragma unroll 1
+        for (int q = 0; q < BN / 16; ++q) {
+          float vm[16];
+          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+          batch(q, vm, zero);
+        }
+      } else {
+#pragma unroll 1
+        for (int q = 0; q < BN / 16; ++q) {
+          float vm[16], vc[16];
+          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+          ptx::tmem_ld_32x32b_x16(t_lane + BN + q * 16, vc);
+          batch(q, vm, vc);
         }
       }
       ptx::tc_fence_before();
@@ -495,12 +606,26 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (MC) ptx::cluster_sync();  // no CTA leaves while a partner may still signal it
 }
 
+using GemmKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, float*,
+                           float*, GemmParams);
+
+// The instantiated (cluster, tile width, pieces) combinations: BN 256 with two pieces for
+// large tile grids, BN 128 otherwise.
+int gemm_threads(int) { return GEMM_THREADS; }
+
+GemmKernel gemm_kernel_for(bool mc, int bn, int np) {
+  if (np == 3) return mc ? split_gemm_kernel<true, 128, 3> : split_gemm_kernel<false, 128, 3>;
+  if (bn == 256) return mc ? split_gemm_kernel<true, 256, 2> : split_gemm_kernel<false, 256, 2>;
+  return mc ? split_gemm_kernel<true, 128, 2> : split_gemm_kernel<false, 128, 2>;
+}
+
 }  // namespace
 
 struct SplitPlan {
   int Ty = 0, Tx = 0, Hy = 0, Hx = 0, Wy = 0, Wx = 0, nty = 0, ntx = 0, M = 0, BNx = 0, BNy = 0;
   int pitch = 0, prow = 0, nsm = 0, bsplit_y = 0;
-  int bn = 128;      // windows per CTA tile (256 for large tile grids)
+  int np = 2;        // FP16 pieces per operand: 2 (four products) or 3 (six products)
+  int bn = 128;      // windows per CTA tile (256 for large tile grids with two pieces)
   int nbx = 0, nby = 0;  // window blocks per grid row / column (the last ones may overhang)
   int clusters = 0;  // > 0: the multicast (2 x 2 cluster) kernel runs with this many clusters
   ResParams rp{};
@@ -508,14 +633,16 @@ struct SplitPlan {
   float* d_ul = nullptr;
   __half* d_Rint = nullptr;
   __half* d_R2 = nullptr;
+  __half* d_R3 = nullptr;
   __half* d_Pint = nullptr;
   __half* d_P2 = nullptr;
+  __half* d_P3 = nullptr;
   int* d_eP = nullptr;
   double* d_S = nullptr;
   unsigned* d_rmax = nullptr;
   int* d_escale = nullptr;
   int* d_err = nullptr;
-  CUtensorMap tm[4];  // P_int, P2, r_int, r2 (half boxes when clustered)
+  CUtensorMap tm[6];  // P_int, P2, P3, r_int, r2, r3 (half boxes when clustered; pieces 3 unused with np = 2)
   int packed_gen = -1;
 };
 
@@ -539,8 +666,7 @@ bool split_eligible(const lem_ctx* ctx) {
   const ClassDesc& c = ctx->classes[0];
   if (c.whole[0] || c.whole[1]) return false;
   const int Wx = Tx + 2 * Hx;
-  if (Wx > KB || Wx % 16 || Tx % 8) return false;
-  if ((Ty * Tx) % BM) return false;
+  if (Wx > KB || Tx % 8) return false;  // TMA: a window row fits one 128-byte row; 16-byte strides
   if (ctx->ny <= d.overlap[0] + RT + 1 || ctx->nx <= Hx + RT + 1) return false;  // single-wrap staging
   return true;
 }
@@ -584,8 +710,10 @@ lem_status split_prepare(lem_ctx* ctx) {
   sp->Wy = sp->Ty + 2 * sp->Hy; sp->Wx = sp->Tx + 2 * sp->Hx;
   sp->nty = int(ctx->ny / sp->Ty); sp->ntx = int(ctx->nx / sp->Tx);
   sp->M = sp->Ty * sp->Tx;
+  sp->np = d.prec == LEM_PREC_SPLIT_FAST ? 2 : 3;
   // 256-wide tiles when they do not waste more than they save on mostly-empty edge blocks
-  sp->bn = int64_t(sp->ntx) * sp->nty >= 1024 ? 256 : 128;
+  // (two pieces only: a stage of three 256-wide pieces leaves room for one stage)
+  sp->bn = sp->np == 2 && int64_t(sp->ntx) * sp->nty >= 1024 ? 256 : 128;
   group_tiles(sp->ntx, sp->bn, &sp->BNx, &sp->BNy);
   sp->nbx = int((sp->ntx + sp->BNx - 1) / sp->BNx);
   sp->nby = int((sp->nty + sp->BNy - 1) / sp->BNy);
@@ -612,32 +740,42 @@ lem_status split_prepare(lem_ctx* ctx) {
   sp->rp.rb = 10;  // set from the packed propagator in split_pack
   const size_t npts = size_t(ctx->npts);
   const size_t rbytes = sizeof(__half) * size_t(sp->prow) * sp->pitch;
-  const size_t pbytes = sizeof(__half) * size_t(sp->M) * sp->Wy * KB;
+  // P slices padded to whole 128-row M blocks (zero rows past Ty*Tx)
+  const int Mpad = (sp->M + BM - 1) / BM * BM;
+  const size_t pbytes = sizeof(__half) * size_t(Mpad) * sp->Wy * KB;
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_uh), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_ul), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Rint), rbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R2), rbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Pint), pbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P2), pbytes));
+  if (sp->np == 3) {
+    LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R3), rbytes));
+    LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P3), pbytes));
+    LEM_CUDA_TRY(cudaMemset(sp->d_R3, 0, rbytes));
+    LEM_CUDA_TRY(cudaMemset(sp->d_P3, 0, pbytes));
+  }
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_eP), sizeof(int) * sp->M));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_S), sizeof(double) * sp->M));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_rmax), sizeof(unsigned) * 2));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_escale), sizeof(int) * 2));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_err), sizeof(int)));
+  LEM_CUDA_TRY(cudaMemset(sp->d_Pint, 0, pbytes));
+  LEM_CUDA_TRY(cudaMemset(sp->d_P2, 0, pbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_R2, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
   // Clustered (multicast) kernel when the tile grid splits into 2 x 2 groups and the device
   // can co-schedule clusters of 4 one-CTA-per-SM blocks.
-  const int nMB = sp->M / BM, nNB = sp->nbx * sp->nby;
+  const int nMB = (sp->M + BM - 1) / BM, nNB = sp->nbx * sp->nby;
   const bool bsplit_y = sp->BNy % 2 == 0;
   const bool mc_ok = nMB % 2 == 0 && nNB % 2 == 0 && (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) &&
                      std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
   sp->bsplit_y = bsplit_y ? 1 : 0;
-  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  LEM_CUDA_TRY(cudaFuncSetAttribute(split_gemm_kernel<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(false, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(true, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES));
   sp->clusters = 0;
   if (mc_ok) {
     cudaLaunchConfig_t cfg{};
@@ -645,13 +783,12 @@ lem_status split_prepare(lem_ctx* ctx) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 4; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(4 * ((nMB / 2) * (nNB / 2)));
-    cfg.blockDim = dim3(GEMM_THREADS);
+    cfg.blockDim = dim3(gemm_threads(sp->np));
     cfg.dynamicSmemBytes = SMEM_BYTES;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclus = 0;
-    cudaError_t e = sp->bn == 256 ? cudaOccupancyMaxActiveClusters(&nclus, split_gemm_kernel<true, 256>, &cfg)
-                                  : cudaOccupancyMaxActiveClusters(&nclus, split_gemm_kernel<true, 128>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclus, gemm_kernel_for(true, sp->bn, sp->np), &cfg);
     if (e == cudaSuccess && nclus > 0) sp->clusters = std::min(nclus, (nMB / 2) * (nNB / 2));
     cudaGetLastError();
   }
@@ -659,9 +796,10 @@ lem_status split_prepare(lem_ctx* ctx) {
   // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx]
   {
     const bool mc = sp->clusters > 0;
-    __half* pbase[2] = {sp->d_Pint, sp->d_P2};
-    __half* rbase[2] = {sp->d_Rint, sp->d_R2};
-    cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(sp->M)};
+    // with two pieces the third maps alias the second (never loaded)
+    __half* pbase[3] = {sp->d_Pint, sp->d_P2, sp->np == 3 ? sp->d_P3 : sp->d_P2};
+    __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
+    cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(Mpad)};
     cuuint64_t ps[1] = {cuuint64_t(sp->Wy) * KB * 2};
     cuuint32_t pbox[2] = {KB, cuuint32_t(mc ? BM / 2 : BM)};
     cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
@@ -671,15 +809,15 @@ lem_status split_prepare(lem_ctx* ctx) {
       if (bsplit_y) rbox[3] /= 2;
       else rbox[1] /= 2;
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
       LEM_TRY(encode(&sp->tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
-      LEM_TRY(encode(&sp->tm[2 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
+      LEM_TRY(encode(&sp->tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
     }
   }
   cudaFuncAttributes fa{};
-  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, split_gemm_kernel<false, 256>));
-  if (fa.maxThreadsPerBlock < GEMM_THREADS)
-    return fail(LEM_ECUDA, "split GEMM kernel cannot launch " + std::to_string(GEMM_THREADS) + " threads (" +
+  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(false, sp->bn, sp->np)));
+  if (fa.maxThreadsPerBlock < gemm_threads(sp->np))
+    return fail(LEM_ECUDA, "split GEMM kernel cannot launch " + std::to_string(gemm_threads(sp->np)) + " threads (" +
                                std::to_string(fa.numRegs) + " registers per thread)");
   return LEM_OK;
 }
@@ -690,7 +828,7 @@ static lem_status split_pack(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
   pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->d_Pint, sp->d_P2,
-                                       sp->d_eP, sp->d_S);
+                                       sp->d_P3, sp->d_eP, sp->d_S);
   LEM_CUDA_TRY(cudaGetLastError());
   std::vector<double> S(sp->M);
   LEM_CUDA_TRY(cudaMemcpyAsync(S.data(), sp->d_S, sizeof(double) * sp->M, cudaMemcpyDeviceToHost, st));
@@ -698,7 +836,8 @@ static lem_status split_pack(lem_ctx* ctx) {
   double smax = 1.0;
   for (double v : S) smax = std::max(smax, v);
   int rb = 0;
-  while (std::ldexp(smax, rb + 1) < 16777216.0 && rb < 14) ++rb;
+  // rb <= 12: the target |r_int| <= 2^11 is an integer FP16 holds exactly
+  while (std::ldexp(smax, rb + 1) < 16777216.0 && rb < 12) ++rb;
   if (rb < 4) return fail(LEM_ENUMERIC, "split path: propagator rows too heavy for an exact integer product");
   sp->rp.rb = rb;
   sp->packed_gen = ctx->build_gen;
@@ -716,18 +855,19 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   // to form a scale it never uses)
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
   const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + RT - 1) / RT, (sp->prow + RT - 1) / RT);
-  residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->rp, sp->d_rmax,
-                                               sp->d_escale, 1, 1);
+  residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
+                                               sp->d_rmax, sp->d_escale, 1, 1);
   LEM_CUDA_TRY(cudaGetLastError());
   GemmParams g{};
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx;
-  g.nMB = sp->M / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
+  g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
+  g.M = sp->M;
   g.nty = sp->nty; g.nbx = sp->nbx;
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.err = sp->d_err;
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(GEMM_THREADS);
+  cfg.blockDim = dim3(gemm_threads(sp->np));
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
   if (sp->clusters > 0) {
@@ -741,14 +881,13 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   }
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
-    residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->rp, sp->d_rmax,
-                                                 sp->d_escale, parity, 0);
+    residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
+                                                 sp->d_rmax, sp->d_escale, parity, 0);
     g.parity = parity;
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    auto kern = sp->clusters > 0 ? (sp->bn == 256 ? split_gemm_kernel<true, 256> : split_gemm_kernel<true, 128>)
-                                 : (sp->bn == 256 ? split_gemm_kernel<false, 256> : split_gemm_kernel<false, 128>);
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, sp->tm[0], sp->tm[1], sp->tm[2], sp->tm[3], sp->d_uh, sp->d_ul, g));
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->clusters > 0, sp->bn, sp->np), sp->tm[0], sp->tm[1],
+                                    sp->tm[2], sp->tm[3], sp->tm[4], sp->tm[5], sp->d_uh, sp->d_ul, g));
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
@@ -773,6 +912,7 @@ void split_destroy(lem_ctx* ctx) {
   if (!sp) return;
   cudaFree(sp->d_uh); cudaFree(sp->d_ul); cudaFree(sp->d_Rint); cudaFree(sp->d_R2);
   cudaFree(sp->d_Pint); cudaFree(sp->d_P2); cudaFree(sp->d_eP); cudaFree(sp->d_S);
+  cudaFree(sp->d_P3); cudaFree(sp->d_R3);
   cudaFree(sp->d_rmax); cudaFree(sp->d_escale); cudaFree(sp->d_err);
   delete sp;
   ctx->split = nullptr;

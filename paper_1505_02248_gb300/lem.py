@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "liblem.so")
 LEM_OK, LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA, LEM_EBUSY, LEM_ENOTREADY, LEM_ETIMEOUT, LEM_ENUMERIC = range(8)
 BC = {"dirichlet": 0, "periodic": 1}
 MODE = {"phi": 0, "exp": 1}
-PREC = {"fp64": 0, "split": 1}
+PREC = {"fp64": 0, "split": 1, "split_fast": 2}
 
 
 class LemError(RuntimeError):
@@ -83,6 +83,11 @@ SIGNATURES = [
     ("lem_get_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     ("lem_sync", C.c_int, [C.c_void_p]),
     ("lem_destroy", None, [C.c_void_p]),
+    ("lem_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
+                                   C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("lem_batch_run", C.c_int, [C.c_void_p, C.c_int]),
+    ("lem_batch_schedule", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("lem_batch_destroy", None, [C.c_void_p]),
     ("lem_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     ("lem_submit", C.c_int, [C.c_void_p, C.POINTER(ProblemDesc), C.c_double, C.c_void_p, C.c_int,
                              C.POINTER(C.c_uint64)]),
@@ -296,6 +301,45 @@ class Server:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.lem_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """lem_batch: one CUDA graph advancing many contexts' device states together."""
+
+    def __init__(self, ctxs, states, steps_per_launch: int = 1, lanes: int = 8, stream=None):
+        lib = load()
+        self._lib = lib
+        n = len(ctxs)
+        self._ctxs = list(ctxs)
+        self._states = list(states)  # keep the captured tensors alive
+        hc = (C.c_void_p * n)(*[c._h.value for c in ctxs])
+        hs = (C.c_void_p * n)(*[s.data_ptr() for s in states])
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream is not None else None
+        check(lib.lem_batch_create(hc, hs, n, int(steps_per_launch), int(lanes), st, C.byref(h)), "lem_batch_create")
+        self._h = h
+        self.n = n
+
+    def run(self, launches: int = 1):
+        check(self._lib.lem_batch_run(self._h, int(launches)), "lem_batch_run")
+
+    def schedule(self):
+        est = np.zeros(self.n)
+        lane = np.zeros(self.n, dtype=np.int32)
+        check(self._lib.lem_batch_schedule(self._h, est.ctypes.data_as(C.c_void_p), lane.ctypes.data_as(C.c_void_p)),
+              "lem_batch_schedule")
+        return est, lane
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lem_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -130,3 +130,22 @@ def vardiff2d(side: int = 1024, tile: int = 16, overlap: int = 6, ell_k: float =
     return dict(name=f"vardiff2d_{side}", shape=(side, side), bc=("dirichlet", "dirichlet"),
                 coef=stencil_vardiff_2d(k, h), dt=dt, tile=(tile, tile),
                 overlap=(overlap, overlap), u0=u0.ravel(), reaction=True)
+
+
+def batch_problems(n: int = 512, seed: int = 3, side_max: int = 512) -> list:
+    """Independent periodic 2D advection-diffusion problems of uneven size: side = 32 *
+    U{2..side_max/32}, mu = nu dt / h^2 ~ U[1, 50], tile in {8, 16, 32}, overlap ~ U{4..8},
+    C_x ~ U[0, 4] with C_y = C_x / 2 (h = 1, dt = 1), u0 = GRF(8)."""
+    g = rng(seed)
+    out = []
+    for i in range(n):
+        side = 32 * int(g.integers(2, side_max // 32 + 1))
+        mu = float(g.uniform(1.0, 50.0))
+        cx = float(g.uniform(0.0, 4.0))
+        tile = int(g.choice([8, 16, 32]))
+        H = int(g.integers(4, 9))
+        coef = stencil_advdiff_2d(mu, cx, cx / 2, 1.0)
+        u0 = grf_2d((side, side), 8.0, seed * 100000 + i).ravel()
+        out.append(dict(name=f"batch{i}_{side}_t{tile}_H{H}", shape=(side, side), bc=("periodic", "periodic"),
+                        coef=coef, dt=1.0, tile=(tile, tile), overlap=(H, H), u0=u0, reaction=False))
+    return out

@@ -1,5 +1,7 @@
-"""GPU parity of the split-precision tensor-core LEM path (FP16 hi/lo propagator and
-residual, tcgen05 MMA with FP32 accumulation, float-float state) against the FP64 oracle.
+"""GPU parity of the split-precision tensor-core LEM path (FP16 pieces of the propagator and
+the residual, tcgen05 MMA with FP32 accumulation, float-float state) against the FP64 oracle.
+Two tiers: "split" (three pieces per operand, six products) and "split_fast" (two pieces,
+four products).
 
 Bar (stated for the mixed-precision path): within 1e-6 relative L2 of the FP64 oracle LEM
 after 100 steps. At 2048^2 the 100-step reference is the FP64 GPU path, itself pinned to the
@@ -44,21 +46,23 @@ def case512():
     return wl, ref
 
 
-def test_split_is_eligible_and_uses_tensor_path(case512):
+@pytest.mark.parametrize("prec", ["split", "split_fast"])
+def test_split_is_eligible_and_uses_tensor_path(case512, prec):
     wl, _ = case512
-    ctx = L.Lem.from_workload(wl, prec="split")
+    ctx = L.Lem.from_workload(wl, prec=prec)
     assert ctx.info()["split_path"] == 1
 
 
+@pytest.mark.parametrize("prec", ["split", "split_fast"])
 @pytest.mark.parametrize("steps", [1, 10, 100])
-def test_split_512_vs_oracle(case512, steps):
+def test_split_512_vs_oracle(case512, steps, prec):
     wl, ref = case512
-    ctx = L.Lem.from_workload(wl, prec="split")
+    ctx = L.Lem.from_workload(wl, prec=prec)
     u = torch.tensor(wl["u0"], device="cuda")
     ctx.step(u, steps)
     ctx.sync()
     err = rel_l2(u.cpu().numpy(), ref[steps])
-    print(f"split 512^2 {steps} steps rel_l2 = {err:.3e}")
+    print(f"{prec} 512^2 {steps} steps rel_l2 = {err:.3e}")
     assert err <= TOL_SPLIT_100
 
 
@@ -103,13 +107,15 @@ def test_split_full_size_100_steps():
     assert err <= TOL_SPLIT_100
 
 
-def test_split_without_shared_propagator_uses_f32_gemv():
-    """1D heat has three propagator classes: LEM_PREC_SPLIT applies FP32 propagators with a
-    float-float GEMV there; 100 steps stay within the split bar of the oracle."""
+def test_split_without_shared_propagator_paths():
+    """1D heat has three propagator classes: LEM_PREC_SPLIT_FAST applies FP32 propagators
+    with a float-float GEMV there (100 steps within the split bar of the oracle), and
+    LEM_PREC_SPLIT falls back to the FP64 path."""
     wl = W.heat1d()
     X = assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
     wins = decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
-    ctx = L.Lem.from_workload(wl, prec="split")
+    assert L.APPLY_PATHS[L.Lem.from_workload(wl, prec="split").info()["apply_path"]].startswith("fp64")
+    ctx = L.Lem.from_workload(wl, prec="split_fast")
     assert L.APPLY_PATHS[ctx.info()["apply_path"]] == "f32_gemv"
     u = torch.tensor(wl["u0"], device="cuda")
     ctx.step(u, 100)
@@ -144,3 +150,55 @@ def test_split_ragged_tile_grids_vs_oracle(shared_P, side):
     ctx.step(u, 10)
     ctx.sync()
     assert rel_l2(u.cpu().numpy(), ref) <= TOL_SPLIT_100
+
+
+@pytest.mark.parametrize("side,tile,H", [
+    (128, 8, 4),    # 16-wide windows, 64-row propagator (one M block, half masked)
+    (128, 8, 7),    # 22-wide windows: K slice not a multiple of 16
+    (96, 16, 5),    # 26-wide windows, 256 rows
+    (160, 16, 8),   # 32-wide windows, ragged 10-tile grid
+    (128, 32, 4),   # 40-wide windows, 1024 rows
+])
+def test_split_small_tiles_vs_oracle(side, tile, H):
+    """Tile and overlap shapes of uneven-size batches (tile 8/16/32, H 4-8): window widths
+    that are not multiples of the 16-wide MMA K step and propagators with fewer rows than an
+    MMA block still take the tensor path and stay within the split bar."""
+    wl = W.advdiff2d(side=side, tile=tile, overlap=H, nu=7.0, a=(2.0, 1.0), dt=2.0, ell=8.0, seed=11)
+    X = assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    wins = decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
+    P = local_propagators(X, wins, "phi", tiles=[0])[0]
+    props = [P] * len(wins)
+    ref = wl["u0"].copy()
+    for _ in range(20):
+        ref = lem_step(X, ref, wins, props, "phi")
+    ctx = L.Lem.from_workload(wl, prec="split")
+    assert ctx.info()["split_path"] == 1
+    u = torch.tensor(wl["u0"], device="cuda")
+    ctx.step(u, 20)
+    ctx.sync()
+    err = rel_l2(u.cpu().numpy(), ref)
+    print(f"split {side}^2 tile {tile} H {H} 20 steps rel_l2 = {err:.3e}")
+    assert err <= TOL_SPLIT_100
+
+
+def test_split_rough_decaying_field_100_steps():
+    """A rough field (correlation length 8 h on a 64^2 mesh) under strong diffusion
+    (nu dt / h^2 = 42) loses three orders of magnitude in 100 steps, so early rounding
+    errors in its slow modes count against a much smaller final state. The three-piece tier
+    keeps 100 steps within the bar; the two-piece tier is only reported."""
+    p = W.batch_problems(n=20, seed=5, side_max=128)[4]
+    assert p["shape"] == (64, 64) and p["tile"] == (32, 32) and p["overlap"] == (7, 7)
+    X = assemble_operator(p["shape"], p["bc"], p["coef"], p["dt"])
+    wins = decompose(p["shape"], p["bc"], p["tile"], p["overlap"])
+    from oracle import lem_run
+    ref = lem_run(X, p["u0"], wins, 100)
+    errs = {}
+    for prec in ("split", "split_fast"):
+        ctx = L.Lem.from_workload(p, prec=prec)
+        assert ctx.info()["split_path"] == 1
+        u = torch.tensor(p["u0"], device="cuda")
+        ctx.step(u, 100)
+        ctx.sync()
+        errs[prec] = rel_l2(u.cpu().numpy(), ref)
+    print(f"rough decaying 64^2, 100 steps: rel_l2 {errs}")
+    assert errs["split"] <= TOL_SPLIT_100

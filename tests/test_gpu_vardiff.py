@@ -51,7 +51,7 @@ def test_fp64_gemv_dirichlet_no_reaction():
 def test_f32_gemv_reaction_within_split_bar():
     wl = W.vardiff2d(side=96, tile=16, overlap=6)
     wl["refresh"] = 5
-    err, path = _run(wl, "split", 20)
+    err, path = _run(wl, "split_fast", 20)
     print(f"f32 gemv vardiff 96^2 20 steps rel_l2 = {err:.3e}")
     assert path == "f32_gemv" and err <= 1e-6
 
