@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LEM dof-steps/s"
 WORKLOAD = "advdiff2d_2048x2048_periodic_tile32_H8_phi"
+BATCH_WORKLOAD = "batch512_uneven_advdiff2d_periodic_side64-512_tile8-32_H4-8"
 
 
 def parse():
@@ -42,6 +43,11 @@ def parse():
                          "pieces (four products); fp64: the plain FP64 GPU path")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--workload", default="advdiff2d", choices=["advdiff2d", "batch512"],
+                    help="advdiff2d: one 2048^2 problem (default); batch512: 512 uneven problems under one "
+                         "CUDA graph")
+    ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
+    ap.add_argument("--lanes", type=int, default=16, help="batch512: concurrent lanes in the graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
@@ -159,9 +165,58 @@ def oracle_sample(side, max_seconds=20.0):
                       f"the one-time propagator build took {t_build:.1f} s and is excluded"}
 
 
+def oracle_batch_sample(nprob, inner, max_seconds=20.0):
+    """The FP64 oracle on a bounded sample of the uneven batch: whole problems (the smallest
+    first, so that several fit), their propagators built once, then LEM steps."""
+    import oracle as O
+    from paper_1505_02248_gb300 import workloads as W
+    probs = sorted(W.batch_problems(n=nprob, seed=3), key=lambda p: p["shape"][0])[:4]
+    t_build = 0.0
+    prepared = []
+    for p in probs:
+        X = O.assemble_operator(p["shape"], p["bc"], p["coef"], p["dt"])
+        wins = O.decompose(p["shape"], p["bc"], p["tile"], p["overlap"])
+        t0 = time.perf_counter()
+        P = O.local_propagators(X, wins, "phi", tiles=[0])[0]
+        t_build += time.perf_counter() - t0
+        prepared.append((X, wins, [P] * len(wins), p["u0"].copy()))
+    dofs, t_step, steps = 0, 0.0, 0
+    while t_step < max_seconds / 2 and steps < inner:
+        for k, (X, wins, props, u) in enumerate(prepared):
+            t0 = time.perf_counter()
+            u = O.lem_step(X, u, wins, props, "phi")
+            t_step += time.perf_counter() - t0
+            prepared[k] = (X, wins, props, u)
+            dofs += u.size
+        steps += 1
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": dofs / t_step, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{len(prepared)} smallest of {nprob} problems x {steps} LEM steps (numpy FP64 oracle); "
+                      f"their propagator builds took {t_build:.1f} s and are excluded"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if a.workload == "batch512":
+        per, cb = [], None
+        for _ in range(a.warmup + a.steps):
+            cb = oracle_batch_sample(a.nprob, a.inner, max_seconds=4.0)
+            per.append(cb["value"])
+        v = statistics.median(per[a.warmup:]) if len(per) > a.warmup else per[-1]
+        cb["value"] = v
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": BATCH_WORKLOAD, "impl": "FP64 CPU oracle on a problem sample"},
+                "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     per = []
     cb = None
@@ -179,10 +234,158 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a):
+    """Uneven batch: a.nprob independent periodic advection-diffusion problems (side
+    32 U{2..16}, mu U[1, 50], tile {8, 16, 32}, overlap U{4..8}) advanced by one CUDA graph
+    launch per bench step (a.inner LEM steps each). Replicas per rank for N > 1."""
+    import torch
+    import torch.distributed as dist
+    from paper_1505_02248_gb300 import lem as L
+    from paper_1505_02248_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    L.load()
+    stream = torch.cuda.current_stream(dev)
+    probs = W.batch_problems(n=a.nprob, seed=3)
+    npts = [p["u0"].size for p in probs]
+    t0 = time.perf_counter()
+    ctxs = [L.Lem.from_workload(p, prec=a.prec, device=local, stream=stream.cuda_stream) for p in probs]
+    states = [torch.tensor(p["u0"], device=dev) for p in probs]
+    for c in ctxs:
+        c.build()
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch = L.Batch(ctxs, states, steps_per_launch=a.inner, lanes=a.lanes, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    schedule_s = time.perf_counter() - t0
+    est, lane = batch.schedule()
+    loads = np.bincount(lane, weights=est)
+    sched = batch.info()
+    paths = sorted({L.APPLY_PATHS[c.info()["apply_path"]] for c in ctxs})
+
+    batch.run(a.warmup)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            starts[k].record(stream)
+            batch.run(1)
+            stops[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
+    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms_max = float(t.item())
+    total = sum(npts)
+
+    # end to end: every problem's state from pinned host memory, one graph launch, back to host
+    host = [torch.tensor(p["u0"]).pin_memory() for p in probs]
+    e2e_ms = []
+    for _ in range(max(3, min(a.steps, 5))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for s, h in zip(states, host):
+            s.copy_(h, non_blocking=True)
+        batch.run(1)
+        for s, h in zip(states, host):
+            h.copy_(s, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_ms_med = statistics.median(e2e_ms)
+
+    # dominant kernel (the split GEMM), algorithmic FLOPs = products x 2 x owner rows x window
+    # nodes x windows. Fused schedule: the multi-problem GEMM launches of a.inner steps timed
+    # with events outside the graph; lanes: each problem's launches timed on a copy of its state.
+    gemm_ms, gemm_n, flops, prof = 0.0, 0, 0.0, None
+    if sched["fused"]:
+        prof = batch.profile(a.inner)
+        gemm_ms, gemm_n, flops = prof["gemm_ms"], a.inner, prof["gemm_flops"]
+    else:
+        nprod = {"split": 6, "split_fast": 4}.get(a.prec, 1)
+        for p, c, s in zip(probs, ctxs, states):
+            v = s.clone()
+            c.set_timing(True)
+            c.get_timing()
+            c.step(v, 1)
+            ms, n = c.get_timing()
+            c.set_timing(False)
+            gemm_ms += ms
+            gemm_n += n
+            (ty, tx), (hy, hx) = p["tile"], p["overlap"]
+            ntiles = (p["shape"][0] // ty) * (p["shape"][1] // tx)
+            flops += nprod * 2.0 * ty * tx * (ty + 2 * hy) * (tx + 2 * hx) * ntiles
+    batch.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    tflops_peak, _, peak_src = peaks()
+    value = total * a.inner * a.steps * world / (dev_ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dev_ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"split": "f16x3-split/f32-acc", "split_fast": "f16x2-split/f32-acc"}.get(a.prec, "f64"),
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "problems": a.nprob, "nodes": total,
+                   "lem_steps_per_step": a.inner, "lanes": int(len(loads)), "prec": a.prec, "apply_paths": paths,
+                   "l2": "working set (states, residual pieces, propagator pieces) several GB > L2",
+                   "parallelism": f"replicas x{world}", "build_s": round(build_s, 1),
+                   "schedule_s": round(schedule_s, 1),
+                   "schedule": "fused" if sched["fused"] else "lanes",
+                   "candidate_ms_per_launch": {"lanes": sched["lanes_ms"], "fused": sched["fused_ms"]},
+                   "lane_load_ms": {"max": float(loads.max()), "mean": float(loads.mean())}},
+        # per problem and launch: FP64->float-float, max|r| pass, (residual + GEMM) per LEM
+        # step, float-float->FP64 (split); residual, gather, GEMM, scatter per step (FP64)
+        # fused: conversion, max|r| pass, (residual + GEMM) per LEM step, conversion back
+        "gpu_launches": a.steps * (3 + 2 * a.inner) if sched["fused"] else
+        a.steps * sum((3 + 2 * a.inner) if L.APPLY_PATHS[c.info()["apply_path"]] == "tc_split"
+                      else 4 * a.inner for c in ctxs),
+    }
+    if gemm_n:
+        ach = flops / (gemm_ms * 1e-3) / 1e12
+        line["roofline"] = {"kernel": "split_gemm_kernel (tcgen05 kind::f16), " +
+                            ("one multi-problem launch per step" if sched["fused"] else "per problem"),
+                            "bound": "tensor",
+                            "achieved": ach, "peak": tflops_peak, "unit": "TFLOP/s", "frac": ach / tflops_peak,
+                            "traffic": None, "avg_launch_us": gemm_ms / gemm_n * 1e3, "launches": gemm_n,
+                            "peak_source": f"{peak_src} bf16 dense (fp16 same rate)"}
+    line["e2e"] = {"value": total * a.inner / (e2e_ms_med * 1e-3), "unit": METRIC,
+                   "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "ms_per_step": e2e_ms_med}
+    line["clocks"] = clk.summary()
+    if prof is not None:
+        line["step_breakdown_ms"] = {"gemm": prof["gemm_ms"], "residual": prof["residual_ms"],
+                                     "conversions": prof["other_ms"], "lem_steps": a.inner}
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_batch_sample(a.nprob, a.inner)
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.workload == "batch512":
+        run_batch(a)
         return
     import torch
     import torch.distributed as dist

@@ -198,11 +198,9 @@ void lem_destroy(lem_ctx* ctx);
 /* ------------------------------------------------------------------ batching
  * Advance many independent problems (contexts) together with one CUDA graph launch per
  * `steps_per_launch` LEM steps. At creation every context is built and warmed up on a copy
- * of its state, its step time is measured, and the problems are spread over up to `lanes`
- * concurrent lanes by longest-processing-time-first (the schedule is chosen from the
- * measurements); the graph then holds each lane's problems in sequence and the lanes in
- * parallel. The states d_states[i] (device, FP64) are captured: each launch advances them in
- * place. Contexts with a Jacobian refresh (reaction with refresh > 0) are rejected, because
+ * of its state and its step time is measured; the schedule (lem_batch_info) is then picked
+ * by timing the candidates. The states d_states[i] (device, FP64) are captured: each launch
+ * advances them in place. Contexts with a Jacobian refresh (reaction with refresh > 0) are rejected, because
  * rebuilding propagators cannot be captured. The contexts' streams are used only outside the
  * graph; the graph runs on `stream`. The paper has no batching layer (its local problems are
  * independent, Sec. 3). Errors: LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA. */
@@ -216,6 +214,25 @@ lem_status lem_batch_run(lem_batch* b, int launches);
 
 /* Measured single-launch time of each problem (ms, host array of n) and its lane. */
 lem_status lem_batch_schedule(const lem_batch* b, double* est_ms, int* lane);
+
+/* Which schedule the graph runs. Both candidates are captured and timed on scratch copies of
+ * the states at creation, and the faster is kept: lanes (every context's own launches on
+ * concurrent graph branches, problems assigned longest-first) or fused (all contexts on the
+ * same tensor-core split tier: one residual and one persistent GEMM launch per LEM step for
+ * the whole batch). fused_ms = -1 when the contexts cannot be fused. The environment variable
+ * LEM_BATCH_SCHEDULE=lanes|fused, read at creation, overrides the timed choice. */
+lem_status lem_batch_info(const lem_batch* b, int* fused, double* lanes_ms, double* fused_ms);
+
+/* Wait for the batch stream; LEM_ETIMEOUT if a tensor-core kernel gave up waiting. */
+lem_status lem_batch_sync(lem_batch* b);
+
+/* Fused schedule only: run `nsteps` LEM steps of every problem outside the graph (advancing the
+ * captured states like a launch does) with CUDA events around each kernel, and report the
+ * time spent in the GEMM launches, in the residual launches and in the rest (state
+ * conversions), plus the GEMM launches' algorithmic FLOPs (products x 2 x owner rows x window
+ * nodes x windows). LEM_EINVAL on a lanes schedule. */
+lem_status lem_batch_profile(lem_batch* b, int nsteps, double* gemm_ms, double* residual_ms, double* other_ms,
+                             double* gemm_flops);
 
 void lem_batch_destroy(lem_batch* b);
 

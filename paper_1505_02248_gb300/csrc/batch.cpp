@@ -1,5 +1,13 @@
 // Batched advance of independent problems under one CUDA graph (lem_batch_*, include/lem.h).
+//
+// Two schedules are built and timed, and the faster one is kept:
+//  * lanes: every context's own step launches, spread over concurrent lanes (graph branches)
+//    by longest-processing-time-first from each problem's measured step time;
+//  * fused (all contexts on the same tensor-core split tier): one residual launch and one
+//    persistent GEMM launch per LEM step for all problems together.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -7,22 +15,99 @@
 
 struct lem_batch {
   int n = 0, steps = 0, nlanes = 0, device = 0;
+  int fused = 0;              // the graph runs the fused schedule
+  double lanes_ms = -1.0;     // measured time of one launch of each candidate (-1: not built)
+  double fused_ms = -1.0;
   cudaStream_t stream = nullptr;
   std::vector<cudaStream_t> lane_streams;
+  std::vector<lem_ctx*> ctxs;
   std::vector<double> est_ms;
   std::vector<int> lane;
+  std::vector<std::vector<int>> lane_items;
+  lem::SplitBatch* sb = nullptr;  // fused tables the graph reads
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
 
+using lem::fail;
+
 void free_batch(lem_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (cudaStream_t s : b->lane_streams) cudaStreamDestroy(s);
+  for (cudaStream_t s : b->lane_streams)
+    if (s) cudaStreamDestroy(s);
+  lem::split_batch_destroy(b->sb);
   delete b;
+}
+
+// Capture one launch of a schedule into an executable graph. lanes: each lane's problems in
+// sequence on the lane's stream, the lanes in parallel; fused: the multi-problem steps.
+lem_status capture(lem_batch* b, double* const* states, lem::SplitBatch* sb, cudaGraph_t* g_out,
+                   cudaGraphExec_t* e_out) {
+  *g_out = nullptr;
+  *e_out = nullptr;
+  cudaStream_t cap = nullptr;
+  LEM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  std::vector<cudaEvent_t> ev(b->nlanes + 1, nullptr);
+  lem_status st = LEM_OK;
+  for (auto& e : ev)
+    if (st == LEM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = LEM_ECUDA;
+  if (st == LEM_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LEM_ECUDA;
+  if (st == LEM_OK) {
+    if (sb) {
+      st = lem::split_batch_step(sb, b->steps, cap);
+    } else {
+      cudaEventRecord(ev[b->nlanes], cap);
+      for (int l = 0; l < b->nlanes && st == LEM_OK; ++l) {
+        cudaStreamWaitEvent(b->lane_streams[l], ev[b->nlanes], 0);
+        for (int i : b->lane_items[l]) {
+          lem_ctx* c = b->ctxs[i];
+          cudaStream_t keep = c->stream;
+          c->stream = b->lane_streams[l];
+          st = lem_step(c, states[i], b->steps);
+          c->stream = keep;
+          if (st != LEM_OK) break;
+        }
+        cudaEventRecord(ev[l], b->lane_streams[l]);
+        cudaStreamWaitEvent(cap, ev[l], 0);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (st == LEM_OK && e != cudaSuccess) st = lem::cuda_fail(e, "cudaStreamEndCapture");
+    if (st == LEM_OK) {
+      const cudaError_t e2 = cudaGraphInstantiate(e_out, g, 0);
+      if (e2 != cudaSuccess) st = lem::cuda_fail(e2, "cudaGraphInstantiate");
+    }
+    if (st == LEM_OK) *g_out = g;
+    else if (g) cudaGraphDestroy(g);
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  cudaStreamDestroy(cap);
+  cudaGetLastError();
+  return st;
+}
+
+// One warm launch, then the time of one launch.
+lem_status time_graph(cudaGraphExec_t exec, cudaStream_t s, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LEM_CUDA_TRY(cudaEventCreate(&e0));
+  LEM_CUDA_TRY(cudaEventCreate(&e1));
+  lem_status st = LEM_OK;
+  if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+      cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+      cudaEventSynchronize(e1) != cudaSuccess)
+    st = lem::cuda_fail(cudaGetLastError(), "timing a batch graph");
+  float f = 0.0f;
+  if (st == LEM_OK) cudaEventElapsedTime(&f, e0, e1);
+  *ms = f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 }  // namespace
@@ -31,43 +116,51 @@ extern "C" {
 
 lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n, int steps_per_launch, int lanes,
                             void* cuda_stream, lem_batch** out) {
-  if (!out) return lem::fail(LEM_EINVAL, "out is NULL");
+  if (!out) return fail(LEM_EINVAL, "out is NULL");
   *out = nullptr;
   if (!ctxs || !d_states || n <= 0 || steps_per_launch <= 0 || lanes <= 0)
-    return lem::fail(LEM_EINVAL, "bad batch arguments");
+    return fail(LEM_EINVAL, "bad batch arguments");
   const int dev = ctxs[0] ? ctxs[0]->device : -1;
   for (int i = 0; i < n; ++i) {
-    if (!ctxs[i] || !d_states[i]) return lem::fail(LEM_EINVAL, "NULL context or state");
-    if (ctxs[i]->device != dev) return lem::fail(LEM_EINVAL, "contexts on different devices");
+    if (!ctxs[i] || !d_states[i]) return fail(LEM_EINVAL, "NULL context or state");
+    if (ctxs[i]->device != dev) return fail(LEM_EINVAL, "contexts on different devices");
     if (ctxs[i]->desc.reaction && ctxs[i]->desc.refresh > 0)
-      return lem::fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators and cannot be captured");
+      return fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators and cannot be captured");
   }
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != dev) cudaSetDevice(dev);
+  lem::DeviceGuard guard(dev);
   lem_batch* b = new lem_batch();
   b->n = n;
   b->steps = steps_per_launch;
   b->device = dev;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
   b->nlanes = std::min(lanes, n);
+  b->ctxs.assign(ctxs, ctxs + n);
   lem_status st = LEM_OK;
-  // warm up every context on a copy of its state (builds, lazy buffers, packed propagators)
-  // and measure one launch worth of steps
+  // scratch copies of every state: warm-up, per-problem timing and the candidate schedules
+  // run on them, so the caller's states are untouched until the first lem_batch_run
+  std::vector<double*> tmp(n, nullptr);
+  for (int i = 0; i < n && st == LEM_OK; ++i) {
+    if (cudaMalloc(&tmp[i], sizeof(double) * ctxs[i]->npts) != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(LEM_ENOMEM, "batch scratch states");
+      break;
+    }
+    if (cudaMemcpyAsync(tmp[i], d_states[i], sizeof(double) * ctxs[i]->npts, cudaMemcpyDeviceToDevice,
+                        ctxs[i]->stream) != cudaSuccess)
+      st = LEM_ECUDA;
+  }
+  // warm up (builds, lazy buffers, packed propagators) and time each problem
   b->est_ms.assign(n, 0.0);
-  {
+  if (st == LEM_OK) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int i = 0; i < n && st == LEM_OK; ++i) {
       lem_ctx* c = ctxs[i];
-      double* tmp = nullptr;
-      if (cudaMalloc(&tmp, sizeof(double) * c->npts) != cudaSuccess) { cudaGetLastError(); st = LEM_ENOMEM; break; }
-      cudaMemcpyAsync(tmp, d_states[i], sizeof(double) * c->npts, cudaMemcpyDeviceToDevice, c->stream);
-      st = lem_step(c, tmp, steps_per_launch);  // first call: builds and allocates
+      st = lem_step(c, tmp[i], steps_per_launch);
       if (st == LEM_OK) {
         cudaEventRecord(e0, c->stream);
-        st = lem_step(c, tmp, steps_per_launch);
+        st = lem_step(c, tmp[i], steps_per_launch);
         cudaEventRecord(e1, c->stream);
       }
       if (st == LEM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
@@ -75,87 +168,94 @@ lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n
         cudaEventElapsedTime(&ms, e0, e1);
         b->est_ms[i] = ms;
       }
-      cudaStreamSynchronize(c->stream);
-      cudaFree(tmp);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st == LEM_OK && cudaDeviceSynchronize() != cudaSuccess) st = lem::cuda_fail(cudaGetLastError(), "warm-up");
   }
-  if (st != LEM_OK) { free_batch(b); if (prev >= 0) cudaSetDevice(prev); return st; }
-  // schedule: longest problems first, each to the lane with the least work so far
-  std::vector<int> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->est_ms[a] > b->est_ms[c]; });
-  std::vector<double> load(b->nlanes, 0.0);
-  std::vector<std::vector<int>> lane_items(b->nlanes);
-  b->lane.assign(n, 0);
-  for (int i : order) {
-    const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
-    load[l] += b->est_ms[i];
-    lane_items[l].push_back(i);
-    b->lane[i] = l;
-  }
-  b->lane_streams.resize(b->nlanes, nullptr);
-  for (auto& s : b->lane_streams)
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); st = LEM_ECUDA; }
-  // capture: fork from the batch stream into the lanes, each lane's problems in sequence,
-  // join back. Each context is redirected to its lane's stream for the capture.
-  cudaStream_t cap = nullptr;
-  if (st == LEM_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) st = LEM_ECUDA;
-  std::vector<cudaEvent_t> ev(b->nlanes + 1, nullptr);
-  for (auto& e : ev)
-    if (st == LEM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = LEM_ECUDA;
-  if (st == LEM_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LEM_ECUDA;
+  // lanes: longest problems first, each to the lane with the least work so far
   if (st == LEM_OK) {
-    cudaEventRecord(ev[b->nlanes], cap);
-    for (int l = 0; l < b->nlanes && st == LEM_OK; ++l) {
-      cudaStreamWaitEvent(b->lane_streams[l], ev[b->nlanes], 0);
-      for (int i : lane_items[l]) {
-        lem_ctx* c = ctxs[i];
-        cudaStream_t keep = c->stream;
-        c->stream = b->lane_streams[l];
-        st = lem_step(c, d_states[i], steps_per_launch);
-        c->stream = keep;
-        if (st != LEM_OK) break;
-      }
-      cudaEventRecord(ev[l], b->lane_streams[l]);
-      cudaStreamWaitEvent(cap, ev[l], 0);
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->est_ms[a] > b->est_ms[c]; });
+    std::vector<double> load(b->nlanes, 0.0);
+    b->lane_items.assign(b->nlanes, {});
+    b->lane.assign(n, 0);
+    for (int i : order) {
+      const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
+      load[l] += b->est_ms[i];
+      b->lane_items[l].push_back(i);
+      b->lane[i] = l;
     }
-    cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(cap, &g);
-    if (st == LEM_OK && e != cudaSuccess) st = lem::cuda_fail(e, "cudaStreamEndCapture");
-    b->graph = g;
-    if (st == LEM_OK) {
-      const cudaError_t e2 = cudaGraphInstantiate(&b->exec, b->graph, 0);
-      if (e2 != cudaSuccess) st = lem::cuda_fail(e2, "cudaGraphInstantiate");
-    }
+    b->lane_streams.assign(b->nlanes, nullptr);
+    for (auto& s : b->lane_streams)
+      if (st == LEM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = LEM_ECUDA;
   }
-  for (auto& e : ev)
-    if (e) cudaEventDestroy(e);
-  if (cap) cudaStreamDestroy(cap);
-  cudaGetLastError();
-  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
-  if (st != LEM_OK) { free_batch(b); return st; }
+  // time both candidate schedules on the scratch states
+  const bool can_fuse = lem::split_batch_eligible(const_cast<lem_ctx* const*>(ctxs), n);
+  if (st == LEM_OK) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    st = capture(b, tmp.data(), nullptr, &g, &e);
+    if (st == LEM_OK) st = time_graph(e, b->stream, &b->lanes_ms);
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+  }
+  if (st == LEM_OK && can_fuse) {
+    lem::SplitBatch* sb = nullptr;
+    st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), tmp.data(), n, &sb);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    if (st == LEM_OK) st = capture(b, tmp.data(), sb, &g, &e);
+    if (st == LEM_OK) st = time_graph(e, b->stream, &b->fused_ms);
+    if (st == LEM_OK) st = lem::split_batch_check_error(sb);
+    if (e) cudaGraphExecDestroy(e);
+    if (g) cudaGraphDestroy(g);
+    lem::split_batch_destroy(sb);
+  }
+  for (double* p : tmp)
+    if (p) cudaFree(p);
+  // the chosen schedule on the caller's states
+  if (st == LEM_OK) {
+    b->fused = can_fuse && b->fused_ms >= 0.0 && b->fused_ms < b->lanes_ms;
+    // LEM_BATCH_SCHEDULE=lanes|fused overrides the timing (a fused request on contexts that
+    // cannot be fused keeps lanes)
+    if (const char* f = std::getenv("LEM_BATCH_SCHEDULE")) {
+      if (std::strcmp(f, "lanes") == 0) b->fused = 0;
+      if (std::strcmp(f, "fused") == 0) b->fused = can_fuse && b->fused_ms >= 0.0;
+    }
+    if (b->fused) st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), const_cast<double* const*>(d_states), n, &b->sb);
+    if (st == LEM_OK) st = capture(b, const_cast<double* const*>(d_states), b->sb, &b->graph, &b->exec);
+  }
+  if (st != LEM_OK) {
+    free_batch(b);
+    return st;
+  }
   *out = b;
   return LEM_OK;
 }
 
 lem_status lem_batch_run(lem_batch* b, int launches) {
-  if (!b || launches < 0) return lem::fail(LEM_EINVAL, "bad batch run arguments");
-  int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != b->device) cudaSetDevice(b->device);
-  lem_status st = LEM_OK;
-  for (int k = 0; k < launches && st == LEM_OK; ++k) {
+  if (!b || launches < 0) return fail(LEM_EINVAL, "bad batch run arguments");
+  lem::DeviceGuard guard(b->device);
+  for (int k = 0; k < launches; ++k) {
     const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
-    if (e != cudaSuccess) st = lem::cuda_fail(e, "cudaGraphLaunch");
+    if (e != cudaSuccess) return lem::cuda_fail(e, "cudaGraphLaunch");
   }
-  if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
-  return st;
+  return LEM_OK;
+}
+
+lem_status lem_batch_sync(lem_batch* b) {
+  if (!b) return fail(LEM_EINVAL, "batch is NULL");
+  lem::DeviceGuard guard(b->device);
+  LEM_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (b->sb) return lem::split_batch_check_error(b->sb);
+  for (lem_ctx* c : b->ctxs) LEM_TRY(lem::split_check_error(c));
+  return LEM_OK;
 }
 
 lem_status lem_batch_schedule(const lem_batch* b, double* est_ms, int* lane) {
-  if (!b) return lem::fail(LEM_EINVAL, "batch is NULL");
+  if (!b) return fail(LEM_EINVAL, "batch is NULL");
   for (int i = 0; i < b->n; ++i) {
     if (est_ms) est_ms[i] = b->est_ms[i];
     if (lane) lane[i] = b->lane[i];
@@ -163,8 +263,50 @@ lem_status lem_batch_schedule(const lem_batch* b, double* est_ms, int* lane) {
   return LEM_OK;
 }
 
+lem_status lem_batch_info(const lem_batch* b, int* fused, double* lanes_ms, double* fused_ms) {
+  if (!b) return fail(LEM_EINVAL, "batch is NULL");
+  if (fused) *fused = b->fused;
+  if (lanes_ms) *lanes_ms = b->lanes_ms;
+  if (fused_ms) *fused_ms = b->fused_ms;
+  return LEM_OK;
+}
+
+lem_status lem_batch_profile(lem_batch* b, int nsteps, double* gemm_ms, double* residual_ms, double* other_ms,
+                             double* gemm_flops) {
+  if (!b || nsteps <= 0 || !gemm_ms || !residual_ms || !other_ms || !gemm_flops)
+    return fail(LEM_EINVAL, "bad batch profile arguments");
+  lem::DeviceGuard guard(b->device);
+  *gemm_ms = *residual_ms = *other_ms = *gemm_flops = 0.0;
+  if (!b->fused) return fail(LEM_EINVAL, "the batch runs the lanes schedule; time its contexts with lem_set_timing");
+  std::vector<cudaEvent_t> ev(2 * nsteps + 4, nullptr);
+  lem_status st = LEM_OK;
+  for (auto& e : ev)
+    if (st == LEM_OK && cudaEventCreate(&e) != cudaSuccess) st = LEM_ECUDA;
+  if (st == LEM_OK) st = cudaEventRecord(ev[2 * nsteps + 2], b->stream) == cudaSuccess ? LEM_OK : LEM_ECUDA;
+  if (st == LEM_OK) st = lem::split_batch_step(b->sb, nsteps, b->stream, ev.data());
+  if (st == LEM_OK) st = cudaEventRecord(ev[2 * nsteps + 3], b->stream) == cudaSuccess ? LEM_OK : LEM_ECUDA;
+  if (st == LEM_OK && cudaEventSynchronize(ev[2 * nsteps + 3]) != cudaSuccess) st = LEM_ECUDA;
+  if (st == LEM_OK) {
+    float t = 0.0f, total = 0.0f;
+    cudaEventElapsedTime(&total, ev[2 * nsteps + 2], ev[2 * nsteps + 3]);
+    for (int k = 0; k < nsteps; ++k) {
+      cudaEventElapsedTime(&t, ev[1 + 2 * k], ev[2 + 2 * k]);
+      *gemm_ms += t;
+      cudaEventElapsedTime(&t, k == 0 ? ev[0] : ev[2 * k], ev[1 + 2 * k]);
+      *residual_ms += t;
+    }
+    *other_ms = total - *gemm_ms - *residual_ms;
+    *gemm_flops = lem::split_batch_gemm_flops(b->sb, b->ctxs.data()) * nsteps;
+    st = lem::split_batch_check_error(b->sb);
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  return st;
+}
+
 void lem_batch_destroy(lem_batch* b) {
   if (!b) return;
+  lem::DeviceGuard guard(b->device);
   cudaStreamSynchronize(b->stream);
   free_batch(b);
 }

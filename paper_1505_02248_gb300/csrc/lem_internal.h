@@ -15,6 +15,17 @@ namespace lem {
 void set_error(const std::string& msg);
 lem_status fail(lem_status s, const std::string& msg);
 lem_status cuda_fail(cudaError_t e, const char* what);
+// makes `dev` current for a scope and restores the caller's device
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 #define LEM_CUDA_TRY(call)                                 \
   do {                                                     \
@@ -118,6 +129,14 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
 void split_destroy(lem_ctx* ctx);
 lem_status split_check_error(lem_ctx* ctx);
 bool split_eligible(const lem_ctx* ctx);
+// multi-problem split steps (one residual and one GEMM launch per step for a whole batch)
+struct SplitBatch;
+bool split_batch_eligible(lem_ctx* const* ctxs, int n);
+lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, SplitBatch** out);
+lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEvent_t* ev = nullptr);
+double split_batch_gemm_flops(const SplitBatch* b, lem_ctx* const* ctxs);
+lem_status split_batch_check_error(SplitBatch* b);
+void split_batch_destroy(SplitBatch* b);
 // allocation helper that tracks bytes
 lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes);
 }  // namespace lem

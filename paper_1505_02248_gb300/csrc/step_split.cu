@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -74,17 +75,28 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
 
 enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3 };
 
-struct GemmParams {
+// Geometry of one problem's GEMM (all counts in tiles unless stated).
+struct GemmGeom {
   int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx, nty;
   int M;                // owner rows (Ty * Tx); M blocks past it are masked
   int nbx;              // window blocks per row of the tile grid
-  int nMB, nNB;         // M blocks of 128 owner rows, window blocks of 128 windows
+  int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int bsplit_y;         // clustered: a window block's two halves split along y (else x)
+  int drain_rows;       // three pieces: window rows per correction drain
+  int unit0;            // multi-problem launch: this problem's first unit
   const int* eP;        // per owner row: P scale exponent
   const int* escale;    // [2] residual scale exponent of each step parity
-  unsigned* rmax;       // [2] max|r| accumulators (this kernel clears the current one)
-  int* err;
-  int parity;
+  unsigned* rmax;       // [2] max|r| accumulators (the GEMM clears the current one)
+  float* uh;            // float-float state
+  float* ul;
+};
+
+// Everything one problem's GEMM reads: its six tensor maps (P_int, P2, P3, r_int, r2, r3;
+// the third pieces unused with two) and its geometry. Passed by value (__grid_constant__)
+// for a single problem, or as a device array for a multi-problem launch.
+struct SplitProblem {
+  CUtensorMap tm[6];
+  GemmGeom g;
 };
 
 struct ResParams {
@@ -145,20 +157,17 @@ constexpr int RT = 32;  // residual output tile (padded coordinates), RT x RT pe
 // patch of u around it (mesh coordinates wrapped) is staged in shared memory, so each node
 // is read from global memory once per block with coalesced loads.
 // measure != 0: only accumulate max|r| into rmax[parity ^ 1] (no writes of r).
-__global__ void __launch_bounds__(256) residual_split_kernel(const float* __restrict__ uh,
-                                                             const float* __restrict__ ul,
-                                                             __half* __restrict__ Rint,
-                                                             __half* __restrict__ R2,
-                                                             __half* __restrict__ R3, ResParams p,
-                                                             unsigned* rmax, int* escale, int parity,
-                                                             int measure) {
+__device__ __forceinline__ void residual_tile(const float* __restrict__ uh, const float* __restrict__ ul,
+                                              __half* __restrict__ Rint, __half* __restrict__ R2,
+                                              __half* __restrict__ R3, const ResParams& p, unsigned* rmax,
+                                              int* escale, int parity, int measure, int bx, int by) {
   __shared__ float sh[RT + 2][RT + 3], sl[RT + 2][RT + 3];
   __shared__ float red[8];
   const float rm = __uint_as_float(rmax[parity]);
   const int er = rm > 0.0f ? (p.rb - 1) - exponent_above(rm) : 0;
   const float scale = pow2f(er);
-  if (!measure && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) escale[parity] = er;
-  const int x0 = blockIdx.x * RT, y0 = blockIdx.y * RT;  // padded tile origin
+  if (!measure && bx == 0 && by == 0 && threadIdx.x == 0) escale[parity] = er;
+  const int x0 = bx * RT, y0 = by * RT;  // padded tile origin
   const int wpad = p.nx + 2 * p.Hx;
   // stage u over padded rows y0-1 .. y0+RT and columns x0-1 .. x0+RT
   for (int e = threadIdx.x; e < (RT + 2) * (RT + 2); e += blockDim.x) {
@@ -229,6 +238,80 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
   }
 }
 
+__global__ void __launch_bounds__(256) residual_split_kernel(const float* __restrict__ uh,
+                                                             const float* __restrict__ ul,
+                                                             __half* __restrict__ Rint,
+                                                             __half* __restrict__ R2,
+                                                             __half* __restrict__ R3, ResParams p,
+                                                             unsigned* rmax, int* escale, int parity,
+                                                             int measure) {
+  residual_tile(uh, ul, Rint, R2, R3, p, rmax, escale, parity, measure, int(blockIdx.x), int(blockIdx.y));
+}
+
+// One problem of a multi-problem step: its residual arrays, parameters and block range.
+struct ResProblem {
+  ResParams p;
+  const float* uh;
+  const float* ul;
+  __half* Rint;
+  __half* R2;
+  __half* R3;
+  unsigned* rmax;
+  int* escale;
+  int gx;      // residual tiles along x
+  int block0;  // first block of this problem
+};
+
+__device__ __forceinline__ int find_block(const int* __restrict__ first, int n, int b) {
+  int lo = 0, hi = n - 1;  // last problem whose first block is <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The residual of every problem of a batch in one launch (one RT x RT tile per block).
+__global__ void __launch_bounds__(256) residual_multi_kernel(const ResProblem* __restrict__ rps,
+                                                             const int* __restrict__ first, int nprob, int parity,
+                                                             int measure) {
+  const int i = find_block(first, nprob, int(blockIdx.x));
+  const ResProblem& q = rps[i];
+  const int lb = int(blockIdx.x) - q.block0;
+  residual_tile(q.uh, q.ul, q.Rint, q.R2, q.R3, q.p, q.rmax, q.escale, parity, measure, lb % q.gx, lb / q.gx);
+}
+
+// FP64 <-> float-float for every problem of a batch; to_ff also clears each max|r| pair.
+struct ConvProblem {
+  double* u;
+  float* uh;
+  float* ul;
+  unsigned* rmax;
+  int64_t n;
+  int block0;
+};
+constexpr int CONV_CHUNK = 4096;
+
+__global__ void __launch_bounds__(256) convert_multi_kernel(const ConvProblem* __restrict__ cps,
+                                                            const int* __restrict__ first, int nprob, int to_ff) {
+  const int i = find_block(first, nprob, int(blockIdx.x));
+  const ConvProblem& q = cps[i];
+  const int64_t b0 = int64_t(int(blockIdx.x) - q.block0) * CONV_CHUNK;
+  const int64_t b1 = b0 + CONV_CHUNK < q.n ? b0 + CONV_CHUNK : q.n;
+  if (to_ff) {
+    if (b0 == 0 && threadIdx.x < 2) q.rmax[threadIdx.x] = 0u;
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+      const double v = q.u[k];
+      const float h = __double2float_rn(v);
+      q.uh[k] = h;
+      q.ul[k] = __double2float_rn(v - double(h));
+    }
+  } else {
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) q.u[k] = double(q.uh[k]) + double(q.ul[k]);
+  }
+}
+
 __global__ void f64_to_ff_kernel(const double* __restrict__ u, float* __restrict__ uh,
                                  float* __restrict__ ul, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -293,20 +376,20 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
   }
 }
 
-// Persistent GEMM. MC = false: each CTA walks output tiles t = blockIdx.x, + gridDim.x, ...
-// (M block t % nMB, window block t / nMB) and loads its own operands. MC = true: clusters of
-// 4 CTAs walk 2 x 2 groups of tiles; the two CTAs on the same M block each load half of
-// its P rows and multicast them to both, and the two on the same window block each load half
-// of the windows and multicast them, so every CTA issues half the TMA rows. A stage is reused
-// only after all three CTAs that write into it (self, P partner, window partner) released it.
-// Two TMEM accumulator sets alternate between tiles, so the epilogue of one tile overlaps the
-// MMAs of the next.
+// Persistent GEMM. MC = false: each CTA walks output units u = blockIdx.x, + gridDim.x, ...
+// A unit is one (M block, window block) tile of one problem: of the single problem `one`
+// (M block u % nMB, window block u / nMB), or, when `many` is given, of the problem whose
+// unit range holds u (a multi-problem launch: every problem of a batch advances by one step
+// in one launch). MC = true (single problem only): clusters of 4 CTAs walk 2 x 2 groups of
+// tiles; the two CTAs on the same M block each load half of its P rows and multicast them to
+// both, and the two on the same window block each load half of the windows and multicast
+// them, so every CTA issues half the TMA rows. A stage is reused only after all three CTAs
+// that write into it (self, P partner, window partner) released it. Two TMEM accumulator sets
+// alternate between tiles, so the epilogue of one tile overlaps the MMAs of the next.
 template <bool MC, int BN, int NP>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
-    split_gemm_kernel(const __grid_constant__ CUtensorMap tmPint, const __grid_constant__ CUtensorMap tmP2,
-                      const __grid_constant__ CUtensorMap tmP3, const __grid_constant__ CUtensorMap tmRint,
-                      const __grid_constant__ CUtensorMap tmR2, const __grid_constant__ CUtensorMap tmR3,
-                      float* __restrict__ uh, float* __restrict__ ul, GemmParams g) {
+    split_gemm_kernel(const __grid_constant__ SplitProblem one, const SplitProblem* __restrict__ many, int nprob,
+                      int nunits_many, int parity, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = Shape<BN, NP>::STAGES, STAGE_BYTES = Shape<BN, NP>::STAGE_BYTES;
@@ -321,26 +404,40 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   static_assert(!DRAIN || BN == 128, "drained correction: main[2] + corr[2] of 128 columns fill TMEM");
   uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set (main) ready
   uint64_t* acce = accf + 2;             // [2] accumulator set (main) drained
-  uint64_t* cf = acce + 2;               // DRAIN: [2] correction of one window row ready
+  uint64_t* cf = acce + 2;               // DRAIN: [2] correction of one row group ready
   uint64_t* ce = cf + 2;                 // DRAIN: [2] correction drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ce + 2);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = g.Wy;
-  const int nbx = g.nbx;
   const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
   const int mh = int(rank & 1u), nh = int(rank >> 1);  // MC: place in the 2 x 2 tile group
   const int unit0 = MC ? int(ptx::cluster_id_x()) : int(blockIdx.x);
   const int nunit_step = MC ? int(ptx::nclusters_x()) : int(gridDim.x);
-  const int nMBu = MC ? g.nMB / 2 : g.nMB;
-  const int nunits = nMBu * (MC ? g.nNB / 2 : g.nNB);
-  auto tile_of = [&](int u, int& m0, int& tx0, int& ty0) {
-    const int mb = MC ? 2 * (u % nMBu) + nh : u % nMBu;
-    const int nb = MC ? 2 * (u / nMBu) + mh : u / nMBu;
+  const int nMBu = MC ? one.g.nMB / 2 : one.g.nMB;
+  const int nunits = MC ? nMBu * (one.g.nNB / 2) : (many ? nunits_many : one.g.nMB * one.g.nNB);
+  // unit -> problem and its tile
+  auto locate = [&](int u, int& lu) -> const SplitProblem* {
+    if (!many) {
+      lu = u;
+      return &one;
+    }
+    int lo = 0, hi = nprob - 1;  // last problem with unit0 <= u
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (many[mid].g.unit0 <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    lu = u - many[lo].g.unit0;
+    return many + lo;
+  };
+  auto tile_of = [&](const GemmGeom& g, int lu, int& m0, int& tx0, int& ty0) {
+    const int nmb = MC ? nMBu : g.nMB;
+    const int mb = MC ? 2 * (lu % nmb) + nh : lu % nmb;
+    const int nb = MC ? 2 * (lu / nmb) + mh : lu / nmb;
     m0 = mb * BM;
-    tx0 = (nb % nbx) * g.BNx;
-    ty0 = (nb / nbx) * g.BNy;
+    tx0 = (nb % g.nbx) * g.BNx;
+    ty0 = (nb / g.nbx) * g.BNy;
   };
   // MC multicast masks: P partner shares the M block (differs in mh), window partner the
   // window block (differs in nh)
@@ -358,12 +455,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       ptx::mbar_init(&ce[b], EPI_WARPS);
     }
     ptx::fence_barrier_init();
-    ptx::tma_prefetch_desc(&tmPint); ptx::tma_prefetch_desc(&tmP2);
-    ptx::tma_prefetch_desc(&tmRint); ptx::tma_prefetch_desc(&tmR2);
-    if (NP == 3) { ptx::tma_prefetch_desc(&tmP3); ptx::tma_prefetch_desc(&tmR3); }
+    if (!many) {
+      for (int q = 0; q < 2 * NP; ++q) ptx::tma_prefetch_desc(&one.tm[q < NP ? q : 3 + q - NP]);
+    }
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
-    if (blockIdx.x == 0) g.rmax[g.parity] = 0u;
+    if (!many) {
+      if (blockIdx.x == 0) one.g.rmax[parity] = 0u;
+    } else {
+      for (int i = int(blockIdx.x); i < nprob; i += int(gridDim.x)) many[i].g.rmax[parity] = 0u;
+    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -380,13 +481,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (lane == 0) {
       int it = 0, issued = 0;
       for (int u = unit0; u < nunits && !s_abort; u += nunit_step) {
+        int lu;
+        const SplitProblem* pr = locate(u, lu);
+        const GemmGeom& g = pr->g;
         int m0, tx0, ty0;
-        tile_of(u, m0, tx0, ty0);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        tile_of(g, lu, m0, tx0, ty0);
+        for (int kb = 0; kb < g.Wy; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t use = it / STAGES;
           if (it >= STAGES && !ptx::mbar_wait(&empty[s], (use & 1) ^ 1, WAIT_NS)) {
-            atomicExch(g.err, ERR_TIMEOUT_PRODUCER);
+            atomicExch(err, ERR_TIMEOUT_PRODUCER);
             s_abort = 1;
             break;
           }
@@ -396,24 +500,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (MC) {
             // my half of the P rows (to me and the P partner), my half of the windows (to me
             // and the window partner); the partners send the other halves
-            const CUtensorMap* tp[3] = {&tmPint, &tmP2, &tmP3};
-            const CUtensorMap* tr[3] = {&tmRint, &tmR2, &tmR3};
             const int wx = g.bsplit_y ? tx0 : tx0 + nh * (g.BNx / 2);
             const int wy = g.bsplit_y ? ty0 + nh * (g.BNy / 2) : ty0;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-              ptx::tma_load_2d_mc(st + q * A_BYTES + mh * (A_BYTES / 2), tp[q], &full[s], kb * KB,
+              ptx::tma_load_2d_mc(st + q * A_BYTES + mh * (A_BYTES / 2), &pr->tm[q], &full[s], kb * KB,
                                   m0 + mh * (BM / 2), maskP);
-              ptx::tma_load_4d_mc(st + R_OFF + q * B_BYTES + nh * (B_BYTES / 2), tr[q], &full[s], 0, wx, kb, wy,
-                                  maskR);
+              ptx::tma_load_4d_mc(st + R_OFF + q * B_BYTES + nh * (B_BYTES / 2), &pr->tm[3 + q], &full[s], 0, wx,
+                                  kb, wy, maskR);
             }
           } else {
-            const CUtensorMap* tp[3] = {&tmPint, &tmP2, &tmP3};
-            const CUtensorMap* tr[3] = {&tmRint, &tmR2, &tmR3};
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-              ptx::tma_load_2d(st + q * A_BYTES, tp[q], &full[s], kb * KB, m0);
-              ptx::tma_load_4d(st + R_OFF + q * B_BYTES, tr[q], &full[s], 0, tx0, kb, ty0);
+              ptx::tma_load_2d(st + q * A_BYTES, &pr->tm[q], &full[s], kb * KB, m0);
+              ptx::tma_load_4d(st + R_OFF + q * B_BYTES, &pr->tm[3 + q], &full[s], 0, tx0, kb, ty0);
             }
           }
           issued = it + 1;
@@ -426,23 +526,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     // TMEM columns: without DRAIN, set b = [main | corr] at b * 2BN; with DRAIN, main b at
-    // b * BN and the two correction buffers at 2BN and 3BN.
+    // b * BN and the two correction buffers at 2BN and 3BN. A DRAIN correction buffer
+    // collects drain_rows window rows before the epilogue takes it.
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
       bool ok = true;
       int it = 0, lt = 0, kc = 0;
       for (int u = unit0; u < nunits && ok; u += nunit_step, ++lt) {
+        int lu;
+        const GemmGeom& g = locate(u, lu)->g;
+        const int nk = g.Wy, ksteps = (g.Wx + 15) / 16, dr = DRAIN ? g.drain_rows : 1;
         const int b = lt % NBUF;
         if (lt >= NBUF) {
           if (!ptx::mbar_wait(&acce[b], ((lt / NBUF) - 1) & 1, WAIT_NS)) { ok = false; break; }
           ptx::tc_fence_after();
         }
         const uint32_t main = DRAIN ? tmem + b * BN : tmem + b * 2 * BN;
+        uint32_t corr = main + BN;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, WAIT_NS)) { ok = false; break; }
-          uint32_t corr = main + BN;
-          if (DRAIN) {
+          const bool group_first = DRAIN && kb % dr == 0;
+          const bool group_last = DRAIN && (kb % dr == dr - 1 || kb == nk - 1);
+          if (group_first) {
             const int j = kc & 1;
             if (kc >= 2 && !ptx::mbar_wait(&ce[j], ((kc >> 1) - 1) & 1, WAIT_NS)) { ok = false; break; }
             corr = tmem + (2 + j) * BN;
@@ -456,11 +562,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint64_t dP3 = ptx::sw128_kmajor_desc(base + 2 * A_BYTES);       // NP == 3 only
           const uint64_t dR3 = ptx::sw128_kmajor_desc(base + R_OFF + 2 * B_BYTES);  // NP == 3 only
           // ceil(Wx / 16) K steps: P is zero beyond Wx in each padded window row
-          for (int kk = 0; kk < (g.Wx + 15) / 16; ++kk) {
+          for (int kk = 0; kk < ksteps; ++kk) {
             const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
             const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-            // DRAIN: each window row starts a fresh correction sum
-            const uint32_t cacc = DRAIN ? (kk > 0 ? 1u : 0u) : acc;
+            // DRAIN: each row group starts a fresh correction sum
+            const uint32_t cacc = DRAIN ? ((group_first && kk == 0) ? 0u : 1u) : acc;
             ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
             ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, cacc);
             ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
@@ -472,13 +578,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
           if (MC) ptx::mma_commit_mc(&empty[s], maskE);
           else ptx::mma_commit(&empty[s]);
-          if (DRAIN) ptx::mma_commit(&cf[kc & 1]);
-          ++kc;
+          if (group_last) {
+            ptx::mma_commit(&cf[kc & 1]);
+            ++kc;
+          }
         }
         if (ok) ptx::mma_commit(&accf[b]);
       }
       if (!ok) {
-        atomicExch(g.err, ERR_TIMEOUT_MMA);
+        atomicExch(err, ERR_TIMEOUT_MMA);
         s_abort = 1;
       }
       if (MC) {
@@ -493,13 +601,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int row = lane_base + lane;       // TMEM lane = owner row within the M block
     int lt = 0, kc = 0;
     for (int u = unit0; u < nunits; u += nunit_step, ++lt) {
+      int lu;
+      const GemmGeom& g = locate(u, lu)->g;
       const int b = lt % NBUF;
-      float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over window rows
+      float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over row groups
       if constexpr (DRAIN) {
 #pragma unroll
         for (int i = 0; i < BN; ++i) cs[i] = 0.0f;
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++kc) {
+        const int ngroups = (g.Wy + g.drain_rows - 1) / g.drain_rows;
+        for (int gi = 0; gi < ngroups; ++gi, ++kc) {
           const int j = kc & 1;
           if (s_abort || !ptx::mbar_wait(&cf[j], (kc >> 1) & 1, WAIT_NS)) { ok = false; break; }
           ptx::tc_fence_after();
@@ -517,23 +628,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (lane == 0) ptx::mbar_arrive(&ce[j]);
         }
         if (!ok) {
-          atomicExch(g.err, ERR_TIMEOUT_EPI);
+          atomicExch(err, ERR_TIMEOUT_EPI);
           break;
         }
       }
       if (!ptx::mbar_wait(&accf[b], (lt / NBUF) & 1, WAIT_NS)) {
-        atomicExch(g.err, ERR_TIMEOUT_EPI);
+        atomicExch(err, ERR_TIMEOUT_EPI);
         break;
       }
       ptx::tc_fence_after();
       const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(DRAIN ? b * BN : b * 2 * BN);
       int m0, tx0, ty0;
-      tile_of(u, m0, tx0, ty0);
+      tile_of(g, lu, m0, tx0, ty0);
       const int ii = m0 + row;
       const bool row_in = ii < g.M;  // the last M block may extend past the owner rows
-      const float oscale = pow2f(-((row_in ? g.eP[ii] : 0) + g.escale[g.parity]));
+      const float oscale = pow2f(-((row_in ? g.eP[ii] : 0) + g.escale[parity]));
       const int iy = row_in ? ii / g.Tx : 0, ix = row_in ? ii % g.Tx : 0;
       const int rowbase = iy * g.nx + ix;
+      float* __restrict__ uh = g.uh;
+      float* __restrict__ ul = g.ul;
       // one batch of 16 windows: y = (main + corr) 2^-(eP_i + er) added into the owner nodes
       auto batch = [&](int q, const float (&vm)[16], const float (&vc)[16]) {
         // all 32 state loads of this batch go out before any store (the stores go through
@@ -606,13 +719,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   if (MC) ptx::cluster_sync();  // no CTA leaves while a partner may still signal it
 }
 
-using GemmKernel = void (*)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, float*,
-                           float*, GemmParams);
+using GemmKernel = void (*)(SplitProblem, const SplitProblem*, int, int, int, int*);
+
+int gemm_threads(int) { return GEMM_THREADS; }
 
 // The instantiated (cluster, tile width, pieces) combinations: BN 256 with two pieces for
 // large tile grids, BN 128 otherwise.
-int gemm_threads(int) { return GEMM_THREADS; }
-
 GemmKernel gemm_kernel_for(bool mc, int bn, int np) {
   if (np == 3) return mc ? split_gemm_kernel<true, 128, 3> : split_gemm_kernel<false, 128, 3>;
   if (bn == 256) return mc ? split_gemm_kernel<true, 256, 2> : split_gemm_kernel<false, 256, 2>;
@@ -642,18 +754,26 @@ struct SplitPlan {
   unsigned* d_rmax = nullptr;
   int* d_escale = nullptr;
   int* d_err = nullptr;
-  CUtensorMap tm[6];  // P_int, P2, P3, r_int, r2, r3 (half boxes when clustered; pieces 3 unused with np = 2)
+  SplitProblem prob{};       // tensor maps (half boxes when clustered) and GEMM geometry
+  SplitProblem prob_flat{};  // the same with whole boxes, for launches without clusters
   int packed_gen = -1;
 };
 
-// Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn and
-// BNx a power of two no wider than the grid; blocks may overhang the grid at its right and
-// bottom edges (TMA zero-fills those windows and the epilogue skips them).
-static void group_tiles(int64_t ntx, int bn, int* bnx, int* bny) {
-  int x = 1;
-  while (x * 2 <= bn && x * 2 <= ntx) x *= 2;
-  *bnx = x;
-  *bny = bn / x;
+// Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn (both
+// powers of two). Blocks may overhang the grid at its right and bottom edges (TMA zero-fills
+// those windows and the epilogue skips them), so the shape with the fewest blocks wins (ties:
+// the wider one).
+static void group_tiles(int64_t ntx, int64_t nty, int bn, int* bnx, int* bny) {
+  int64_t best = -1;
+  for (int x = bn; x >= 1; x /= 2) {
+    const int y = bn / x;
+    const int64_t blocks = ((ntx + x - 1) / x) * ((nty + y - 1) / y);
+    if (best < 0 || blocks < best) {
+      best = blocks;
+      *bnx = x;
+      *bny = y;
+    }
+  }
 }
 
 bool split_eligible(const lem_ctx* ctx) {
@@ -714,7 +834,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   // 256-wide tiles when they do not waste more than they save on mostly-empty edge blocks
   // (two pieces only: a stage of three 256-wide pieces leaves room for one stage)
   sp->bn = sp->np == 2 && int64_t(sp->ntx) * sp->nty >= 1024 ? 256 : 128;
-  group_tiles(sp->ntx, sp->bn, &sp->BNx, &sp->BNy);
+  group_tiles(sp->ntx, sp->nty, sp->bn, &sp->BNx, &sp->BNy);
   sp->nbx = int((sp->ntx + sp->BNx - 1) / sp->BNx);
   sp->nby = int((sp->nty + sp->BNy - 1) / sp->BNy);
   LEM_CUDA_TRY(cudaDeviceGetAttribute(&sp->nsm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -794,8 +914,11 @@ lem_status split_prepare(lem_ctx* ctx) {
   }
   // tensor maps: P slices [M][Wy*64] fp16 (2D, box 64 x rows); residual slices through a 4D
   // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx]
-  {
-    const bool mc = sp->clusters > 0;
+  for (int variant = 0; variant < 2; ++variant) {
+    // variant 0: the maps the single-problem launch uses (half boxes when clustered);
+    // variant 1: whole boxes, for multi-problem launches (never clustered)
+    const bool mc = variant == 0 && sp->clusters > 0;
+    SplitProblem& pr = variant == 0 ? sp->prob : sp->prob_flat;
     // with two pieces the third maps alias the second (never loaded)
     __half* pbase[3] = {sp->d_Pint, sp->d_P2, sp->np == 3 ? sp->d_P3 : sp->d_P2};
     __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
@@ -810,10 +933,20 @@ lem_status split_prepare(lem_ctx* ctx) {
       else rbox[1] /= 2;
     }
     for (int k = 0; k < 3; ++k) {
-      LEM_TRY(encode(&sp->tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
-      LEM_TRY(encode(&sp->tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
+      LEM_TRY(encode(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
+      LEM_TRY(encode(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
     }
   }
+  GemmGeom& g = sp->prob.g;
+  g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
+  g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx; g.nty = sp->nty; g.M = sp->M;
+  g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
+  // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
+  // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
+  g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
+  g.unit0 = 0;
+  g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
+  sp->prob_flat.g = g;
   cudaFuncAttributes fa{};
   LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(false, sp->bn, sp->np)));
   if (fa.maxThreadsPerBlock < gemm_threads(sp->np))
@@ -858,13 +991,7 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
                                                sp->d_rmax, sp->d_escale, 1, 1);
   LEM_CUDA_TRY(cudaGetLastError());
-  GemmParams g{};
-  g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
-  g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx;
-  g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
-  g.M = sp->M;
-  g.nty = sp->nty; g.nbx = sp->nbx;
-  g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.err = sp->d_err;
+  const GemmGeom& g = sp->prob.g;
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(gemm_threads(sp->np));
@@ -883,16 +1010,155 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
     const int parity = k & 1;
     residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
                                                  sp->d_rmax, sp->d_escale, parity, 0);
-    g.parity = parity;
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->clusters > 0, sp->bn, sp->np), sp->tm[0], sp->tm[1],
-                                    sp->tm[2], sp->tm[3], sp->tm[4], sp->tm[5], sp->d_uh, sp->d_ul, g));
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->clusters > 0, sp->bn, sp->np), sp->prob,
+                                    static_cast<const SplitProblem*>(nullptr), 1, 0, parity, sp->d_err));
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
   ff_to_f64_kernel<<<1024, 256, 0, st>>>(sp->d_uh, sp->d_ul, d_u, npts);
   LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
+// ------------------------------------------------------------------ multi-problem steps
+// Every problem of a batch advances one LEM step with one residual launch and one persistent
+// GEMM launch (units of all problems, the heaviest problems' units first).
+struct SplitBatch {
+  int n = 0, np = 2, bn = 128, nunits = 0, res_blocks = 0, conv_blocks = 0, grid = 0;
+  SplitProblem first{};  // by-value kernel argument (unused when the array is given)
+  SplitProblem* d_probs = nullptr;
+  ResProblem* d_res = nullptr;
+  int* d_res_first = nullptr;
+  ConvProblem* d_conv = nullptr;
+  int* d_conv_first = nullptr;
+  int* d_err = nullptr;
+};
+
+bool split_batch_eligible(lem_ctx* const* ctxs, int n) {
+  if (n <= 0 || !ctxs[0]->split) return false;
+  for (int i = 0; i < n; ++i) {
+    const SplitPlan* sp = ctxs[i]->split;
+    if (!sp || sp->np != ctxs[0]->split->np || sp->bn != ctxs[0]->split->bn) return false;
+    if (ctxs[i]->device != ctxs[0]->device) return false;
+  }
+  return true;
+}
+
+void split_batch_destroy(SplitBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_probs); cudaFree(b->d_res); cudaFree(b->d_res_first);
+  cudaFree(b->d_conv); cudaFree(b->d_conv_first); cudaFree(b->d_err);
+  delete b;
+}
+
+lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, SplitBatch** out) {
+  *out = nullptr;
+  if (!split_batch_eligible(ctxs, n)) return fail(LEM_EINVAL, "batch is not one tensor-core split tier");
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->split->packed_gen != ctxs[i]->build_gen) return fail(LEM_ENOTREADY, "split propagator not packed");
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto work = [&](int i) {
+    const SplitPlan* sp = ctxs[i]->split;
+    return int64_t(sp->Wy) * ((sp->Wx + 15) / 16);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work(a) > work(c); });
+  SplitBatch* b = new SplitBatch();
+  b->n = n;
+  b->np = ctxs[0]->split->np;
+  b->bn = ctxs[0]->split->bn;
+  std::vector<SplitProblem> probs(n);
+  std::vector<ResProblem> res(n);
+  std::vector<ConvProblem> conv(n);
+  std::vector<int> res_first(n), conv_first(n);
+  for (int k = 0; k < n; ++k) {
+    const lem_ctx* c = ctxs[order[k]];
+    const SplitPlan* sp = c->split;
+    probs[k] = sp->prob_flat;
+    probs[k].g.unit0 = b->nunits;
+    b->nunits += sp->prob.g.nMB * sp->prob.g.nNB;
+    ResProblem& r = res[k];
+    r.p = sp->rp;
+    r.uh = sp->d_uh; r.ul = sp->d_ul; r.Rint = sp->d_Rint; r.R2 = sp->d_R2; r.R3 = sp->d_R3;
+    r.rmax = sp->d_rmax; r.escale = sp->d_escale;
+    r.gx = (int(c->nx) + 2 * sp->Hx + RT - 1) / RT;
+    r.block0 = res_first[k] = b->res_blocks;
+    b->res_blocks += r.gx * ((sp->prow + RT - 1) / RT);
+    ConvProblem& v = conv[k];
+    v.u = d_states[order[k]]; v.uh = sp->d_uh; v.ul = sp->d_ul; v.rmax = sp->d_rmax; v.n = c->npts;
+    v.block0 = conv_first[k] = b->conv_blocks;
+    b->conv_blocks += int((c->npts + CONV_CHUNK - 1) / CONV_CHUNK);
+  }
+  b->first = probs[0];
+  b->grid = std::min(b->nunits, ctxs[0]->split->nsm);
+  auto upload = [&](void** d, const void* h, size_t bytes) -> lem_status {
+    if (cudaMalloc(d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LEM_ENOMEM, "batch tables");
+    }
+    LEM_CUDA_TRY(cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice));
+    return LEM_OK;
+  };
+  lem_status st = upload(reinterpret_cast<void**>(&b->d_probs), probs.data(), sizeof(SplitProblem) * n);
+  if (st == LEM_OK) st = upload(reinterpret_cast<void**>(&b->d_res), res.data(), sizeof(ResProblem) * n);
+  if (st == LEM_OK) st = upload(reinterpret_cast<void**>(&b->d_res_first), res_first.data(), sizeof(int) * n);
+  if (st == LEM_OK) st = upload(reinterpret_cast<void**>(&b->d_conv), conv.data(), sizeof(ConvProblem) * n);
+  if (st == LEM_OK) st = upload(reinterpret_cast<void**>(&b->d_conv_first), conv_first.data(), sizeof(int) * n);
+  const int zero = 0;
+  if (st == LEM_OK) st = upload(reinterpret_cast<void**>(&b->d_err), &zero, sizeof(int));
+  if (st != LEM_OK) {
+    split_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return LEM_OK;
+}
+
+lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEvent_t* ev) {
+  // ev (not under capture): 2 * nsteps + 2 events bracketing [conversion + measure],
+  // then each step's residual and GEMM
+  convert_multi_kernel<<<b->conv_blocks, 256, 0, st>>>(b->d_conv, b->d_conv_first, b->n, 1);
+  residual_multi_kernel<<<b->res_blocks, 256, 0, st>>>(b->d_res, b->d_res_first, b->n, 1, 1);
+  LEM_CUDA_TRY(cudaGetLastError());
+  if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3(gemm_threads(b->np));
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = st;
+  cfg.gridDim = dim3(b->grid);
+  for (int k = 0; k < nsteps; ++k) {
+    const int parity = k & 1;
+    residual_multi_kernel<<<b->res_blocks, 256, 0, st>>>(b->d_res, b->d_res_first, b->n, parity, 0);
+    if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[1 + 2 * k], st));
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(false, b->bn, b->np), b->first,
+                                    static_cast<const SplitProblem*>(b->d_probs), b->n, b->nunits, parity, b->d_err));
+    if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[2 + 2 * k], st));
+  }
+  convert_multi_kernel<<<b->conv_blocks, 256, 0, st>>>(b->d_conv, b->d_conv_first, b->n, 0);
+  LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
+// Algorithmic FLOPs of one fused GEMM launch: products x 2 x owner rows x window nodes, summed
+// over every window of every problem.
+double split_batch_gemm_flops(const SplitBatch* b, lem_ctx* const* ctxs) {
+  double f = 0.0;
+  for (int i = 0; i < b->n; ++i) {
+    const SplitPlan* sp = ctxs[i]->split;
+    f += 2.0 * sp->np * 2.0 * sp->M * double(sp->Wy) * sp->Wx * double(sp->ntx) * sp->nty;
+  }
+  return f;
+}
+
+lem_status split_batch_check_error(SplitBatch* b) {
+  int e = 0;
+  LEM_CUDA_TRY(cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(b->d_err, 0, sizeof(int));
+    return fail(LEM_ETIMEOUT, "tensor-core kernel gave up waiting on an mbarrier (code " + std::to_string(e) + ")");
+  }
   return LEM_OK;
 }
 

@@ -88,6 +88,10 @@ SIGNATURES = [
     ("lem_batch_run", C.c_int, [C.c_void_p, C.c_int]),
     ("lem_batch_schedule", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lem_batch_destroy", None, [C.c_void_p]),
+    ("lem_batch_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("lem_batch_sync", C.c_int, [C.c_void_p]),
+    ("lem_batch_profile", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lem_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
     ("lem_submit", C.c_int, [C.c_void_p, C.POINTER(ProblemDesc), C.c_double, C.c_void_p, C.c_int,
                              C.POINTER(C.c_uint64)]),
@@ -336,6 +340,20 @@ class Batch:
         check(self._lib.lem_batch_schedule(self._h, est.ctypes.data_as(C.c_void_p), lane.ctypes.data_as(C.c_void_p)),
               "lem_batch_schedule")
         return est, lane
+
+    def info(self):
+        f, lm, fm = C.c_int(), C.c_double(), C.c_double()
+        check(self._lib.lem_batch_info(self._h, C.byref(f), C.byref(lm), C.byref(fm)), "lem_batch_info")
+        return {"fused": bool(f.value), "lanes_ms": lm.value, "fused_ms": fm.value}
+
+    def sync(self):
+        check(self._lib.lem_batch_sync(self._h), "lem_batch_sync")
+
+    def profile(self, nsteps: int = 1):
+        g, r, o, f = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        check(self._lib.lem_batch_profile(self._h, int(nsteps), C.byref(g), C.byref(r), C.byref(o), C.byref(f)),
+              "lem_batch_profile")
+        return {"gemm_ms": g.value, "residual_ms": r.value, "other_ms": o.value, "gemm_flops": f.value}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

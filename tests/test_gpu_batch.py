@@ -103,3 +103,32 @@ def test_batch_rejects_bad_arguments():
     sr = torch.tensor(v["u0"], device="cuda")
     with pytest.raises(L.LemError):
         L.Batch([cr], [sr])
+
+
+@pytest.mark.parametrize("schedule", ["fused", "lanes"])
+def test_split_batch_schedules_equal_per_problem_steps(schedule, monkeypatch):
+    """All-split batches can run fused (one residual and one persistent GEMM launch per step
+    for every problem) or on lanes; both give each problem exactly its own lem_step result."""
+    monkeypatch.setenv("LEM_BATCH_SCHEDULE", schedule)
+    probs = W.batch_problems(n=24, seed=7, side_max=160)
+    ref = []
+    for p in probs:
+        c = L.Lem.from_workload(p, prec="split")
+        u = torch.tensor(p["u0"], device="cuda")
+        for _ in range(2):
+            c.step(u, 3)
+        c.sync()
+        ref.append(u.cpu().numpy())
+        c.close()
+    ctxs = [L.Lem.from_workload(p, prec="split") for p in probs]
+    states = [torch.tensor(p["u0"], device="cuda") for p in probs]
+    b = L.Batch(ctxs, states, steps_per_launch=3, lanes=4)
+    info = b.info()
+    assert info["fused_ms"] > 0 and info["lanes_ms"] > 0
+    assert info["fused"] == (schedule == "fused")
+    b.run(2)
+    b.sync()
+    for i, (s, r) in enumerate(zip(states, ref)):
+        assert np.array_equal(s.cpu().numpy(), r), probs[i]["name"]
+    print(f"{schedule}: lanes {info['lanes_ms']:.3f} ms, fused {info['fused_ms']:.3f} ms per launch")
+    b.close()
