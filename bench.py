@@ -43,9 +43,12 @@ def parse():
                          "pieces (four products); fp64: the plain FP64 GPU path")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=2048)
-    ap.add_argument("--workload", default="advdiff2d", choices=["advdiff2d", "batch512"],
+    ap.add_argument("--workload", default="advdiff2d", choices=["advdiff2d", "batch512", "serve"],
                     help="advdiff2d: one 2048^2 problem (default); batch512: 512 uneven problems under one "
-                         "CUDA graph")
+                         "CUDA graph; serve: a Poisson stream of advance requests through the server")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
+    ap.add_argument("--duration", type=float, default=1.0, help="serve: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=120.0, help="serve: seconds to wait for completions")
     ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
     ap.add_argument("--lanes", type=int, default=16, help="batch512: concurrent lanes in the graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -199,9 +202,51 @@ def oracle_batch_sample(nprob, inner, max_seconds=20.0):
                       f"their propagator builds took {t_build:.1f} s and are excluded"}
 
 
+def oracle_serve_sample(rate, duration, max_seconds=20.0):
+    """The FP64 oracle on a bounded sample of the request stream: the smallest requests (their
+    propagators built once per operator and excluded), each for its own number of steps."""
+    import oracle as O
+    from paper_1505_02248_gb300 import workloads as W
+    reqs = sorted(serve_requests(rate, duration), key=lambda r: int(np.prod(r["shape"])))
+    props, dofs, t_run, done = {}, 0, 0.0, 0
+    for r in reqs:
+        if t_run > max_seconds / 2 or done >= 32:
+            break
+        X = O.assemble_operator(r["shape"], r["bc"], r["coef"], r["dt"])
+        wins = O.decompose(r["shape"], r["bc"], r["tile"], r["overlap"])
+        key = (len(r["shape"]), tuple(sorted(r["coef"].items())))
+        if key not in props:
+            props[key] = O.local_propagators(X, wins, "phi", tiles=[0])[0]
+        u = (W.grf_1d(r["shape"][0], 8.0, 1) if len(r["shape"]) == 1 else W.grf_2d(r["shape"], 16.0, 1).ravel())
+        t0 = time.perf_counter()
+        for _ in range(r["steps"]):
+            u = O.lem_step(X, u, wins, [props[key]] * len(wins), "phi")
+        t_run += time.perf_counter() - t0
+        dofs += u.size * r["steps"]
+        done += 1
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": dofs / t_run, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"the {done} smallest of {len(reqs)} requests, each for its own steps (numpy FP64 oracle); "
+                      f"propagator builds excluded"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if a.workload == "serve":
+        cb = oracle_serve_sample(a.rate, a.duration)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": SERVE_WORKLOAD, "impl": "FP64 CPU oracle on a request sample"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     if a.workload == "batch512":
         per, cb = [], None
@@ -379,8 +424,123 @@ def run_batch(a):
         dist.destroy_process_group()
 
 
+SERVE_WORKLOAD = "serve_poisson_1d2d_advdiff_periodic_tiers_1e-6_1e-10"
+
+
+def serve_requests(rate, duration, seed=4, variants=8):
+    """Poisson arrivals (mean `rate` per second for `duration` s), seed 4. Half 1D (N log-uniform
+    in [256, 65536], rounded to 64, tile 64 + H 16), half 2D (side log-uniform in [128, 2048],
+    rounded to 32, tile 32 + H 8); periodic upwind advection-diffusion, h = dt = 1, drawn from
+    `variants` operators per dimension (mu ~ U[1, 20], C ~ U[0, 4], C_y = C / 2); steps U{1..50};
+    tolerance tier 1e-6 (70 %) or 1e-10 (30 %)."""
+    from paper_1505_02248_gb300 import workloads as W
+    g = W.rng(seed)
+    ops = {1: [], 2: []}
+    for dim in (1, 2):
+        for _ in range(variants):
+            mu, c = float(g.uniform(1.0, 20.0)), float(g.uniform(0.0, 4.0))
+            ops[dim].append(W.stencil_advdiff_1d(mu, c, 1.0, upwind=True) if dim == 1
+                            else W.stencil_advdiff_2d(mu, c, c / 2, 1.0))
+    t, out = 0.0, []
+    while True:
+        t += float(g.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        dim = 1 if g.random() < 0.5 else 2
+        if dim == 1:
+            n = int(round(np.exp(g.uniform(np.log(256), np.log(65536))) / 64)) * 64
+            shape, tile, H = (n,), (64,), (16,)
+        else:
+            side = int(round(np.exp(g.uniform(np.log(128), np.log(2048))) / 32)) * 32
+            shape, tile, H = (side, side), (32, 32), (8, 8)
+        out.append(dict(t=t, shape=shape, bc=("periodic",) * dim, coef=ops[dim][int(g.integers(variants))],
+                        dt=1.0, tile=tile, overlap=H, steps=int(g.integers(1, 51)),
+                        tol=1e-6 if g.random() < 0.7 else 1e-10))
+    return out
+
+
+def run_serve(a):
+    """Stream of requests through lem_server (continuous batching, 80 GB budget): submitted on
+    their Poisson arrival times, latency arrival -> result back in host memory."""
+    import torch
+    from paper_1505_02248_gb300 import lem as L
+    from paper_1505_02248_gb300 import workloads as W
+
+    L.load()
+    reqs = serve_requests(a.rate, a.duration)
+    base = {}
+    for r in reqs:  # one initial field per mesh size (a fresh copy per request)
+        if r["shape"] not in base:
+            base[r["shape"]] = (W.grf_1d(r["shape"][0], 8.0, 1) if len(r["shape"]) == 1
+                                else W.grf_2d(r["shape"], 16.0, 1).ravel())
+    states = [base[r["shape"]].copy() for r in reqs]
+    srv = L.Server(80 * 10 ** 9)
+    # warm-up: one small request per (operator, tier) builds every propagator of the catalogue
+    # (the server keeps them and lends them to every mesh size), then the counters restart
+    seen, warm = set(), []
+    for r in reqs:
+        key = (len(r["shape"]), tuple(sorted(r["coef"].items())), r["tol"])
+        if key in seen:
+            continue
+        seen.add(key)
+        shape = (256,) if len(r["shape"]) == 1 else (128, 128)
+        h = (W.grf_1d(256, 8.0, 2) if len(shape) == 1 else W.grf_2d(shape, 16.0, 2).ravel())
+        warm.append((srv.submit(shape, r["bc"], r["coef"], r["dt"], r["tile"], r["overlap"], h, 1, r["tol"]), h))
+    t_w = time.perf_counter()
+    for t, _ in warm:
+        srv.wait(t, 300.0)
+    warm_s = time.perf_counter() - t_w
+    srv.reset_stats()
+    tickets = []
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clk:
+        i = 0
+        while i < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i]["t"] <= now:
+                r = reqs[i]
+                tickets.append(srv.submit(r["shape"], r["bc"], r["coef"], r["dt"], r["tile"], r["overlap"], states[i],
+                                          r["steps"], r["tol"]))
+                i += 1
+            time.sleep(0.0002)
+        t_sub = time.perf_counter() - t0
+        while time.perf_counter() - t0 < a.duration + a.drain:
+            st = srv.stats()
+            if st["completed"] + st["failed"] >= len(reqs):
+                break
+            time.sleep(0.01)
+    st = srv.stats()
+    srv.close()
+    dofs = sum(int(np.prod(r["shape"])) * r["steps"] for r in reqs)
+    span = st["first_admit_to_last_done_s"]
+    line = {
+        "metric": METRIC, "value": st["dof_steps"] / span if span > 0 else None, "unit": METRIC, "n_gpus": 1,
+        "steps": len(reqs), "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed: f16x3-split (tier 1e-6, 2D) / f64", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "rate_per_s": a.rate, "arrival_s": a.duration,
+                   "submit_span_s": round(t_sub, 3), "requests": len(reqs), "offered_dof_steps": dofs,
+                   "budget_bytes": 80 * 10 ** 9, "operator_variants_per_dim": 8,
+                   "warmup": f"{len(warm)} one-step requests (one per operator and tier) in {warm_s:.1f} s, "
+                             "then the counters restart"},
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+        "requests": {k: st[k] for k in ("submitted", "admitted", "completed", "failed", "queued", "active")},
+        "contexts": {"hits": st["ctx_hits"], "misses": st["ctx_misses"], "adopted_propagators": st["ctx_adopted"]},
+        "worker_s": {"admit": st["worker_admit_s"], "issue": st["worker_issue_s"], "build": st["worker_build_s"],
+                     "contexts_built": st["ctx_built"], "adopt_failed": st["adopt_failed"]},
+        "gpu_launches": None,
+        "e2e": {"value": st["dof_steps"] / span if span > 0 else None, "unit": METRIC,
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "every request's state goes host -> device -> host inside its latency"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.workload == "serve" and a.impl == "ours":
+        run_serve(a)
+        return
     if a.impl == "reference":
         run_reference(a)
         return

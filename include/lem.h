@@ -256,7 +256,14 @@ typedef struct {
   double p50_ms, p99_ms;        /* submit-to-result latency of completed requests */
   double first_admit_to_last_done_s;
   int64_t device_bytes;         /* states, scratch and cached contexts held now */
-  int64_t ctx_hits, ctx_misses; /* context (propagator) cache */
+  int64_t ctx_hits, ctx_misses; /* context cache */
+  int64_t ctx_adopted;          /* new contexts that took a cached propagator of the same local
+                                   operator (another mesh size) instead of building one */
+  double worker_admit_s;        /* worker-thread time spent admitting (context creation) */
+  double worker_issue_s;        /* worker-thread time spent issuing steps (incl. first builds) */
+  double worker_build_s;        /* of worker_admit_s: building the first propagator of each operator */
+  int64_t ctx_built;            /* contexts that built at admission (first of their operator) */
+  int64_t adopt_failed;         /* contexts whose operator had a donor that did not match */
 } lem_server_stats;
 
 /* Create a server on `device` with a device-memory budget in bytes (states, scratch and cached
@@ -279,6 +286,10 @@ lem_status lem_poll(lem_server* srv, uint64_t ticket, int* done);
 lem_status lem_wait(lem_server* srv, uint64_t ticket, double timeout_s);
 
 lem_status lem_server_get_stats(lem_server* srv, lem_server_stats* out);
+
+/* Zero the counters, timers and latency record (after a warm-up, say); requests in flight
+ * are still counted when they complete. Cached contexts and propagators stay. */
+lem_status lem_server_reset_stats(lem_server* srv);
 
 /* Stop the worker after the admitted requests finish (queued ones are failed with LEM_EBUSY),
  * free everything. */

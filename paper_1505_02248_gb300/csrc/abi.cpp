@@ -116,6 +116,38 @@ lem_status init_plan(lem_ctx* c, const lem_problem_desc* desc) {
 
 }  // namespace
 
+namespace lem {
+
+// Take the propagators of `src` instead of building them: both contexts have one class whose
+// local matrix is the same (same stencil, dt, tile, overlap, mode and window shape; the mesh
+// size may differ, which does not change a window that does not wrap onto itself). `built` is
+// an event recorded on src's stream after its build: dst's stream waits for it, the host
+// does not.
+lem_status adopt_propagators(lem_ctx* dst, lem_ctx* src, cudaEvent_t built) {
+  if (!dst || !src || !src->built) return fail(LEM_EINVAL, "no built donor");
+  if (dst->classes.size() != 1 || src->classes.size() != 1) return fail(LEM_EINVAL, "donor needs one class");
+  const ClassDesc &a = dst->classes[0], &b = src->classes[0];
+  const lem_problem_desc &da = dst->desc, &db = src->desc;
+  bool same = da.ndim == db.ndim && da.mode == db.mode && da.dt == db.dt && da.reaction == 0 && db.reaction == 0 &&
+              da.coef_stride == 0 && db.coef_stride == 0 && dst->n_loc == src->n_loc && dst->n_int == src->n_int;
+  for (int k = 0; k < da.ndim && same; ++k)  // per mesh axis (a 1D problem has one)
+    same = da.tile[k] == db.tile[k] && da.overlap[k] == db.overlap[k] && da.bc[k] == db.bc[k] &&
+           a.wext[k] == b.wext[k] && a.iext[k] == b.iext[k] && a.iofs[k] == b.iofs[k] && !a.whole[k] && !b.whole[k];
+  DeviceGuard g(dst->device);
+  same = same && dst->h_coef == src->h_coef;  // the dt-scaled constant stencils
+  if (!same) return fail(LEM_EINVAL, "donor has a different local operator");
+  LEM_CUDA_TRY(cudaStreamWaitEvent(dst->stream, built, 0));
+  LEM_CUDA_TRY(cudaMemcpyAsync(dst->d_P, src->d_P, sizeof(double) * dst->n_int * dst->n_loc,
+                               cudaMemcpyDeviceToDevice, dst->stream));
+  dst->squarings = src->squarings;
+  dst->built = true;
+  dst->build_gen++;
+  dst->steps_since_build = 0;
+  return LEM_OK;
+}
+
+}  // namespace lem
+
 extern "C" {
 
 const char* lem_status_str(lem_status s) {
@@ -185,6 +217,7 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_r), sizeof(double) * c->npts);
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
   if (s != LEM_OK) { free_ctx(c); return s; }
+  if (!desc->coef_stride) c->h_coef = hc;
   e = cudaMemcpy(c->d_coef, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * nt, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->d_class_order, c->class_order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice);

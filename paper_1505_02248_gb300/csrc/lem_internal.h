@@ -83,6 +83,7 @@ struct lem_ctx {
   std::vector<lem::ClassDesc> classes;
   std::vector<int32_t> class_order;    // tiles sorted by class
   std::vector<int32_t> class_offset;   // start of each class in class_order (nclasses+1)
+  std::vector<double> h_coef;          // dt-scaled constant stencil (C, W, E, S, N); empty if per node
   std::vector<int> squarings;          // per class, after the build
   int64_t n_loc = 0, n_int = 0;        // padded window / tile sizes
   bool built = false;
@@ -137,6 +138,8 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
 double split_batch_gemm_flops(const SplitBatch* b, lem_ctx* const* ctxs);
 lem_status split_batch_check_error(SplitBatch* b);
 void split_batch_destroy(SplitBatch* b);
+// abi.cpp: take a built single-class propagator from a context with the same local operator
+lem_status adopt_propagators(lem_ctx* dst, lem_ctx* src, cudaEvent_t built);
 // allocation helper that tracks bytes
 lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes);
 }  // namespace lem

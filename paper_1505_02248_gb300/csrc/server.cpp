@@ -45,7 +45,8 @@ struct Request {
   uint64_t id = 0;
   lem_problem_desc desc{};
   std::vector<double> coef[5];
-  std::string key;
+  std::string key;     // problem identity (context cache)
+  std::string op_key;  // local operator identity (propagator sharing across mesh sizes)
   double tol = 0.0;
   double* h_state = nullptr;
   int64_t npts = 0;
@@ -53,6 +54,8 @@ struct Request {
   RS state = RS::Queued;
   lem_status status = LEM_OK;
   double* d_state = nullptr;
+  double* h_stage = nullptr;  // pinned staging copy of the state (asynchronous transfers)
+  size_t stage_bytes = 0;
   CachedCtx* cc = nullptr;
   cudaEvent_t ev = nullptr;
   bool in_flight = false;
@@ -66,11 +69,12 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
   return h;
 }
 
-// Problem identity for the propagator cache (everything but the state).
-std::string make_key(const lem_problem_desc& d, const std::vector<double>* coef) {
+// Problem identity for the context cache (everything but the state); with_n = false gives the
+// local operator's identity, shared by meshes of every size.
+std::string make_key(const lem_problem_desc& d, const std::vector<double>* coef, bool with_n = true) {
   uint64_t h = 1469598103934665603ull;
   h = fnv1a(&d.ndim, sizeof d.ndim, h);
-  h = fnv1a(d.n, sizeof d.n, h);
+  if (with_n) h = fnv1a(d.n, sizeof d.n, h);
   h = fnv1a(d.bc, sizeof d.bc, h);
   h = fnv1a(&d.coef_stride, sizeof d.coef_stride, h);
   h = fnv1a(&d.reaction, sizeof d.reaction, h);
@@ -94,13 +98,22 @@ struct lem_server {
   std::deque<std::shared_ptr<Request>> queue;
   std::vector<std::shared_ptr<Request>> active;  // worker-owned
   std::map<std::string, std::unique_ptr<CachedCtx>> cache;
+  // pinned host buffers by size class (powers of two), reused across requests: transfers from
+  // pageable memory would block the worker until the context's stream drains
+  std::map<size_t, std::vector<void*>> stage_pool;
+  int64_t stage_bytes_held = 0;
+  // a built one-class context per local operator, with an event recorded after its build
+  std::map<std::string, std::pair<lem_ctx*, cudaEvent_t>> donors;
   int64_t used = 0;
   uint64_t next_id = 1, tick = 0;
   std::atomic<bool> stop{false};
   std::thread worker;
   // statistics
   int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, dof_steps = 0;
-  int64_t ctx_hits = 0, ctx_misses = 0;
+  int64_t ctx_hits = 0, ctx_misses = 0, ctx_adopted = 0;
+  double admit_s = 0.0, issue_s = 0.0;  // worker host time in admission and in step launches
+  double build_s = 0.0;                  // of admit_s: building donor propagators
+  int64_t ctx_built = 0, adopt_failed = 0;
   std::vector<double> lat_ms;
   bool any_admitted = false;
   Clock::time_point t_first_admit, t_last_done;
@@ -108,11 +121,48 @@ struct lem_server {
 
 namespace {
 
+constexpr int64_t kStagePoolMax = int64_t(16) << 30;  // pinned bytes kept for reuse
+
+void* stage_get(lem_server* s, size_t bytes, size_t* cls) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  *cls = c;
+  auto& v = s->stage_pool[c];
+  if (!v.empty()) {
+    void* p = v.back();
+    v.pop_back();
+    s->stage_bytes_held -= int64_t(c);
+    return p;
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void stage_put(lem_server* s, void* p, size_t cls) {
+  if (!p) return;
+  if (s->stage_bytes_held + int64_t(cls) > kStagePoolMax) {
+    cudaFreeHost(p);
+    return;
+  }
+  s->stage_pool[cls].push_back(p);
+  s->stage_bytes_held += int64_t(cls);
+}
+
 void finish(lem_server* s, const std::shared_ptr<Request>& r, lem_status st) {
   if (r->ev) { cudaEventDestroy(r->ev); r->ev = nullptr; }
   if (r->d_state) {
-    cudaFree(r->d_state);
+    // stream-ordered: a plain cudaFree would wait for every stream of the device
+    cudaFreeAsync(r->d_state, r->cc ? r->cc->stream : nullptr);
     r->d_state = nullptr;
+  }
+  if (r->h_stage) {
+    if (st == LEM_OK) std::memcpy(r->h_state, r->h_stage, sizeof(double) * size_t(r->npts));
+    stage_put(s, r->h_stage, r->stage_bytes);  // worker thread only
+    r->h_stage = nullptr;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (r->accounted) {
@@ -138,7 +188,9 @@ void finish(lem_server* s, const std::shared_ptr<Request>& r, lem_status st) {
   }
 }
 
-int64_t ctx_bytes_estimate(const lem_problem_desc& d) {
+// Device bytes a context keeps (*scratch: the builder's transient workspace, freed after the
+// build, which only a context that builds needs on top).
+int64_t ctx_bytes_estimate(const lem_problem_desc& d, int64_t* scratch) {
   int64_t nt = 0, nc = 0, nl = 0, ni = 0;
   if (lem_plan_query(&d, &nt, &nc, &nl, &ni, nullptr) != LEM_OK) return -1;
   const int64_t npts = d.ndim == 1 ? d.n[0] : d.n[0] * d.n[1];
@@ -148,7 +200,8 @@ int64_t ctx_bytes_estimate(const lem_problem_desc& d) {
   // transient builder scratch (freed after the build): 19 n_loc^2 doubles per class batch
   const int64_t per = 19 * nl * nl * 8;
   const int64_t batch = std::max<int64_t>(1, std::min<int64_t>(nc, (int64_t(8) << 30) / std::max<int64_t>(per, 1)));
-  return b + per * batch;
+  *scratch = per * batch;
+  return b;
 }
 
 // Admit r if its state (and a new context, when it needs one) fits the budget. Returns
@@ -172,11 +225,18 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
         break;
       }
     }
-    const int64_t need = ctx_bytes_estimate(d);
-    if (need < 0) {
+    int64_t scratch = 0;
+    const int64_t keep = ctx_bytes_estimate(d, &scratch);
+    if (keep < 0) {
       finish(s, r, LEM_EINVAL);
       return true;
     }
+    bool has_donor;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      has_donor = s->donors.count(r->op_key) > 0;
+    }
+    const int64_t need = keep + (has_donor ? 0 : scratch);  // room needed now
     if (need + sbytes > s->budget) {  // larger than the whole budget
       if (attempt == 0) continue;
       finish(s, r, LEM_ENOMEM);
@@ -184,13 +244,34 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      // evict idle contexts, least recently used first, until the new one fits
+      // evict idle contexts, least recently used first (contexts that lend their propagators
+      // to later ones last), until the new one fits
+      auto is_donor = [&](const lem_ctx* c) {
+        for (auto& kv : s->donors)
+          if (kv.second.first == c) return true;
+        return false;
+      };
       while (s->used + need + sbytes > s->budget) {
         auto victim = s->cache.end();
-        for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
-          if (it->second->users == 0 && (victim == s->cache.end() || it->second->last_use < victim->second->last_use))
+        bool victim_donor = true;
+        for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
+          if (it->second->users != 0) continue;
+          const bool dn = is_donor(it->second->ctx);
+          if (victim == s->cache.end() || (victim_donor && !dn) ||
+              (victim_donor == dn && it->second->last_use < victim->second->last_use)) {
             victim = it;
+            victim_donor = dn;
+          }
+        }
         if (victim == s->cache.end()) break;
+        for (auto d = s->donors.begin(); d != s->donors.end();) {
+          if (d->second.first == victim->second->ctx) {
+            cudaEventDestroy(d->second.second);
+            d = s->donors.erase(d);
+          } else {
+            ++d;
+          }
+        }
         lem_destroy(victim->second->ctx);
         cudaStreamDestroy(victim->second->stream);
         s->used -= victim->second->bytes;
@@ -211,9 +292,39 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
       finish(s, r, st);
       return true;
     }
-    c->bytes = need;
+    c->bytes = keep;
+    {
+      // a context with the same local operator (another mesh size) lends its propagators
+      std::pair<lem_ctx*, cudaEvent_t> donor{nullptr, nullptr};
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->donors.find(r->op_key);
+        if (it != s->donors.end()) donor = it->second;
+      }
+      if (donor.first && lem::adopt_propagators(c->ctx, donor.first, donor.second) == LEM_OK) {
+        s->ctx_adopted++;
+      } else if (donor.first) {
+        s->adopt_failed++;
+      } else if (c->ctx->classes.size() == 1) {
+        // first context of this local operator: build now and lend the result to later ones
+        // (other mesh sizes, the other precision tier)
+        const auto tb = Clock::now();
+        const lem_status bs = lem_build_propagators(c->ctx, nullptr);
+        s->build_s += std::chrono::duration<double>(Clock::now() - tb).count();
+        s->ctx_built++;
+        cudaEvent_t built = nullptr;
+        if (bs == LEM_OK && cudaEventCreateWithFlags(&built, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventRecord(built, c->stream) == cudaSuccess) {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->donors.emplace(r->op_key, std::make_pair(c->ctx, built));
+        } else {
+          cudaGetLastError();
+          if (built) cudaEventDestroy(built);
+        }
+      }
+    }
     std::lock_guard<std::mutex> lk(s->mu);
-    s->used += need;
+    s->used += keep;
     s->ctx_misses++;
     cc = c.get();
     s->cache[key] = std::move(c);
@@ -222,7 +333,7 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
     finish(s, r, LEM_EINVAL);
     return true;
   }
-  if (cudaMalloc(&r->d_state, size_t(sbytes)) != cudaSuccess) {
+  if (cudaMallocAsync(reinterpret_cast<void**>(&r->d_state), size_t(sbytes), cc->stream) != cudaSuccess) {
     cudaGetLastError();
     r->d_state = nullptr;
     finish(s, r, LEM_ENOMEM);
@@ -233,7 +344,13 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
     finish(s, r, LEM_ECUDA);
     return true;
   }
-  cudaMemcpyAsync(r->d_state, r->h_state, size_t(sbytes), cudaMemcpyHostToDevice, cc->stream);
+  r->h_stage = static_cast<double*>(stage_get(s, size_t(sbytes), &r->stage_bytes));
+  if (!r->h_stage) {
+    finish(s, r, LEM_ENOMEM);
+    return true;
+  }
+  std::memcpy(r->h_stage, r->h_state, size_t(sbytes));
+  cudaMemcpyAsync(r->d_state, r->h_stage, size_t(sbytes), cudaMemcpyHostToDevice, cc->stream);
   std::lock_guard<std::mutex> lk(s->mu);
   s->used += sbytes;
   r->accounted = true;
@@ -262,7 +379,10 @@ void worker_loop(lem_server* s) {
         if (s->queue.empty()) break;
         r = s->queue.front();
       }
-      if (!try_admit(s, r)) break;
+      const auto ta = Clock::now();
+      const bool admitted = try_admit(s, r);
+      s->admit_s += std::chrono::duration<double>(Clock::now() - ta).count();
+      if (!admitted) break;
       {
         std::lock_guard<std::mutex> lk(s->mu);
         s->queue.pop_front();
@@ -275,12 +395,14 @@ void worker_loop(lem_server* s) {
       if (r->state != RS::Running && r->state != RS::CopyBack) continue;
       if (!r->in_flight) {
         if (r->state == RS::Running && r->remaining == 0) {
-          cudaMemcpyAsync(r->h_state, r->d_state, sizeof(double) * size_t(r->npts), cudaMemcpyDeviceToHost,
+          cudaMemcpyAsync(r->h_stage, r->d_state, sizeof(double) * size_t(r->npts), cudaMemcpyDeviceToHost,
                           r->cc->stream);
           r->state = RS::CopyBack;
         } else {
           const int chunk = std::min(r->remaining, kChunk);
+          const auto ti = Clock::now();
           lem_status st = lem_step(r->cc->ctx, r->d_state, chunk);
+          s->issue_s += std::chrono::duration<double>(Clock::now() - ti).count();
           if (st != LEM_OK) { finish(s, r, st); progress = true; continue; }
           r->pending = chunk;
         }
@@ -295,7 +417,7 @@ void worker_loop(lem_server* s) {
       progress = true;
       if (q != cudaSuccess) { cudaGetLastError(); finish(s, r, LEM_ECUDA); continue; }
       if (r->state == RS::CopyBack) {
-        finish(s, r, lem_sync(r->cc->ctx));
+        finish(s, r, lem::split_check_error(r->cc->ctx));  // the event covers this request's work
       } else {
         r->remaining -= r->pending;
         r->pending = 0;
@@ -332,6 +454,17 @@ lem_status lem_server_create(size_t hbm_budget_bytes, int device, lem_server** o
   lem_server* s = new lem_server();
   s->device = device;
   s->budget = int64_t(hbm_budget_bytes ? hbm_budget_bytes : kDefaultBudget);
+  {
+    // request states come from the device's stream-ordered pool; keep freed blocks in it
+    // (up to the budget) instead of returning them to the driver at every synchronisation
+    lem::DeviceGuard g(device);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = uint64_t(s->budget);
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   s->worker = std::thread(worker_loop, s);
   *out = s;
   return LEM_OK;
@@ -352,6 +485,7 @@ lem_status lem_submit(lem_server* s, const lem_problem_desc* desc, double tol, d
   for (int k = 0; k < ncoef; ++k) r->coef[k].assign(desc->coef[k], desc->coef[k] + per);
   for (int k = 0; k < 5; ++k) r->desc.coef[k] = nullptr;
   r->key = make_key(r->desc, r->coef);
+  r->op_key = make_key(r->desc, r->coef, false);
   r->tol = tol;
   r->h_state = h_state;
   r->npts = npts;
@@ -389,6 +523,17 @@ lem_status lem_wait(lem_server* s, uint64_t ticket, double timeout_s) {
   }
 }
 
+lem_status lem_server_reset_stats(lem_server* s) {
+  if (!s) return lem::fail(LEM_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->submitted = s->admitted = s->completed = s->failed = s->dof_steps = 0;
+  s->ctx_hits = s->ctx_misses = s->ctx_adopted = s->ctx_built = s->adopt_failed = 0;
+  s->admit_s = s->issue_s = s->build_s = 0.0;
+  s->lat_ms.clear();
+  s->any_admitted = false;
+  return LEM_OK;
+}
+
 lem_status lem_server_get_stats(lem_server* s, lem_server_stats* o) {
   if (!s || !o) return lem::fail(LEM_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
@@ -416,6 +561,12 @@ lem_status lem_server_get_stats(lem_server* s, lem_server_stats* o) {
   o->device_bytes = s->used;
   o->ctx_hits = s->ctx_hits;
   o->ctx_misses = s->ctx_misses;
+  o->ctx_adopted = s->ctx_adopted;
+  o->worker_admit_s = s->admit_s;
+  o->worker_issue_s = s->issue_s;
+  o->worker_build_s = s->build_s;
+  o->ctx_built = s->ctx_built;
+  o->adopt_failed = s->adopt_failed;
   return LEM_OK;
 }
 
@@ -431,6 +582,11 @@ void lem_server_destroy(lem_server* s) {
     cudaStreamDestroy(kv.second->stream);
   }
   s->cache.clear();
+  for (auto& kv : s->donors) cudaEventDestroy(kv.second.second);
+  s->donors.clear();
+  for (auto& kv : s->stage_pool)
+    for (void* p : kv.second) cudaFreeHost(p);
+  s->stage_pool.clear();
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
 }

@@ -73,7 +73,7 @@ constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int P_INT_BITS = 9;            // |P_int| <= 2^9
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
 
-enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3 };
+enum : int { ERR_TIMEOUT_PRODUCER = 1, ERR_TIMEOUT_MMA = 2, ERR_TIMEOUT_EPI = 3, ERR_NUMERIC = 4 };
 
 // Geometry of one problem's GEMM (all counts in tiles unless stated).
 struct GemmGeom {
@@ -103,7 +103,7 @@ struct ResParams {
   int ny, nx, Hy, Hx, pitch, prow;
   float c_hi[5], c_lo[5];   // dt-scaled C, W, E, S, N as float pairs
   float csum_hi, csum_lo;   // sum of all five
-  int rb;                   // |r_int| target 2^(rb-1) (2x headroom below 2^rb)
+  const int* rb;            // device: |r_int| target 2^(rb-1) (2x headroom below 2^rb), set at packing
   int has_lo;               // some coefficient (or their sum) is not exact in float
 };
 
@@ -164,7 +164,7 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
   __shared__ float sh[RT + 2][RT + 3], sl[RT + 2][RT + 3];
   __shared__ float red[8];
   const float rm = __uint_as_float(rmax[parity]);
-  const int er = rm > 0.0f ? (p.rb - 1) - exponent_above(rm) : 0;
+  const int er = rm > 0.0f ? (*p.rb - 1) - exponent_above(rm) : 0;
   const float scale = pow2f(er);
   if (!measure && bx == 0 && by == 0 && threadIdx.x == 0) escale[parity] = er;
   const int x0 = bx * RT, y0 = by * RT;  // padded tile origin
@@ -373,6 +373,30 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
   if (threadIdx.x == 0) {
     eP[i] = ei;
     S[i] = red[0];
+  }
+}
+
+// rb from the packed rows' exactness sums S_i: the largest rb <= 12 with
+// max_i S_i 2^(rb+1) < 2^24 (rb <= 12: the target |r_int| <= 2^11 is an integer FP16 holds
+// exactly). Rows too heavy for rb >= 4 set the numeric error flag.
+__global__ void choose_rb_kernel(const double* __restrict__ S, int M, int* rb, int* err) {
+  __shared__ double red[256];
+  double m = 1.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) m = fmax(m, S[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int r = 0;
+    while (ldexp(red[0], r + 1) < 16777216.0 && r < 12) ++r;
+    if (r < 4) {
+      atomicExch(err, ERR_NUMERIC);
+      r = 4;
+    }
+    *rb = r;
   }
 }
 
@@ -754,6 +778,7 @@ struct SplitPlan {
   unsigned* d_rmax = nullptr;
   int* d_escale = nullptr;
   int* d_err = nullptr;
+  int* d_rb = nullptr;
   SplitProblem prob{};       // tensor maps (half boxes when clustered) and GEMM geometry
   SplitProblem prob_flat{};  // the same with whole boxes, for launches without clusters
   int packed_gen = -1;
@@ -843,8 +868,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   int need = std::max<int>(int(ctx->nx) + 2 * sp->Hx, (sp->ntx - 1) * sp->Tx + KB);
   sp->pitch = (need + 7) / 8 * 8;
   // stencil constants (dt-scaled) as float pairs
-  std::vector<double> hc(5);
-  LEM_CUDA_TRY(cudaMemcpy(hc.data(), ctx->d_coef, sizeof(double) * 5, cudaMemcpyDeviceToHost));
+  const std::vector<double>& hc = ctx->h_coef;  // dt-scaled constant stencil
   double csum = 0.0;
   for (int k = 0; k < 5; ++k) {
     csum += hc[k];
@@ -857,7 +881,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   for (int k = 0; k < 5; ++k) sp->rp.has_lo |= sp->rp.c_lo[k] != 0.0f;
   sp->rp.ny = int(ctx->ny); sp->rp.nx = int(ctx->nx); sp->rp.Hy = sp->Hy; sp->rp.Hx = sp->Hx;
   sp->rp.pitch = sp->pitch; sp->rp.prow = sp->prow;
-  sp->rp.rb = 10;  // set from the packed propagator in split_pack
+  sp->rp.rb = nullptr;  // device value, set from the packed propagator in split_pack
   const size_t npts = size_t(ctx->npts);
   const size_t rbytes = sizeof(__half) * size_t(sp->prow) * sp->pitch;
   // P slices padded to whole 128-row M blocks (zero rows past Ty*Tx)
@@ -880,6 +904,8 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_rmax), sizeof(unsigned) * 2));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_escale), sizeof(int) * 2));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_err), sizeof(int)));
+  LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_rb), sizeof(int)));
+  sp->rp.rb = sp->d_rb;
   LEM_CUDA_TRY(cudaMemset(sp->d_Pint, 0, pbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_P2, 0, pbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
@@ -962,17 +988,8 @@ static lem_status split_pack(lem_ctx* ctx) {
   cudaStream_t st = ctx->stream;
   pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->d_Pint, sp->d_P2,
                                        sp->d_P3, sp->d_eP, sp->d_S);
+  choose_rb_kernel<<<1, 256, 0, st>>>(sp->d_S, sp->M, sp->d_rb, sp->d_err);
   LEM_CUDA_TRY(cudaGetLastError());
-  std::vector<double> S(sp->M);
-  LEM_CUDA_TRY(cudaMemcpyAsync(S.data(), sp->d_S, sizeof(double) * sp->M, cudaMemcpyDeviceToHost, st));
-  LEM_CUDA_TRY(cudaStreamSynchronize(st));
-  double smax = 1.0;
-  for (double v : S) smax = std::max(smax, v);
-  int rb = 0;
-  // rb <= 12: the target |r_int| <= 2^11 is an integer FP16 holds exactly
-  while (std::ldexp(smax, rb + 1) < 16777216.0 && rb < 12) ++rb;
-  if (rb < 4) return fail(LEM_ENUMERIC, "split path: propagator rows too heavy for an exact integer product");
-  sp->rp.rb = rb;
   sp->packed_gen = ctx->build_gen;
   return LEM_OK;
 }
@@ -1157,6 +1174,7 @@ lem_status split_batch_check_error(SplitBatch* b) {
   LEM_CUDA_TRY(cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (e != 0) {
     cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == ERR_NUMERIC) return fail(LEM_ENUMERIC, "split path: propagator rows too heavy for an exact integer product");
     return fail(LEM_ETIMEOUT, "tensor-core kernel gave up waiting on an mbarrier (code " + std::to_string(e) + ")");
   }
   return LEM_OK;
@@ -1168,6 +1186,7 @@ lem_status split_check_error(lem_ctx* ctx) {
   LEM_CUDA_TRY(cudaMemcpy(&e, ctx->split->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (e != 0) {
     cudaMemset(ctx->split->d_err, 0, sizeof(int));
+    if (e == ERR_NUMERIC) return fail(LEM_ENUMERIC, "split path: propagator rows too heavy for an exact integer product");
     return fail(LEM_ETIMEOUT, "tensor-core kernel gave up waiting on an mbarrier (code " + std::to_string(e) + ")");
   }
   return LEM_OK;
@@ -1179,7 +1198,7 @@ void split_destroy(lem_ctx* ctx) {
   cudaFree(sp->d_uh); cudaFree(sp->d_ul); cudaFree(sp->d_Rint); cudaFree(sp->d_R2);
   cudaFree(sp->d_Pint); cudaFree(sp->d_P2); cudaFree(sp->d_eP); cudaFree(sp->d_S);
   cudaFree(sp->d_P3); cudaFree(sp->d_R3);
-  cudaFree(sp->d_rmax); cudaFree(sp->d_escale); cudaFree(sp->d_err);
+  cudaFree(sp->d_rmax); cudaFree(sp->d_escale); cudaFree(sp->d_err); cudaFree(sp->d_rb);
   delete sp;
   ctx->split = nullptr;
 }

@@ -61,6 +61,8 @@ class ServerStats(C.Structure):
         ("queued", C.c_int64), ("active", C.c_int64), ("dof_steps", C.c_int64),
         ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("first_admit_to_last_done_s", C.c_double),
         ("device_bytes", C.c_int64), ("ctx_hits", C.c_int64), ("ctx_misses", C.c_int64),
+        ("ctx_adopted", C.c_int64), ("worker_admit_s", C.c_double), ("worker_issue_s", C.c_double),
+        ("worker_build_s", C.c_double), ("ctx_built", C.c_int64), ("adopt_failed", C.c_int64),
     ]
 
 
@@ -93,6 +95,7 @@ SIGNATURES = [
     ("lem_batch_profile", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lem_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+    ("lem_server_reset_stats", C.c_int, [C.c_void_p]),
     ("lem_submit", C.c_int, [C.c_void_p, C.POINTER(ProblemDesc), C.c_double, C.c_void_p, C.c_int,
                              C.POINTER(C.c_uint64)]),
     ("lem_poll", C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]),
@@ -301,6 +304,9 @@ class Server:
         st = ServerStats()
         check(self._lib.lem_server_get_stats(self._h, C.byref(st)), "lem_server_get_stats")
         return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        check(self._lib.lem_server_reset_stats(self._h), "lem_server_reset_stats")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

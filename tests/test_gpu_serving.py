@@ -34,7 +34,7 @@ def _requests():
     out = []
     h = W.heat1d(n=1024)
     out.append((h, 1e-10, 9))
-    out.append((W.heat1d(n=4096, tile=64, overlap=16, seed=5), 1e-6, 12))  # 1D at 1e-6: FP32 GEMV path
+    out.append((W.heat1d(n=4096, tile=64, overlap=16, seed=5), 1e-6, 12))  # 1D at 1e-6: no tensor path, FP64
     out.append((W.advdiff2d(side=512, ell=8.0, seed=6), 1e-6, 7))          # split path
     out.append((W.advdiff2d(side=160, ell=8.0, seed=7), 1e-6, 5))          # split path, ragged blocks
     out.append((W.advdiff2d(side=256, tile=16, overlap=4, ell=8.0, seed=8), 1e-10, 6))  # FP64 tier
@@ -138,3 +138,21 @@ def test_injected_allocation_failure_reports_enomem():
         del os.environ["LEM_FAULT"]
     assert srv.status(t) == L.LEM_ENOMEM
     srv.close()
+
+
+def test_propagator_shared_across_mesh_sizes():
+    """Periodic problems with the same stencil, dt, tile and overlap have the same local
+    operator whatever the mesh size: a new context takes the cached propagator instead of
+    building it, and its result is exactly the one of a context that built its own."""
+    srv = L.Server()
+    a = W.advdiff2d(side=256, ell=8.0, seed=11)
+    b = W.advdiff2d(side=384, ell=8.0, seed=12)
+    sa, sb = a["u0"].copy(), b["u0"].copy()
+    ta = srv.submit(a["shape"], a["bc"], a["coef"], a["dt"], a["tile"], a["overlap"], sa, 3, 1e-10)
+    srv.wait(ta, 120.0)
+    tb = srv.submit(b["shape"], b["bc"], b["coef"], b["dt"], b["tile"], b["overlap"], sb, 4, 1e-10)
+    srv.wait(tb, 120.0)
+    st = srv.stats()
+    srv.close()
+    assert st["ctx_adopted"] == 1 and st["ctx_misses"] == 2
+    assert np.array_equal(sb, _alone(b, 1e-10, 4)[0])
