@@ -151,49 +151,57 @@ __device__ __forceinline__ int exponent_above(float x) {
   return e;
 }
 
-constexpr int RT = 32;  // residual output tile (padded coordinates), RT x RT per block
+constexpr int RTX = 64, RTY = 32;  // residual output tile (padded coordinates) per block
 
-// One RT x RT tile of the padded residual per 256-thread block: the (RT+2)^2 float-float
-// patch of u around it (mesh coordinates wrapped) is staged in shared memory, so each node
-// is read from global memory once per block with coalesced loads.
-// measure != 0: only accumulate max|r| into rmax[parity ^ 1] (no writes of r).
+// One RTX x RTY tile of the padded residual per 256-thread block: the (RTY+2) x (RTX+2)
+// float-float patch of u around it (mesh coordinates wrapped, any number of times for small
+// meshes) is staged in shared memory row by row, so each node is read from global memory once
+// per block. Each thread then forms the outputs of columns tx and tx + 32 in four rows, so a
+// warp's shared-memory reads and its FP16 stores are consecutive (no bank conflicts).
+// measure != 0: only accumulate max|r| into rmax[parity ^ 1].
 __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, const float* __restrict__ ul,
                                               __half* __restrict__ Rint, __half* __restrict__ R2,
                                               __half* __restrict__ R3, const ResParams& p, unsigned* rmax,
                                               int* escale, int parity, int measure, int bx, int by) {
-  __shared__ float sh[RT + 2][RT + 3], sl[RT + 2][RT + 3];
+  constexpr int SW = RTX + 3;  // staged row stride (odd: conflict-free column reads)
+  __shared__ float sh[RTY + 2][SW], sl[RTY + 2][SW];
   __shared__ float red[8];
   const float rm = __uint_as_float(rmax[parity]);
   const int er = rm > 0.0f ? (*p.rb - 1) - exponent_above(rm) : 0;
   const float scale = pow2f(er);
   if (!measure && bx == 0 && by == 0 && threadIdx.x == 0) escale[parity] = er;
-  const int x0 = bx * RT, y0 = by * RT;  // padded tile origin
+  const int x0 = bx * RTX, y0 = by * RTY;  // padded tile origin
   const int wpad = p.nx + 2 * p.Hx;
-  // stage u over padded rows y0-1 .. y0+RT and columns x0-1 .. x0+RT
-  for (int e = threadIdx.x; e < (RT + 2) * (RT + 2); e += blockDim.x) {
-    const int ly = e / (RT + 2), lx = e % (RT + 2);
-    // one wrap suffices: -Hy-1 <= y < ny + Hy + RT and Hy + RT < ny (checked at prepare)
-    int y = y0 + ly - 1 - p.Hy, x = x0 + lx - 1 - p.Hx;
-    y += y < 0 ? p.ny : (y >= p.ny ? -p.ny : 0);
-    x += x < 0 ? p.nx : (x >= p.nx ? -p.nx : 0);
-    const int c = y * p.nx + x;
-    sh[ly][lx] = uh[c];
-    sl[ly][lx] = ul[c];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  // stage u over padded rows y0-1 .. y0+RTY and columns x0-1 .. x0+RTX: the three wrapped
+  // mesh columns of this thread first, then row by row
+  int gx[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    int x = (x0 + tx + 32 * j - 1 - p.Hx) % p.nx;
+    gx[j] = x < 0 ? x + p.nx : x;
+  }
+  for (int ly = ty; ly < RTY + 2; ly += 8) {
+    int y = (y0 + ly - 1 - p.Hy) % p.ny;
+    y = y < 0 ? y + p.ny : y;
+    const float* rh = uh + int64_t(y) * p.nx;
+    const float* rl = ul + int64_t(y) * p.nx;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int lx = tx + 32 * j;
+      if (lx < RTX + 2) {
+        sh[ly][lx] = rh[gx[j]];
+        sl[ly][lx] = rl[gx[j]];
+      }
+    }
   }
   __syncthreads();
-  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;  // 32 x 8
-  const int xp = x0 + tx;
   float rabs = 0.0f;
-#pragma unroll
-  for (int k = 0; k < RT / 8; ++k) {
-    const int ly = ty + 8 * k;
-    const int yp = y0 + ly;
-    if (xp >= wpad || yp >= p.prow) continue;
-    const int cy = ly + 1, cx = tx + 1;
-    const float ch = sh[cy][cx], cl = sl[cy][cx];
+  auto one = [&](int cy, int cx) -> ffv {
     // r = sum_nbr c_j (u_j - u_C) + (sum_all c) u_C, every term and the sum in float-float:
     // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
     // about log2(|c d| / |r|) bits of r.
+    const float ch = sh[cy][cx], cl = sl[cy][cx];
     ffv acc{0.0f, 0.0f};
     const ffv dW = ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl);
     const ffv dE = ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl);
@@ -212,21 +220,38 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
       ff_mac<false>(acc, p.c_hi[4], 0.0f, dN);
       if (p.csum_hi != 0.0f) ff_mac<false>(acc, p.csum_hi, 0.0f, ffv{ch, cl});
     }
-    const ffv r = two_sum(acc.h, acc.l);  // normalised: |r.l| <= ulp(r.h) / 2
-    rabs = fmaxf(rabs, fabsf(r.h));
-    if (measure) continue;
-    // r 2^er = r_int + r2 (+ r3), split from the float-float value: r_int an integer, the
-    // remainder t + l (t exact in float) rounded to FP16 twice. Three pieces carry about
-    // rb + 22 bits, more than one float holds, so the low word takes part.
+    return two_sum(acc.h, acc.l);  // normalised: |r.l| <= ulp(r.h) / 2
+  };
+  // r 2^er = r_int + r2 (+ r3), split from the float-float value: r_int an integer, the
+  // remainder t + l (t exact in float) rounded to FP16 twice. Three pieces carry about rb + 22
+  // bits, more than one float holds, so the low word takes part.
+  auto pieces = [&](ffv r, __half& hi, __half& h2, __half& h3) {
     const float rh = __fmul_rn(r.h, scale), rl = __fmul_rn(r.l, scale);  // exact (powers of two)
-    const float ri = rintf(rh);
-    const __half hi = __float2half_rn(ri);
-    const int o = yp * p.pitch + xp;
-    Rint[o] = hi;
+    hi = __float2half_rn(rintf(rh));
     const float t = __fsub_rn(rh, __half2float(hi));  // exact (r_int may round in FP16 past 2048)
-    const __half h2 = __float2half_rn(__fadd_rn(t, rl));
-    R2[o] = h2;
-    if (R3) R3[o] = __float2half_rn(__fadd_rn(__fsub_rn(t, __half2float(h2)), rl));  // t - r2 exact
+    h2 = __float2half_rn(__fadd_rn(t, rl));
+    h3 = __float2half_rn(__fadd_rn(__fsub_rn(t, __half2float(h2)), rl));  // t - r2 exact
+  };
+#pragma unroll
+  for (int k = 0; k < RTY / 8; ++k) {
+    const int ly = ty + 8 * k;
+    const int yp = y0 + ly;
+    if (yp >= p.prow) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int lx = tx + 32 * j;
+      const int xp = x0 + lx;
+      if (xp >= wpad) continue;
+      const ffv r = one(ly + 1, lx + 1);
+      rabs = fmaxf(rabs, fabsf(r.h));
+      if (measure) continue;
+      __half h1, h2, h3;
+      pieces(r, h1, h2, h3);
+      const int64_t o = int64_t(yp) * p.pitch + xp;
+      Rint[o] = h1;
+      R2[o] = h2;
+      if (R3) R3[o] = h3;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) rabs = fmaxf(rabs, __shfl_xor_sync(0xffffffffu, rabs, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = rabs;
@@ -272,7 +297,7 @@ __device__ __forceinline__ int find_block(const int* __restrict__ first, int n, 
   return lo;
 }
 
-// The residual of every problem of a batch in one launch (one RT x RT tile per block).
+// The residual of every problem of a batch in one launch (one RTX x RTY tile per block).
 __global__ void __launch_bounds__(256) residual_multi_kernel(const ResProblem* __restrict__ rps,
                                                              const int* __restrict__ first, int nprob, int parity,
                                                              int measure) {
@@ -410,10 +435,11 @@ __global__ void choose_rb_kernel(const double* __restrict__ S, int M, int* rb, i
 // them, so every CTA issues half the TMA rows. A stage is reused only after all three CTAs
 // that write into it (self, P partner, window partner) released it. Two TMEM accumulator sets
 // alternate between tiles, so the epilogue of one tile overlaps the MMAs of the next.
-template <bool MC, int BN, int NP>
+template <bool MC, int BN, int NP, bool MULTI>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ SplitProblem one, const SplitProblem* __restrict__ many, int nprob,
                       int nunits_many, int parity, int* err) {
+  static_assert(!(MC && MULTI), "clusters pair the tiles of one problem");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = Shape<BN, NP>::STAGES, STAGE_BYTES = Shape<BN, NP>::STAGE_BYTES;
@@ -439,10 +465,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   const int unit0 = MC ? int(ptx::cluster_id_x()) : int(blockIdx.x);
   const int nunit_step = MC ? int(ptx::nclusters_x()) : int(gridDim.x);
   const int nMBu = MC ? one.g.nMB / 2 : one.g.nMB;
-  const int nunits = MC ? nMBu * (one.g.nNB / 2) : (many ? nunits_many : one.g.nMB * one.g.nNB);
-  // unit -> problem and its tile
+  const int nunits = MC ? nMBu * (one.g.nNB / 2) : (MULTI ? nunits_many : one.g.nMB * one.g.nNB);
+  // unit -> problem and its tile (one problem: the by-value parameter, addressed statically)
   auto locate = [&](int u, int& lu) -> const SplitProblem* {
-    if (!many) {
+    if constexpr (!MULTI) {
       lu = u;
       return &one;
     }
@@ -463,6 +489,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tx0 = (nb % g.nbx) * g.BNx;
     ty0 = (nb / g.nbx) * g.BNy;
   };
+  // Work items: whole units u = unit0, + step, ... (kb1 = -1: all window rows of the unit)
+  auto next_seg = [&](int64_t& cur, int& u, int& kb0, int& kb1) -> bool {
+    if (cur >= nunits) return false;
+    u = int(cur);
+    kb0 = 0;
+    kb1 = -1;
+    cur += nunit_step;
+    return true;
+  };
+  const int64_t cur0 = int64_t(unit0);
   // MC multicast masks: P partner shares the M block (differs in mh), window partner the
   // window block (differs in nh)
   const uint16_t maskP = uint16_t((1u << rank) | (1u << (rank ^ 1u)));
@@ -479,12 +515,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       ptx::mbar_init(&ce[b], EPI_WARPS);
     }
     ptx::fence_barrier_init();
-    if (!many) {
+    if (!MULTI) {
       for (int q = 0; q < 2 * NP; ++q) ptx::tma_prefetch_desc(&one.tm[q < NP ? q : 3 + q - NP]);
     }
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
-    if (!many) {
+    if (!MULTI) {
       if (blockIdx.x == 0) one.g.rmax[parity] = 0u;
     } else {
       for (int i = int(blockIdx.x); i < nprob; i += int(gridDim.x)) many[i].g.rmax[parity] = 0u;
@@ -504,13 +540,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int it = 0, issued = 0;
-      for (int u = unit0; u < nunits && !s_abort; u += nunit_step) {
+      int64_t cur = cur0;
+      int u, kb0, kb1;
+      while (!s_abort && next_seg(cur, u, kb0, kb1)) {
         int lu;
         const SplitProblem* pr = locate(u, lu);
         const GemmGeom& g = pr->g;
+        if (kb1 < 0) kb1 = g.Wy;
         int m0, tx0, ty0;
         tile_of(g, lu, m0, tx0, ty0);
-        for (int kb = 0; kb < g.Wy; ++kb, ++it) {
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t use = it / STAGES;
           if (it >= STAGES && !ptx::mbar_wait(&empty[s], (use & 1) ^ 1, WAIT_NS)) {
@@ -556,10 +595,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
       bool ok = true;
       int it = 0, lt = 0, kc = 0;
-      for (int u = unit0; u < nunits && ok; u += nunit_step, ++lt) {
+      int64_t cur = cur0;
+      int u, kb0, kb1;
+      for (; ok && next_seg(cur, u, kb0, kb1); ++lt) {
         int lu;
         const GemmGeom& g = locate(u, lu)->g;
-        const int nk = g.Wy, ksteps = (g.Wx + 15) / 16, dr = DRAIN ? g.drain_rows : 1;
+        if (kb1 < 0) kb1 = g.Wy;
+        const int ksteps = (g.Wx + 15) / 16, dr = DRAIN ? g.drain_rows : 1;
         const int b = lt % NBUF;
         if (lt >= NBUF) {
           if (!ptx::mbar_wait(&acce[b], ((lt / NBUF) - 1) & 1, WAIT_NS)) { ok = false; break; }
@@ -567,11 +609,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         const uint32_t main = DRAIN ? tmem + b * BN : tmem + b * 2 * BN;
         uint32_t corr = main + BN;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % STAGES;
           if (!ptx::mbar_wait(&full[s], (it / STAGES) & 1, WAIT_NS)) { ok = false; break; }
-          const bool group_first = DRAIN && kb % dr == 0;
-          const bool group_last = DRAIN && (kb % dr == dr - 1 || kb == nk - 1);
+          const bool group_first = DRAIN && (kb - kb0) % dr == 0;
+          const bool group_last = DRAIN && ((kb - kb0) % dr == dr - 1 || kb == kb1 - 1);
           if (group_first) {
             const int j = kc & 1;
             if (kc >= 2 && !ptx::mbar_wait(&ce[j], ((kc >> 1) - 1) & 1, WAIT_NS)) { ok = false; break; }
@@ -588,7 +630,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // ceil(Wx / 16) K steps: P is zero beyond Wx in each padded window row
           for (int kk = 0; kk < ksteps; ++kk) {
             const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
-            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
             // DRAIN: each row group starts a fresh correction sum
             const uint32_t cacc = DRAIN ? ((group_first && kk == 0) ? 0u : 1u) : acc;
             ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
@@ -624,16 +666,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int lane_base = 32 * (warp & 3);  // tcgen05.ld: a warp reaches lane quarter warp % 4
     const int row = lane_base + lane;       // TMEM lane = owner row within the M block
     int lt = 0, kc = 0;
-    for (int u = unit0; u < nunits; u += nunit_step, ++lt) {
+    int64_t cur = cur0;
+    int u, kb0, kb1;
+    for (; next_seg(cur, u, kb0, kb1); ++lt) {
       int lu;
       const GemmGeom& g = locate(u, lu)->g;
+      if (kb1 < 0) kb1 = g.Wy;
       const int b = lt % NBUF;
       float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over row groups
       if constexpr (DRAIN) {
 #pragma unroll
         for (int i = 0; i < BN; ++i) cs[i] = 0.0f;
         bool ok = true;
-        const int ngroups = (g.Wy + g.drain_rows - 1) / g.drain_rows;
+        const int ngroups = (kb1 - kb0 + g.drain_rows - 1) / g.drain_rows;
         for (int gi = 0; gi < ngroups; ++gi, ++kc) {
           const int j = kc & 1;
           if (s_abort || !ptx::mbar_wait(&cf[j], (kc >> 1) & 1, WAIT_NS)) { ok = false; break; }
@@ -749,10 +794,14 @@ int gemm_threads(int) { return GEMM_THREADS; }
 
 // The instantiated (cluster, tile width, pieces) combinations: BN 256 with two pieces for
 // large tile grids, BN 128 otherwise.
-GemmKernel gemm_kernel_for(bool mc, int bn, int np) {
-  if (np == 3) return mc ? split_gemm_kernel<true, 128, 3> : split_gemm_kernel<false, 128, 3>;
-  if (bn == 256) return mc ? split_gemm_kernel<true, 256, 2> : split_gemm_kernel<false, 256, 2>;
-  return mc ? split_gemm_kernel<true, 128, 2> : split_gemm_kernel<false, 128, 2>;
+GemmKernel gemm_kernel_for(bool mc, int bn, int np, bool multi = false) {
+  if (multi) {
+    if (np == 3) return split_gemm_kernel<false, 128, 3, true>;
+    return bn == 256 ? split_gemm_kernel<false, 256, 2, true> : split_gemm_kernel<false, 128, 2, true>;
+  }
+  if (np == 3) return mc ? split_gemm_kernel<true, 128, 3, false> : split_gemm_kernel<false, 128, 3, false>;
+  if (bn == 256) return mc ? split_gemm_kernel<true, 256, 2, false> : split_gemm_kernel<false, 256, 2, false>;
+  return mc ? split_gemm_kernel<true, 128, 2, false> : split_gemm_kernel<false, 128, 2, false>;
 }
 
 }  // namespace
@@ -812,7 +861,6 @@ bool split_eligible(const lem_ctx* ctx) {
   if (c.whole[0] || c.whole[1]) return false;
   const int Wx = Tx + 2 * Hx;
   if (Wx > KB || Tx % 8) return false;  // TMA: a window row fits one 128-byte row; 16-byte strides
-  if (ctx->ny <= d.overlap[0] + RT + 1 || ctx->nx <= Hx + RT + 1) return false;  // single-wrap staging
   return true;
 }
 
@@ -915,13 +963,17 @@ lem_status split_prepare(lem_ctx* ctx) {
   // can co-schedule clusters of 4 one-CTA-per-SM blocks.
   const int nMB = (sp->M + BM - 1) / BM, nNB = sp->nbx * sp->nby;
   const bool bsplit_y = sp->BNy % 2 == 0;
-  const bool mc_ok = nMB % 2 == 0 && nNB % 2 == 0 && (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) &&
-                     std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
+  // (two pieces only: with three, the per-row correction drain dominates and clusters measured
+  // about 2 % slower)
+  const bool mc_ok = sp->np == 2 && nMB % 2 == 0 && nNB % 2 == 0 &&
+                     (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) && std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
   sp->bsplit_y = bsplit_y ? 1 : 0;
   LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(false, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES));
   LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(true, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES));
+  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(false, sp->bn, sp->np, true),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   sp->clusters = 0;
   if (mc_ok) {
     cudaLaunchConfig_t cfg{};
@@ -970,6 +1022,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
   // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
   g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
+  if (const char* e = std::getenv("LEM_SPLIT_DRAIN_ROWS")) g.drain_rows = std::max(1, std::atoi(e));  // tuning knob
   g.unit0 = 0;
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
   sp->prob_flat.g = g;
@@ -1004,7 +1057,7 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   // measure max|r| of the first step into rmax[0] (the measuring pass reads rmax[1] only
   // to form a scale it never uses)
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
-  const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + RT - 1) / RT, (sp->prow + RT - 1) / RT);
+  const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + RTX - 1) / RTX, (sp->prow + RTY - 1) / RTY);
   residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
                                                sp->d_rmax, sp->d_escale, 1, 1);
   LEM_CUDA_TRY(cudaGetLastError());
@@ -1100,9 +1153,9 @@ lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, in
     r.p = sp->rp;
     r.uh = sp->d_uh; r.ul = sp->d_ul; r.Rint = sp->d_Rint; r.R2 = sp->d_R2; r.R3 = sp->d_R3;
     r.rmax = sp->d_rmax; r.escale = sp->d_escale;
-    r.gx = (int(c->nx) + 2 * sp->Hx + RT - 1) / RT;
+    r.gx = (int(c->nx) + 2 * sp->Hx + RTX - 1) / RTX;
     r.block0 = res_first[k] = b->res_blocks;
-    b->res_blocks += r.gx * ((sp->prow + RT - 1) / RT);
+    b->res_blocks += r.gx * ((sp->prow + RTY - 1) / RTY);
     ConvProblem& v = conv[k];
     v.u = d_states[order[k]]; v.uh = sp->d_uh; v.ul = sp->d_ul; v.rmax = sp->d_rmax; v.n = c->npts;
     v.block0 = conv_first[k] = b->conv_blocks;
@@ -1149,7 +1202,7 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
     const int parity = k & 1;
     residual_multi_kernel<<<b->res_blocks, 256, 0, st>>>(b->d_res, b->d_res_first, b->n, parity, 0);
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[1 + 2 * k], st));
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(false, b->bn, b->np), b->first,
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(false, b->bn, b->np, true), b->first,
                                     static_cast<const SplitProblem*>(b->d_probs), b->n, b->nunits, parity, b->d_err));
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[2 + 2 * k], st));
   }
