@@ -8,6 +8,8 @@
 //
 // Jacobi update: all tiles must read u^n, so in EXP mode the source is a copy of u^n and in
 // PHI mode the residual array (computed from u^n before this launch).
+#include <type_traits>
+
 #include "lem_internal.h"
 
 namespace lem {
@@ -20,12 +22,53 @@ __device__ __forceinline__ void two_sum_d(float a, float b, float& s, float& e) 
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Per-lane accumulators. FP64 rows: fused multiply-add. FP32 rows: each product split exactly
+// (FMA) and accumulated in float-float.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+};
+struct AccF {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    float s, e;
+    two_sum_d(hi, p, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+};
+
+// Reduction over the 8 lanes of a row group (lanes 8g .. 8g + 7).
+__device__ __forceinline__ double group_reduce(AccD& a) {
+  for (int o = 4; o > 0; o >>= 1) a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
+  return a.s;
+}
+__device__ __forceinline__ double group_reduce(AccF& a) {
+  for (int o = 4; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    float s, e;
+    two_sum_d(a.hi, oh, s, e);
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(ol, e));
+  }
+  return double(a.hi) + double(a.lo);
+}
+
+// Four propagator rows per warp, 8 lanes per row: y_i = sum_k P[i, k] w[k]. With vec (row
+// length a multiple of the vector width, rows 16-byte aligned) each lane streams its row in
+// 16-byte loads, four in flight; else scalar loads. Several rows in flight per warp keep the
+// load pipe busy through each row's reduction and owner update.
 template <typename PT>
 __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
                                                          const TileDesc* __restrict__ tiles,
                                                          const double* __restrict__ src, double* __restrict__ u,
                                                          int64_t ny, int64_t nx, int accumulate) {
-  extern __shared__ double w[];  // n_loc window values
+  // the tile's window values, converted once to the propagator's precision
+  extern __shared__ __align__(16) unsigned char wraw[];
+  PT* w = reinterpret_cast<PT*>(wraw);
   const int t = blockIdx.x;
   const TileDesc td = tiles[t];
   const int wl = td.wext[0] * td.wext[1];
@@ -34,44 +77,45 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
     int64_t gy = int64_t(td.org[0]) + a, gx = int64_t(td.org[1]) + b;
     gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
     gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-    w[k] = src[gy * nx + gx];
+    w[k] = PT(src[gy * nx + gx]);
   }
   __syncthreads();
   const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
   const int ie = td.iext[0] * td.iext[1];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  for (int i = warp; i < ie; i += nw) {
-    const PT* row = Pt + int64_t(i) * n_loc;
-    double y;
-    if constexpr (sizeof(PT) == 8) {
-      double acc = 0.0;
-      for (int k = lane; k < wl; k += 32) acc = fma(row[k], w[k], acc);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      y = acc;
-    } else {
-      // float-float accumulation of float products: each product is split exactly (FMA)
-      float hi = 0.0f, lo = 0.0f;
-      for (int k = lane; k < wl; k += 32) {
-        const float a = row[k];
-        const float b = float(w[k]);
-        const float p = __fmul_rn(a, b);
-        const float pe = fmaf(a, b, -p);
-        float s, e;
-        two_sum_d(hi, p, s, e);
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  const int grp = lane / 8, gl = lane % 8;
+  constexpr int V = 16 / sizeof(PT);
+  constexpr int U = 4;  // 16-byte loads in flight per lane
+  const bool vec = (n_loc % V) == 0 && (wl % V) == 0;
+  using Acc = typename std::conditional<sizeof(PT) == 8, AccD, AccF>::type;
+  // every lane runs the same number of row iterations (the shuffles need the whole warp)
+  for (int i0 = warp * 4; i0 < ie; i0 += nw * 4) {
+    const int i = i0 + grp;
+    const bool live = i < ie;
+    const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
+    Acc acc;
+    if (vec) {
+      const int nv = wl / V;
+      const int4* r4 = reinterpret_cast<const int4*>(row);
+      for (int j = gl; j < nv; j += 8 * U) {
+        int4 q[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) q[k] = (live && j + 8 * k < nv) ? __ldcs(r4 + j + 8 * k) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          if (j + 8 * k >= nv) break;
+          const PT* pq = reinterpret_cast<const PT*>(&q[k]);
+          const int4 wq = *reinterpret_cast<const int4*>(w + (j + 8 * k) * V);  // same 16 bytes of w
+          const PT* pw = reinterpret_cast<const PT*>(&wq);
+#pragma unroll
+          for (int h = 0; h < V; ++h) acc.add(pq[h], pw[h]);
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-        float s, e;
-        two_sum_d(hi, oh, s, e);
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(ol, e));
-      }
-      y = double(hi) + double(lo);
+    } else if (live) {
+      for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
     }
-    if (lane == 0) {
+    const double y = group_reduce(acc);
+    if (live && gl == 0) {
       const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
       u[p] = accumulate ? u[p] + y : y;
     }
