@@ -452,11 +452,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* empty = bars + STAGES;       // [STAGES] stage released by every CTA writing into it
   constexpr bool DRAIN = NP == 3;
   static_assert(!DRAIN || BN == 128, "drained correction: main[2] + corr[2] of 128 columns fill TMEM");
-  uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set (main) ready
-  uint64_t* acce = accf + 2;             // [2] accumulator set (main) drained
-  uint64_t* cf = acce + 2;               // DRAIN: [2] correction of one row group ready
-  uint64_t* ce = cf + 2;                 // DRAIN: [2] correction drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ce + 2);
+  uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set (main) ready (DRAIN: [0] only)
+  uint64_t* acce = accf + 2;             // [2] accumulator set (main) drained (DRAIN: [0] only)
+  uint64_t* cf = acce + 2;               // DRAIN: [3] correction buffer ready
+  uint64_t* ce = cf + 3;                 // DRAIN: [3] correction buffer free again
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ce + 3);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -511,6 +511,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&accf[b], 1);
       ptx::mbar_init(&acce[b], EPI_WARPS);
+    }
+    for (int b = 0; b < 3; ++b) {
       ptx::mbar_init(&cf[b], 1);
       ptx::mbar_init(&ce[b], EPI_WARPS);
     }
@@ -588,9 +590,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    // TMEM columns: without DRAIN, set b = [main | corr] at b * 2BN; with DRAIN, main b at
-    // b * BN and the two correction buffers at 2BN and 3BN. A DRAIN correction buffer
-    // collects drain_rows window rows before the epilogue takes it.
+    // TMEM columns: without DRAIN, set b = [main | corr] at b * 2BN (two sets alternate between
+    // tiles); with DRAIN, main at 0 and three correction buffers at BN, 2BN, 3BN used in turn,
+    // each collecting drain_rows window rows before the epilogue takes it. The epilogue folds a
+    // tile's main sum into its last correction buffer and frees main at once.
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
       bool ok = true;
@@ -602,12 +605,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const GemmGeom& g = locate(u, lu)->g;
         if (kb1 < 0) kb1 = g.Wy;
         const int ksteps = (g.Wx + 15) / 16, dr = DRAIN ? g.drain_rows : 1;
-        const int b = lt % NBUF;
-        if (lt >= NBUF) {
-          if (!ptx::mbar_wait(&acce[b], ((lt / NBUF) - 1) & 1, WAIT_NS)) { ok = false; break; }
+        const int nbuf = DRAIN ? 1 : NBUF;
+        const int b = lt % nbuf;
+        if (lt >= nbuf) {
+          if (!ptx::mbar_wait(&acce[b], ((lt / nbuf) - 1) & 1, WAIT_NS)) { ok = false; break; }
           ptx::tc_fence_after();
         }
-        const uint32_t main = DRAIN ? tmem + b * BN : tmem + b * 2 * BN;
+        const uint32_t main = DRAIN ? tmem : tmem + b * 2 * BN;
         uint32_t corr = main + BN;
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % STAGES;
@@ -615,9 +619,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const bool group_first = DRAIN && (kb - kb0) % dr == 0;
           const bool group_last = DRAIN && ((kb - kb0) % dr == dr - 1 || kb == kb1 - 1);
           if (group_first) {
-            const int j = kc & 1;
-            if (kc >= 2 && !ptx::mbar_wait(&ce[j], ((kc >> 1) - 1) & 1, WAIT_NS)) { ok = false; break; }
-            corr = tmem + (2 + j) * BN;
+            const int j = kc % 3;
+            if (kc >= 3 && !ptx::mbar_wait(&ce[j], ((kc / 3) - 1) & 1, WAIT_NS)) { ok = false; break; }
+            corr = tmem + (1 + j) * BN;
           }
           ptx::tc_fence_after();
           const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (MC) ptx::mma_commit_mc(&empty[s], maskE);
           else ptx::mma_commit(&empty[s]);
           if (group_last) {
-            ptx::mma_commit(&cf[kc & 1]);
+            ptx::mma_commit(&cf[kc % 3]);
             ++kc;
           }
         }
@@ -672,41 +676,46 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       int lu;
       const GemmGeom& g = locate(u, lu)->g;
       if (kb1 < 0) kb1 = g.Wy;
-      const int b = lt % NBUF;
+      const int nbuf = DRAIN ? 1 : NBUF;
+      const int b = lt % nbuf;
       float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over row groups
+      int fold = 0;              // DRAIN: the correction buffer of the tile's last row group
       if constexpr (DRAIN) {
 #pragma unroll
         for (int i = 0; i < BN; ++i) cs[i] = 0.0f;
         bool ok = true;
         const int ngroups = (kb1 - kb0 + g.drain_rows - 1) / g.drain_rows;
         for (int gi = 0; gi < ngroups; ++gi, ++kc) {
-          const int j = kc & 1;
-          if (s_abort || !ptx::mbar_wait(&cf[j], (kc >> 1) & 1, WAIT_NS)) { ok = false; break; }
+          const int j = kc % 3;
+          if (s_abort || !ptx::mbar_wait(&cf[j], (kc / 3) & 1, WAIT_NS)) { ok = false; break; }
           ptx::tc_fence_after();
-          const uint32_t tc = tmem + (uint32_t(lane_base) << 16) + uint32_t((2 + j) * BN);
+          const uint32_t tc = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + j) * BN);
 #pragma unroll
-          for (int h = 0; h < BN / 32; ++h) {
-            uint32_t r[32];
-            ptx::tmem_ld_32x32b_x32_nowait(tc + h * 32, r);
-            ptx::tmem_wait_ld();
+          for (int h = 0; h < BN / 64; ++h) {  // 64 columns per load round trip
+            uint32_t r[64];
+            ptx::tmem_ld_32x32b_x64(tc + h * 64, r);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) cs[h * 32 + i] = __fadd_rn(cs[h * 32 + i], __uint_as_float(r[i]));
+            for (int i = 0; i < 64; ++i) cs[h * 64 + i] = __fadd_rn(cs[h * 64 + i], __uint_as_float(r[i]));
           }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&ce[j]);
+          if (gi + 1 < ngroups) {  // the last buffer stays held: it receives the folded sum
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&ce[j]);
+          } else {
+            fold = j;
+          }
         }
         if (!ok) {
           atomicExch(err, ERR_TIMEOUT_EPI);
           break;
         }
       }
-      if (!ptx::mbar_wait(&accf[b], (lt / NBUF) & 1, WAIT_NS)) {
+      if (!ptx::mbar_wait(&accf[b], (lt / nbuf) & 1, WAIT_NS)) {
         atomicExch(err, ERR_TIMEOUT_EPI);
         break;
       }
       ptx::tc_fence_after();
-      const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(DRAIN ? b * BN : b * 2 * BN);
+      const uint32_t t_lane = tmem + (uint32_t(lane_base) << 16) + uint32_t(DRAIN ? 0 : b * 2 * BN);
       int m0, tx0, ty0;
       tile_of(g, lu, m0, tx0, ty0);
       const int ii = m0 + row;
@@ -716,8 +725,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int rowbase = iy * g.nx + ix;
       float* __restrict__ uh = g.uh;
       float* __restrict__ ul = g.ul;
-      // one batch of 16 windows: y = (main + corr) 2^-(eP_i + er) added into the owner nodes
-      auto batch = [&](int q, const float (&vm)[16], const float (&vc)[16]) {
+      // one batch of NB windows (columns c0 .. c0 + NB - 1): y = (main + corr) 2^-(eP_i + er)
+      // added into the owner nodes
+      // one batch of 16 windows (columns c0 .. c0 + 15): y = (main + corr) 2^-(eP_i + er) added
+      // into the owner nodes
+      auto batch = [&](int c0, const float (&vm)[16], const float (&vc)[16]) {
         // all 32 state loads of this batch go out before any store (the stores go through
         // the same pointers, so the compiler would otherwise keep them in program order)
         int node[16];
@@ -725,7 +737,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         uint32_t inside = 0;  // windows of this batch that exist (blocks may overhang the grid)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const int n = q * 16 + i;
+          const int n = c0 + i;
           const int ty = ty0 + n / g.BNx, tx = tx0 + n % g.BNx;
           const bool in = row_in && ty < g.nty && tx < g.ntx;
           inside |= uint32_t(in) << i;
@@ -747,31 +759,40 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
       };
       if constexpr (DRAIN) {
-        // fold the correction into the main accumulator (main + corr in FP32, as without the
-        // drain), so the scatter below holds no correction registers
+        // fold main + correction (FP32, as without the drain) into the last row group's
+        // correction buffer and free main at once, so the next tile's MMAs start during the
+        // scatter below; that buffer is released after the scatter
+        const uint32_t t_fold = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + fold) * BN);
 #pragma unroll
         for (int q = 0; q < BN / 16; ++q) {  // unrolled: cs is indexed statically
           float vm[16];
           ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
 #pragma unroll
           for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
-          ptx::tmem_st_32x32b_x16(t_lane + q * 16, vm);
+          ptx::tmem_st_32x32b_x16(t_fold + q * 16, vm);
         }
         ptx::tmem_wait_st();
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&acce[b]);
         const float zero[16] = {};
 #pragma unroll 1
         for (int q = 0; q < BN / 16; ++q) {
           float vm[16];
-          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
-          batch(q, vm, zero);
+          ptx::tmem_ld_32x32b_x16(t_fold + q * 16, vm);
+          batch(q * 16, vm, zero);
         }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&ce[fold]);
+        continue;
       } else {
 #pragma unroll 1
         for (int q = 0; q < BN / 16; ++q) {
           float vm[16], vc[16];
           ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
           ptx::tmem_ld_32x32b_x16(t_lane + BN + q * 16, vc);
-          batch(q, vm, vc);
+          batch(q * 16, vm, vc);
         }
       }
       ptx::tc_fence_before();
