@@ -145,6 +145,12 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
 lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out);
 
 /* Class of tile `tile` (row-major over the tile grid) or -1 on a bad index. */
+/* Load every class's propagator from host memory (FP64, nclasses x n_int x n_loc, the layout
+ * lem_get_propagator returns per class) instead of building them: with lem_get_propagator this
+ * checkpoints and restores a context's propagators bit for bit. h_squarings (nclasses values,
+ * or NULL) is only recorded. Marks the context built. Errors: LEM_EINVAL, LEM_ECUDA. */
+lem_status lem_set_propagators(lem_ctx* ctx, const double* h_P, const int* h_squarings);
+
 int64_t lem_tile_class(const lem_ctx* ctx, int64_t tile);
 
 /* Squaring count s used for class `cls` (-1 before the build or on a bad index). */

@@ -4,6 +4,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lem_internal.h"
 
 namespace lem {
@@ -77,6 +79,14 @@ void lem_ctx::timing_end(cudaEvent_t stop) {
 }
 
 using namespace lem;
+
+namespace {
+// NVTX range for profiler timelines (a no-op without a profiler attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -257,6 +267,7 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
   if (nsteps < 0) return fail(LEM_EINVAL, "nsteps < 0");
   if (nsteps == 0) return LEM_OK;
   DeviceGuard g(ctx->device);
+  NvtxRange range("lem_step");
   if (!ctx->built) LEM_TRY(build_propagators(ctx, d_state));
   if (ctx->split) return split_step(ctx, d_state, nsteps);
   for (int k = 0; k < nsteps; ++k) {
@@ -291,6 +302,19 @@ lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out) {
   LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   LEM_CUDA_TRY(cudaMemcpy(h_out, ctx->d_P + cls * ctx->n_int * ctx->n_loc,
                           sizeof(double) * ctx->n_int * ctx->n_loc, cudaMemcpyDeviceToHost));
+  return LEM_OK;
+}
+
+lem_status lem_set_propagators(lem_ctx* ctx, const double* h_P, const int* h_squarings) {
+  if (!ctx || !h_P) return fail(LEM_EINVAL, "NULL argument");
+  DeviceGuard g(ctx->device);
+  const size_t n = size_t(ctx->classes.size()) * size_t(ctx->n_int) * size_t(ctx->n_loc);
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  LEM_CUDA_TRY(cudaMemcpy(ctx->d_P, h_P, sizeof(double) * n, cudaMemcpyHostToDevice));
+  for (size_t c = 0; c < ctx->classes.size(); ++c) ctx->squarings[c] = h_squarings ? h_squarings[c] : -1;
+  ctx->built = true;
+  ctx->build_gen++;
+  ctx->steps_since_build = 0;
   return LEM_OK;
 }
 

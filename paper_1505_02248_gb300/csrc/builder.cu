@@ -14,6 +14,8 @@
 #include <cmath>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dgemm.cuh"
 #include "lem_internal.h"
 
@@ -386,7 +388,16 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   return LEM_OK;
 }
 
+lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state);
+
 lem_status build_propagators(lem_ctx* ctx, const double* d_state) {
+  nvtxRangePushA("lem_build_propagators");
+  const lem_status st = build_propagators_impl(ctx, d_state);
+  nvtxRangePop();
+  return st;
+}
+
+lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state) {
   if (ctx->desc.reaction && !d_state) return fail(LEM_EINVAL, "the reaction Jacobian needs the state");
   const int64_t nc = int64_t(ctx->classes.size());
   const int64_t n = ctx->n_loc;

@@ -208,6 +208,15 @@ int64_t ctx_bytes_estimate(const lem_problem_desc& d, int64_t* scratch) {
 // false if r must keep waiting; fails r (and returns true) when it can never run.
 bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
   const int64_t sbytes = int64_t(sizeof(double)) * r->npts;
+  {
+    // host-side fault injection for tests: LEM_FAULT=admit refuses every admission
+    const char* f = std::getenv("LEM_FAULT");
+    if (f && std::strcmp(f, "admit") == 0) {
+      lem::fail(LEM_ENOMEM, "admission refused (LEM_FAULT=admit)");
+      finish(s, r, LEM_ENOMEM);
+      return true;
+    }
+  }
   lem_problem_desc d = r->desc;
   for (int k = 0; k < 5; ++k) d.coef[k] = r->coef[k].empty() ? nullptr : r->coef[k].data();
   const bool want_split = r->tol >= 1e-6;

@@ -84,6 +84,8 @@ struct GemmGeom {
   int bsplit_y;         // clustered: a window block's two halves split along y (else x)
   int drain_rows;       // three pieces: window rows per correction drain
   int unit0;            // multi-problem launch: this problem's first unit
+  int fault;            // test hook (LEM_FAULT=timeout): CTA 0 arms its first stage but loads
+                        // nothing, so the MMA issuer's bounded wait expires
   const int* eP;        // per owner row: P scale exponent
   const int* escale;    // [2] residual scale exponent of each step parity
   unsigned* rmax;       // [2] max|r| accumulators (the GEMM clears the current one)
@@ -562,6 +564,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (s_abort) break;
           uint8_t* st = tiles + s * STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          if (g.fault && blockIdx.x == 0 && it == 0) {  // test hook: the bytes never arrive
+            issued = it + 1;
+            continue;
+          }
           if (MC) {
             // my half of the P rows (to me and the P partner), my half of the windows (to me
             // and the window partner); the partners send the other halves
@@ -1045,6 +1051,10 @@ lem_status split_prepare(lem_ctx* ctx) {
   g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
   if (const char* e = std::getenv("LEM_SPLIT_DRAIN_ROWS")) g.drain_rows = std::max(1, std::atoi(e));  // tuning knob
   g.unit0 = 0;
+  {
+    const char* f = std::getenv("LEM_FAULT");
+    g.fault = f && std::strcmp(f, "timeout") == 0;
+  }
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
   sp->prob_flat.g = g;
   cudaFuncAttributes fa{};

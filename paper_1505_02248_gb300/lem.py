@@ -75,6 +75,7 @@ SIGNATURES = [
     ("lem_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lem_step_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lem_get_propagator", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    ("lem_set_propagators", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lem_tile_class", C.c_int64, [C.c_void_p, C.c_int64]),
     ("lem_class_squarings", C.c_int, [C.c_void_p, C.c_int64]),
     ("lem_get_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
@@ -241,6 +242,14 @@ class Lem:
         check(self._lib.lem_get_propagator(self._h, int(cls), out.ctypes.data_as(C.c_void_p)),
               "lem_get_propagator")
         return out
+
+    def set_propagators(self, P: np.ndarray, squarings=None):
+        """Load all classes' propagators (nclasses x n_int x n_loc, float64) instead of building."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        sq = None if squarings is None else np.ascontiguousarray(squarings, dtype=np.int32)
+        check(self._lib.lem_set_propagators(self._h, P.ctypes.data_as(C.c_void_p),
+                                            None if sq is None else sq.ctypes.data_as(C.c_void_p)),
+              "lem_set_propagators")
 
     def tile_class(self, t: int) -> int:
         return int(self._lib.lem_tile_class(self._h, int(t)))
