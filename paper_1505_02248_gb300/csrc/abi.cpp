@@ -145,6 +145,8 @@ lem_status adopt_propagators(lem_ctx* dst, lem_ctx* src, cudaEvent_t built) {
            a.wext[k] == b.wext[k] && a.iext[k] == b.iext[k] && a.iofs[k] == b.iofs[k] && !a.whole[k] && !b.whole[k];
   DeviceGuard g(dst->device);
   same = same && dst->h_coef == src->h_coef;  // the dt-scaled constant stencils
+  // an FP64-tier context takes only propagators built with FP64 products
+  same = same && (dst->build_tc || !src->build_tc);
   if (!same) return fail(LEM_EINVAL, "donor has a different local operator");
   LEM_CUDA_TRY(cudaStreamWaitEvent(dst->stream, built, 0));
   LEM_CUDA_TRY(cudaMemcpyAsync(dst->d_P, src->d_P, sizeof(double) * dst->n_int * dst->n_loc,
@@ -236,6 +238,7 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   // apply path: tensor-core split for a shared propagator, else a batched GEMV when tiles
   // have (mostly) their own propagators or FP32 propagators are asked for, else grouped GEMMs
   const bool many_classes = c->classes.size() * 8 > c->tiles.size();
+  c->build_tc = builder_uses_tc(desc->prec);
   const bool split_tier = desc->prec == LEM_PREC_SPLIT || desc->prec == LEM_PREC_SPLIT_FAST;
   if (split_tier && split_eligible(c)) {
     c->apply_path = LEM_APPLY_TC_SPLIT;

@@ -1,5 +1,8 @@
 // Local propagator builder (Sec. 3 step 2; Pade approximation with scaling and squaring
-// as named in Sec. 1 and Sec. 4), batched over propagator classes, all in FP64.
+// as named in Sec. 1 and Sec. 4), batched over propagator classes, in FP64. For the
+// split-precision tiers the matrix products run on the tensor cores as exact sums of FP16
+// slice products (builder_tc.cu, about 2^-45 relative to the operands' scale); the Pade
+// denominator solve stays in FP64 either way.
 //
 // For each class the local matrix X = dt A_M (principal submatrix on the window, i.e.
 // Dirichlet data at the artificial boundary; plus dt diag(1 - 3u^2) with the reaction) is
@@ -11,7 +14,11 @@
 // products. Degree-13 Pade (Higham 2005 coefficients b_j = (2m-j)! m! / ((2m)! j! (m-j)!)),
 // s = smallest integer >= 0 with ||Z||_1 / 2^s <= theta_13 from the exact 1-norm,
 // (V - U) R = (V + U) by Gauss-Jordan elimination with partial pivoting, then s squarings.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <numeric>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -200,6 +207,20 @@ inline dim3 grid1(int64_t total, int by) { return dim3(unsigned((total + 255) / 
 
 }  // namespace
 
+bool builder_uses_tc(int prec) {
+  if (prec == LEM_PREC_FP64) return false;
+  const char* e = std::getenv("LEM_BUILD_PRODUCTS");  // "fp64": FP64 products in every tier
+  return !(e && std::string(e) == "fp64");
+}
+
+namespace {
+struct TcGuard {
+  TcGemm* g = nullptr;
+  cudaStream_t st = nullptr;
+  ~TcGuard() { tc_gemm_destroy(g, st); }
+};
+}  // namespace
+
 // Build the propagators of classes [c0, c0 + nb) into P (nb x n_int x n_loc).
 static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_state) {
   cudaStream_t st = ctx->stream;
@@ -276,7 +297,12 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LEM_OK : cuda_fail(e, "lincomb_kernel");
   };
+  TcGuard tc;
+  tc.st = st;
+  if (ctx->build_tc) LEM_TRY(tc_gemm_create(n, nb, st, &tc.g));
+  // C = A B + beta C for every class of the batch
   auto mm = [&](const double* A, const double* B, double* C, double beta) -> lem_status {
+    if (tc.g) return tc_gemm(tc.g, nb, nullptr, A, B, C, C, 1.0, beta, st);
     LEM_CUDA_TRY(dgemm_sq(n, nb, A, B, C, 1.0, beta, st));
     return LEM_OK;
   };
@@ -346,11 +372,41 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   double* RB = B2;  double* RBn = B4;
   bool uniform = true;
   for (int b = 0; b < nb; ++b) uniform = uniform && (s[b] == s[0]);
-  if (uniform) {
+  Buf mapbuf;
+  if (tc.g && !uniform) {
+    // Classes sorted by s, descending: at squaring q the classes still squaring (s > q) are a
+    // prefix of the order, so one index map serves every squaring.
+    std::vector<int> order(nb);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s[a] > s[b]; });
+    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&mapbuf.p), sizeof(int) * nb, st));
+    const int* d_map = reinterpret_cast<const int*>(mapbuf.p);
+    LEM_CUDA_TRY(cudaMemcpyAsync(mapbuf.p, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < smax; ++q) {
+      int nact = 0;
+      while (nact < nb && s[order[nact]] > q) ++nact;
+      if (phi) LEM_TRY(tc_gemm(tc.g, nact, d_map, RT, RB, RB, RBn, 1.0, 1.0, st));  // R_T R_B + R_B
+      LEM_TRY(tc_gemm(tc.g, nact, d_map, RT, RT, nullptr, RTn, 1.0, 0.0, st));
+      std::swap(RT, RTn);
+      if (phi) std::swap(RB, RBn);
+    }
+    // a class that stopped squaring an odd number of steps early holds its result in the
+    // other buffer of the pair
+    for (int b = 0; b < nb; ++b) {
+      if ((smax - s[b]) % 2 == 0) continue;
+      LEM_CUDA_TRY(cudaMemcpyAsync(RT + b * nn, RTn + b * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+      if (phi)
+        LEM_CUDA_TRY(cudaMemcpyAsync(RB + b * nn, RBn + b * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+    }
+  } else if (uniform) {
     for (int q = 0; q < s[0]; ++q) {
       if (phi) {  // (R_T, R_B)^2 = (R_T^2, R_T R_B + R_B)
-        LEM_CUDA_TRY(cudaMemcpyAsync(RBn, RB, sizeof(double) * nn * nb, cudaMemcpyDeviceToDevice, st));
-        LEM_TRY(mm(RT, RB, RBn, 1.0));
+        if (tc.g) {
+          LEM_TRY(tc_gemm(tc.g, nb, nullptr, RT, RB, RB, RBn, 1.0, 1.0, st));
+        } else {
+          LEM_CUDA_TRY(cudaMemcpyAsync(RBn, RB, sizeof(double) * nn * nb, cudaMemcpyDeviceToDevice, st));
+          LEM_TRY(mm(RT, RB, RBn, 1.0));
+        }
         std::swap(RB, RBn);
       }
       LEM_TRY(mm(RT, RT, RTn, 0.0));
@@ -385,6 +441,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   // scratch is released by the Buf destructors (stream-ordered frees are unnecessary
   // after the synchronisation above)
   if (status != 0) return fail(LEM_ENUMERIC, "singular Pade denominator (V - U) in the propagator build");
+  if (tc.g) LEM_TRY(tc_gemm_check(tc.g, st));
   return LEM_OK;
 }
 
@@ -403,7 +460,7 @@ lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state) {
   const int64_t n = ctx->n_loc;
   const int nmat = ctx->desc.mode == LEM_MODE_PHI ? 19 : 11;
   // batch size from a scratch budget of 8 GiB
-  const double per = double(nmat) * n * n * sizeof(double);
+  const double per = double(nmat) * n * n * sizeof(double) + (ctx->build_tc ? double(tc_gemm_bytes(int(n), 1)) : 0.0);
   int64_t bmax = std::max<int64_t>(1, int64_t((8.0 * (1ull << 30)) / per));
   bmax = std::min<int64_t>(bmax, 65535);
   for (int64_t c0 = 0; c0 < nc; c0 += bmax) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the liblem translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -87,6 +88,7 @@ struct lem_ctx {
   std::vector<int> squarings;          // per class, after the build
   int64_t n_loc = 0, n_int = 0;        // padded window / tile sizes
   bool built = false;
+  bool build_tc = false;               // propagator products on the tensor cores (split tiers)
   int build_gen = 0;                   // incremented by every propagator build
   int steps_since_build = 0;
   // device buffers (owned)
@@ -130,6 +132,8 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
 void split_destroy(lem_ctx* ctx);
 lem_status split_check_error(lem_ctx* ctx);
 bool split_eligible(const lem_ctx* ctx);
+lem_status encode_f16_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                          const cuuint32_t* box, const char* what);
 // multi-problem split steps (one residual and one GEMM launch per step for a whole batch)
 struct SplitBatch;
 bool split_batch_eligible(lem_ctx* const* ctxs, int n);
@@ -138,6 +142,17 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
 double split_batch_gemm_flops(const SplitBatch* b, lem_ctx* const* ctxs);
 lem_status split_batch_check_error(SplitBatch* b);
 void split_batch_destroy(SplitBatch* b);
+// builder_tc.cu: FP64 products of the propagator build as exact sums of FP16 slice products
+// on the tensor cores (split-precision tiers)
+struct TcGemm;
+size_t tc_gemm_bytes(int n, int nb);
+lem_status tc_gemm_create(int n, int nb, cudaStream_t st, TcGemm** out);
+void tc_gemm_destroy(TcGemm* g, cudaStream_t st);
+lem_status tc_gemm(TcGemm* g, int nbatch, const int* map, const double* A, const double* B, const double* D,
+                   double* C, double alpha, double beta, cudaStream_t st);
+lem_status tc_gemm_check(TcGemm* g, cudaStream_t st);
+// builder.cu: whether propagators of a precision tier are built with the tensor-core products
+bool builder_uses_tc(int prec);
 // abi.cpp: take a built single-class propagator from a context with the same local operator
 lem_status adopt_propagators(lem_ctx* dst, lem_ctx* src, cudaEvent_t built);
 // allocation helper that tracks bytes

@@ -240,10 +240,15 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
       finish(s, r, LEM_EINVAL);
       return true;
     }
+    // donors are keyed by the local operator and the kind of products that built them; a
+    // tensor-core-built propagator is lent only to split-tier contexts
+    const bool tc_build = lem::builder_uses_tc(d.prec);
+    const std::string own_key = r->op_key + (tc_build ? "/tc" : "/f64");
+    const std::string f64_key = r->op_key + "/f64";
     bool has_donor;
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      has_donor = s->donors.count(r->op_key) > 0;
+      has_donor = s->donors.count(own_key) > 0 || s->donors.count(f64_key) > 0;
     }
     const int64_t need = keep + (has_donor ? 0 : scratch);  // room needed now
     if (need + sbytes > s->budget) {  // larger than the whole budget
@@ -307,7 +312,8 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
       std::pair<lem_ctx*, cudaEvent_t> donor{nullptr, nullptr};
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        auto it = s->donors.find(r->op_key);
+        auto it = s->donors.find(own_key);
+        if (it == s->donors.end()) it = s->donors.find(f64_key);
         if (it != s->donors.end()) donor = it->second;
       }
       if (donor.first && lem::adopt_propagators(c->ctx, donor.first, donor.second) == LEM_OK) {
@@ -325,7 +331,7 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
         if (bs == LEM_OK && cudaEventCreateWithFlags(&built, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventRecord(built, c->stream) == cudaSuccess) {
           std::lock_guard<std::mutex> lk(s->mu);
-          s->donors.emplace(r->op_key, std::make_pair(c->ctx, built));
+          s->donors.emplace(own_key, std::make_pair(c->ctx, built));
         } else {
           cudaGetLastError();
           if (built) cudaEventDestroy(built);

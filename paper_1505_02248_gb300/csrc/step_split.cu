@@ -909,8 +909,9 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static lem_status encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                         const cuuint32_t* box, const char* what) {
+// FP16 tiled tensor map, 128-byte swizzle (the layout of every tcgen05 operand tile here)
+lem_status encode_f16_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                          const cuuint32_t* box, const char* what) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return fail(LEM_ECUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint32_t es[4] = {1, 1, 1, 1};
@@ -1038,8 +1039,8 @@ lem_status split_prepare(lem_ctx* ctx) {
       else rbox[1] /= 2;
     }
     for (int k = 0; k < 3; ++k) {
-      LEM_TRY(encode(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
-      LEM_TRY(encode(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
+      LEM_TRY(encode_f16_map(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
+      LEM_TRY(encode_f16_map(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
     }
   }
   GemmGeom& g = sp->prob.g;
