@@ -171,6 +171,100 @@ __global__ void gj_update_kernel(double* G, int n, int ncols, int k) {
     M[int64_t(i) * ncols + j] = fma(-f, M[int64_t(k) * ncols + j], M[int64_t(i) * ncols + j]);
 }
 
+// ---------------------------------------------------------------- blocked Gauss-Jordan
+// For the tensor-core build the elimination runs in panels of GJ_KB columns. The panel's
+// GJ_KB pivot steps (partial pivoting, FP64) are applied to the panel columns and to a tracker
+// Y (n x GJ_KB): at step c, right after the row swap, Y[k0 + c][c] = 1 is injected, and every
+// later swap, scaling and elimination acts on Y too. At the end of the panel the composite row
+// operation is M = T Pi with T = I + W E_K^T (Pi: the panel's swaps, K: rows k0 .. k0 + kb),
+// and Y = T[:, K], so the trailing columns become
+//   rows K:      Y_K (Pi G)[K, :]
+//   other rows:  (Pi G)[i, :] + Y_i (Pi G)[K, :],
+// one rank-kb product C = Y B + D with B the permuted pivot rows and D the permuted trailing
+// columns with rows K taken as zero. The FP64 work drops from n^2 gjcols to about 2 n^2 GJ_KB.
+constexpr int GJ_KB = 64;
+
+__global__ void bgj_pivot_kernel(double* G, int n, int ld, int k0, int c, int kb, double* Y, int* piv,
+                                 int* status) {
+  const int b = blockIdx.x;
+  double* M = G + int64_t(b) * n * ld;
+  double* Yb = Y + int64_t(b) * n * GJ_KB;
+  const int col = k0 + c, r = k0 + c;
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  double best = -1.0;
+  int bi = r;
+  for (int i = r + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(M[int64_t(i) * ld + col]);
+    if (v > best) { best = v; bi = i; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = sv[threadIdx.x + s];
+      const int oi = si[threadIdx.x + s];
+      if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = o;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = si[0];
+  const double pv = M[int64_t(p) * ld + col];
+  __syncthreads();  // every thread holds pv before rows r / p are rewritten
+  if (!(sv[0] > 0.0) || !isfinite(pv)) {
+    if (threadIdx.x == 0) atomicExch(status, int(LEM_ENUMERIC));
+    return;
+  }
+  if (threadIdx.x == 0) piv[b * GJ_KB + c] = p;
+  const double inv = 1.0 / pv;
+  // panel columns col .. k0 + kb - 1 of rows r and p, then the tracker rows
+  for (int j = col + threadIdx.x; j < k0 + kb; j += blockDim.x) {
+    const double a = M[int64_t(r) * ld + j], q = M[int64_t(p) * ld + j];
+    if (p != r) M[int64_t(p) * ld + j] = a;
+    M[int64_t(r) * ld + j] = q * inv;
+  }
+  for (int j = threadIdx.x; j < kb; j += blockDim.x) {
+    const double a = Yb[int64_t(r) * GJ_KB + j], q = Yb[int64_t(p) * GJ_KB + j];
+    if (p != r) Yb[int64_t(p) * GJ_KB + j] = a;
+    Yb[int64_t(r) * GJ_KB + j] = (j == c ? 1.0 : q) * inv;  // inject the unit column, then scale
+  }
+}
+
+// Eliminate panel column k0 + c from every row but the pivot row: 4 rows per block, thread t
+// of a row updates panel column k0 + c + 1 + t and tracker column t.
+__global__ void bgj_elim_kernel(double* G, int n, int ld, int k0, int c, int kb, double* Y) {
+  const int b = blockIdx.y;
+  const int i = blockIdx.x * 4 + threadIdx.x / 64, t = threadIdx.x % 64;
+  const int r = k0 + c, col = k0 + c;
+  if (i >= n || i == r) return;
+  double* M = G + int64_t(b) * n * ld;
+  double* Yb = Y + int64_t(b) * n * GJ_KB;
+  const double f = M[int64_t(i) * ld + col];
+  if (f == 0.0) return;
+  const int j = col + 1 + t;
+  if (j < k0 + kb) M[int64_t(i) * ld + j] = fma(-f, M[int64_t(r) * ld + j], M[int64_t(i) * ld + j]);
+  if (t < kb) Yb[int64_t(i) * GJ_KB + t] = fma(-f, Yb[int64_t(r) * GJ_KB + t], Yb[int64_t(i) * GJ_KB + t]);
+}
+
+// The panel's row swaps, in order, on the trailing columns j >= k0 + kb.
+__global__ void bgj_swap_kernel(double* G, int n, int ld, int k0, int kb, const int* piv) {
+  const int b = blockIdx.y;
+  const int j = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ld) return;
+  double* M = G + int64_t(b) * n * ld;
+  for (int c = 0; c < kb; ++c) {
+    const int p = piv[b * GJ_KB + c];
+    if (p == k0 + c) continue;
+    const double a = M[int64_t(k0 + c) * ld + j];
+    M[int64_t(k0 + c) * ld + j] = M[int64_t(p) * ld + j];
+    M[int64_t(p) * ld + j] = a;
+  }
+}
+
 // rows of the owner tile D inside the window, from the squared result R (n x ld, col0)
 __global__ void extract_rows_kernel(double* P, int64_t n_int, int64_t n_loc, const double* R,
                                     int n, int64_t ld, int col0, const BatchClass* bc) {
@@ -299,10 +393,10 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   };
   TcGuard tc;
   tc.st = st;
-  if (ctx->build_tc) LEM_TRY(tc_gemm_create(n, nb, st, &tc.g));
+  if (ctx->build_tc) LEM_TRY(tc_gemm_create(n, nb, gjcols, st, &tc.g));
   // C = A B + beta C for every class of the batch
   auto mm = [&](const double* A, const double* B, double* C, double beta) -> lem_status {
-    if (tc.g) return tc_gemm(tc.g, nb, nullptr, A, B, C, C, 1.0, beta, st);
+    if (tc.g) return tc_gemm(tc.g, n, nb, nullptr, A, B, C, C, 1.0, beta, st);
     LEM_CUDA_TRY(dgemm_sq(n, nb, A, B, C, 1.0, beta, st));
     return LEM_OK;
   };
@@ -356,10 +450,36 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     LEM_CUDA_TRY(cudaGetLastError());
   }
   LEM_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
-  for (int k = 0; k < n; ++k) {
-    gj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k, ctx->d_status);
-    int bx = std::max(1, std::min(8, (gjcols - k - 1 + 255) / 256));
-    gj_update_kernel<<<dim3(bx, n, nb), 256, 0, st>>>(G, n, gjcols, k);
+  Buf ybuf, pivbuf;  // freed after the final synchronisation
+  if (tc.g) {
+    // blocked elimination: FP64 panels, rank-GJ_KB trailing updates on the tensor cores
+    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&ybuf.p), sizeof(double) * nb * n * GJ_KB, st));
+    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&pivbuf.p), sizeof(int) * nb * GJ_KB, st));
+    double* Y = ybuf.p;
+    int* piv = reinterpret_cast<int*>(pivbuf.p);
+    for (int k0 = 0; k0 < n; k0 += GJ_KB) {
+      const int kb = std::min(GJ_KB, n - k0);
+      LEM_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * nb * n * GJ_KB, st));
+      for (int c = 0; c < kb; ++c) {
+        bgj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y, piv, ctx->d_status);
+        bgj_elim_kernel<<<dim3((n + 3) / 4, nb), 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y);
+      }
+      const int m_r = gjcols - (k0 + kb);
+      bgj_swap_kernel<<<dim3((m_r + 255) / 256, nb), 256, 0, st>>>(G, n, gjcols, k0, kb, piv);
+      LEM_CUDA_TRY(cudaGetLastError());
+      double* T = G + (k0 + kb);                            // trailing columns
+      const int64_t sG = int64_t(n) * gjcols;
+      LEM_TRY(tc_gemm_ex(tc.g, nb, nullptr, n, m_r, kb, Y, GJ_KB, int64_t(n) * GJ_KB,  // A = Y
+                         T + int64_t(k0) * gjcols, gjcols, sG,                         // B = pivot rows
+                         T, gjcols, sG, k0, k0 + kb,                                   // D, rows K zero
+                         T, gjcols, sG, 1.0, 1.0, st));
+    }
+  } else {
+    for (int k = 0; k < n; ++k) {
+      gj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k, ctx->d_status);
+      int bx = std::max(1, std::min(8, (gjcols - k - 1 + 255) / 256));
+      gj_update_kernel<<<dim3(bx, n, nb), 256, 0, st>>>(G, n, gjcols, k);
+    }
   }
   LEM_CUDA_TRY(cudaGetLastError());
   // R_T -> RT2 (ping) ; R_B -> B2 (ping) ; squarings per class (s differs per class:
@@ -385,8 +505,8 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     for (int q = 0; q < smax; ++q) {
       int nact = 0;
       while (nact < nb && s[order[nact]] > q) ++nact;
-      if (phi) LEM_TRY(tc_gemm(tc.g, nact, d_map, RT, RB, RB, RBn, 1.0, 1.0, st));  // R_T R_B + R_B
-      LEM_TRY(tc_gemm(tc.g, nact, d_map, RT, RT, nullptr, RTn, 1.0, 0.0, st));
+      if (phi) LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RB, RB, RBn, 1.0, 1.0, st));  // R_T R_B + R_B
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RT, nullptr, RTn, 1.0, 0.0, st));
       std::swap(RT, RTn);
       if (phi) std::swap(RB, RBn);
     }
@@ -402,7 +522,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     for (int q = 0; q < s[0]; ++q) {
       if (phi) {  // (R_T, R_B)^2 = (R_T^2, R_T R_B + R_B)
         if (tc.g) {
-          LEM_TRY(tc_gemm(tc.g, nb, nullptr, RT, RB, RB, RBn, 1.0, 1.0, st));
+          LEM_TRY(tc_gemm(tc.g, n, nb, nullptr, RT, RB, RB, RBn, 1.0, 1.0, st));
         } else {
           LEM_CUDA_TRY(cudaMemcpyAsync(RBn, RB, sizeof(double) * nn * nb, cudaMemcpyDeviceToDevice, st));
           LEM_TRY(mm(RT, RB, RBn, 1.0));
@@ -460,7 +580,9 @@ lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state) {
   const int64_t n = ctx->n_loc;
   const int nmat = ctx->desc.mode == LEM_MODE_PHI ? 19 : 11;
   // batch size from a scratch budget of 8 GiB
-  const double per = double(nmat) * n * n * sizeof(double) + (ctx->build_tc ? double(tc_gemm_bytes(int(n), 1)) : 0.0);
+  const int gjc = ctx->desc.mode == LEM_MODE_PHI ? 3 * int(n) : 2 * int(n);
+  const double per = double(nmat) * n * n * sizeof(double) +
+                     (ctx->build_tc ? double(tc_gemm_bytes(int(n), 1, gjc)) + sizeof(double) * n * GJ_KB : 0.0);
   int64_t bmax = std::max<int64_t>(1, int64_t((8.0 * (1ull << 30)) / per));
   bmax = std::min<int64_t>(bmax, 65535);
   for (int64_t c0 = 0; c0 < nc; c0 += bmax) {

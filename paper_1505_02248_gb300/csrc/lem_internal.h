@@ -145,10 +145,17 @@ void split_batch_destroy(SplitBatch* b);
 // builder_tc.cu: FP64 products of the propagator build as exact sums of FP16 slice products
 // on the tensor cores (split-precision tiers)
 struct TcGemm;
-size_t tc_gemm_bytes(int n, int nb);
-lem_status tc_gemm_create(int n, int nb, cudaStream_t st, TcGemm** out);
+// workspace for products of nb matrices of n x n and rank-64 updates of n x gjcols ones
+size_t tc_gemm_bytes(int n, int nb, int gjcols);
+lem_status tc_gemm_create(int n, int nb, int gjcols, cudaStream_t st, TcGemm** out);
 void tc_gemm_destroy(TcGemm* g, cudaStream_t st);
-lem_status tc_gemm(TcGemm* g, int nbatch, const int* map, const double* A, const double* B, const double* D,
+// C = alpha A B + beta D on strided batches of row-major FP64 matrices (A M x K, B K x N)
+lem_status tc_gemm_ex(TcGemm* g, int nbatch, const int* map, int M, int N, int K, const double* A, int64_t lda,
+                      int64_t sA, const double* B, int64_t ldb, int64_t sB, const double* D, int64_t ldd,
+                      int64_t sD, int zr0, int zr1, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
+                      cudaStream_t st);
+// the same for square n x n matrices stored back to back
+lem_status tc_gemm(TcGemm* g, int n, int nbatch, const int* map, const double* A, const double* B, const double* D,
                    double* C, double alpha, double beta, cudaStream_t st);
 lem_status tc_gemm_check(TcGemm* g, cudaStream_t st);
 // builder.cu: whether propagators of a precision tier are built with the tensor-core products
