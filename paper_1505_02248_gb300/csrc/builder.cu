@@ -396,7 +396,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   if (ctx->build_tc) LEM_TRY(tc_gemm_create(n, nb, gjcols, st, &tc.g));
   // C = A B + beta C for every class of the batch
   auto mm = [&](const double* A, const double* B, double* C, double beta) -> lem_status {
-    if (tc.g) return tc_gemm(tc.g, n, nb, nullptr, A, B, C, C, 1.0, beta, st);
+    if (tc.g) return tc_gemm(tc.g, n, nb, nullptr, A, B, beta != 0.0 ? C : nullptr, C, st);
     LEM_CUDA_TRY(dgemm_sq(n, nb, A, B, C, 1.0, beta, st));
     return LEM_OK;
   };
@@ -472,7 +472,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
       LEM_TRY(tc_gemm_ex(tc.g, nb, nullptr, n, m_r, kb, Y, GJ_KB, int64_t(n) * GJ_KB,  // A = Y
                          T + int64_t(k0) * gjcols, gjcols, sG,                         // B = pivot rows
                          T, gjcols, sG, k0, k0 + kb,                                   // D, rows K zero
-                         T, gjcols, sG, 1.0, 1.0, st));
+                         T, gjcols, sG, st));
     }
   } else {
     for (int k = 0; k < n; ++k) {
@@ -505,8 +505,8 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     for (int q = 0; q < smax; ++q) {
       int nact = 0;
       while (nact < nb && s[order[nact]] > q) ++nact;
-      if (phi) LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RB, RB, RBn, 1.0, 1.0, st));  // R_T R_B + R_B
-      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RT, nullptr, RTn, 1.0, 0.0, st));
+      if (phi) LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RB, RB, RBn, st));  // R_T R_B + R_B
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, RT, RT, nullptr, RTn, st));
       std::swap(RT, RTn);
       if (phi) std::swap(RB, RBn);
     }
@@ -522,7 +522,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
     for (int q = 0; q < s[0]; ++q) {
       if (phi) {  // (R_T, R_B)^2 = (R_T^2, R_T R_B + R_B)
         if (tc.g) {
-          LEM_TRY(tc_gemm(tc.g, n, nb, nullptr, RT, RB, RB, RBn, 1.0, 1.0, st));
+          LEM_TRY(tc_gemm(tc.g, n, nb, nullptr, RT, RB, RB, RBn, st));
         } else {
           LEM_CUDA_TRY(cudaMemcpyAsync(RBn, RB, sizeof(double) * nn * nb, cudaMemcpyDeviceToDevice, st));
           LEM_TRY(mm(RT, RB, RBn, 1.0));

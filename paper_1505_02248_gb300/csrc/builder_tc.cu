@@ -28,17 +28,27 @@ namespace {
 constexpr int OZ_S = 7;     // slices per operand
 constexpr int OZ_BM = 128;  // output rows per CTA (TMEM lanes)
 constexpr int OZ_BN = 64;   // output columns per CTA
-constexpr int OZ_KB = 64;   // K elements per block (one 128-byte swizzled row)
+constexpr int OZ_KB = 32;   // K elements per block
+constexpr int OZ_CHUNK = 4;  // K blocks per exact chunk (K = 128)
 constexpr int OZ_A_BYTES = OZ_BM * OZ_KB * 2;
 constexpr int OZ_B_BYTES = OZ_BN * OZ_KB * 2;
-constexpr int OZ_STAGE = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);  // 168 KB: one stage
-constexpr int OZ_SMEM = OZ_STAGE + 1024 + 256;
+constexpr int OZ_STAGE = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);  // 84 KB: all slices of one K block
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
 constexpr int OZ_THREADS = 192;                             // producer, MMA issuer, 4 epilogue warps
 constexpr uint64_t OZ_WAIT_NS = 2000000000ull;
 
-// 2^e as a double (built from its bits in the normal range).
-__device__ __forceinline__ double pow2d(int e) {
-  return (e >= -1022 && e <= 1023) ? __longlong_as_double(static_cast<long long>(e + 1023) << 52) : ldexp(1.0, e);
+// x 2^E as a double, built from the bits of the float x with integer operations only (x normal
+// or zero; GB300 runs FP64 conversions and multiplies at a small fraction of its FP32 rate).
+__device__ __forceinline__ double f32_scaled_to_f64(float x, int E) {
+  const uint32_t b = __float_as_uint(x);
+  const int e8 = static_cast<int>((b >> 23) & 0xFF);
+  const int ed = e8 - 127 + E + 1023;
+  if (e8 == 0 || ed <= 0) return 0.0;
+  const unsigned long long sign = static_cast<unsigned long long>(b >> 31) << 63;
+  if (ed >= 2047) return __longlong_as_double(static_cast<long long>(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(ed) << 52) |
+                                                     (static_cast<unsigned long long>(b & 0x7FFFFF) << 29)));
 }
 
 // Biased exponent field of a double (0 for zero and subnormals, which the slices treat as 0).
@@ -89,8 +99,26 @@ struct MatOut {
 // slices and exponents are stored at q.
 __device__ __forceinline__ int mat_of(const int* map, int q) { return map ? map[q] : q; }
 
-// Row exponents and row slices of A (rows x kdim): e[q][i] and out[s][q][i][k] (K contiguous,
-// rows_pad x k_pad per (s, q), zero padding). One block per row.
+// Slice planes are stored as the operand tiles the MMA reads, each one contiguous: for slice s
+// of matrix q, tile (row block, K block) of R x OZ_KB halves (R = 128 for A, 64 for B) in the
+// tcgen05 K-major layout without swizzle: 8-row x 8-element core matrices of 128 contiguous
+// bytes, core matrices along K 128 B apart, along the rows 512 B apart. Element (r, k) of a
+// tile sits at half offset (r / 8) 256 + (k / 8) 64 + (r % 8) 8 + k % 8.
+__device__ __forceinline__ size_t tile_off(int r, int k8) {  // k8: first of 8 consecutive K elements
+  return size_t(r / 8) * 256 + size_t(k8 / 8) * 64 + size_t(r % 8) * 8;
+}
+
+__device__ __forceinline__ void store8(__half* dst, const __half (&v)[8]) {
+  uint4 u;
+  u.x = uint32_t(__half_as_ushort(v[0])) | (uint32_t(__half_as_ushort(v[1])) << 16);
+  u.y = uint32_t(__half_as_ushort(v[2])) | (uint32_t(__half_as_ushort(v[3])) << 16);
+  u.z = uint32_t(__half_as_ushort(v[4])) | (uint32_t(__half_as_ushort(v[5])) << 16);
+  u.w = uint32_t(__half_as_ushort(v[6])) | (uint32_t(__half_as_ushort(v[7])) << 16);
+  *reinterpret_cast<uint4*>(dst) = u;
+}
+
+// Row exponents and row slices of A (rows x kdim): e[q][i], and the A tiles of every slice
+// (zero padding to rows_pad x k_pad). One block per row; a thread cuts 8 consecutive K.
 __global__ void oz_slice_rows_kernel(Mat A, int rows, int kdim, int rows_pad, int k_pad, int nb,
                                      const int* __restrict__ map, int* __restrict__ e,
                                      __half* __restrict__ out) {
@@ -109,12 +137,20 @@ __global__ void oz_slice_rows_kernel(Mat A, int rows, int kdim, int rows_pad, in
   const int ex = scale_exp(red[0]);
   if (threadIdx.x == 0) e[size_t(q) * rows_pad + i] = ex;
   const size_t plane = size_t(nb) * rows_pad * k_pad;
-  for (int k = threadIdx.x; k < k_pad; k += blockDim.x) {
-    __half d[OZ_S];
-    slice_digits((i < rows && k < kdim) ? row[k] : 0.0, ex, d);
-    const size_t o = (size_t(q) * rows_pad + i) * k_pad + k;
+  const int kt = k_pad / OZ_KB;
+  __half* tile_row = out + (size_t(q) * (rows_pad / OZ_BM) + i / OZ_BM) * kt * (OZ_BM * OZ_KB);
+  for (int k8 = threadIdx.x * 8; k8 < k_pad; k8 += blockDim.x * 8) {
+    __half d[8][OZ_S];
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) out[s * plane + o] = d[s];
+    for (int u = 0; u < 8; ++u) slice_digits((i < rows && k8 + u < kdim) ? row[k8 + u] : 0.0, ex, d[u]);
+    __half* dst = tile_row + size_t(k8 / OZ_KB) * (OZ_BM * OZ_KB) + tile_off(i % OZ_BM, k8 % OZ_KB);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      __half v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = d[u][s];
+      store8(dst + s * plane, v);
+    }
   }
 }
 
@@ -132,28 +168,37 @@ __global__ void oz_colexp_kernel(Mat B, int kdim, int cols, int cols_pad, const 
   f[size_t(q) * cols_pad + j] = scale_exp(E);
 }
 
-// Column slices of B, transposed: out[t][q][j][k] = slice t of B[k][j] 2^-f_j. 32 x 32 tiles
-// through shared memory keep both the reads (along j) and the writes (along k) coalesced.
+// Column slices of B, transposed into the B tiles (row j of a tile = column j of B). A block
+// takes 32 columns x 32 K through shared memory (coalesced reads along j); a thread then cuts
+// 8 consecutive K of one column.
 __global__ void oz_slice_cols_kernel(Mat B, int kdim, int cols, int k_pad, int cols_pad, int nb,
                                      const int* __restrict__ map, const int* __restrict__ f,
                                      __half* __restrict__ out) {
   __shared__ double tile[32][33];
   const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32, q = blockIdx.z;
   const double* base = B.p + mat_of(map, q) * B.stride;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    const int k = k0 + r, j = j0 + tx;
-    tile[r][tx] = (k < kdim && j < cols) ? base[int64_t(k) * B.ld + j] : 0.0;
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int r = e / 32, c = e % 32;  // r: K, c: column
+    const int k = k0 + r, j = j0 + c;
+    tile[r][c] = (k < kdim && j < cols) ? base[int64_t(k) * B.ld + j] : 0.0;
   }
   __syncthreads();
   const size_t plane = size_t(nb) * cols_pad * k_pad;
-  for (int r = ty; r < 32; r += 8) {
-    const int j = j0 + r, k = k0 + tx;
-    __half d[OZ_S];
-    slice_digits(tile[tx][r], f[size_t(q) * cols_pad + j], d);
-    const size_t o = (size_t(q) * cols_pad + j) * k_pad + k;
+  const int kt = k_pad / OZ_KB;
+  const int c = threadIdx.x % 32, k8 = (threadIdx.x / 32) * 8;  // blockDim 128: 32 columns x 4 chunks
+  const int j = j0 + c;
+  const int fx = f[size_t(q) * cols_pad + j];
+  __half d[8][OZ_S];
 #pragma unroll
-    for (int t = 0; t < OZ_S; ++t) out[t * plane + o] = d[t];
+  for (int u = 0; u < 8; ++u) slice_digits(tile[k8 + u][c], fx, d[u]);
+  __half* dst = out + ((size_t(q) * (cols_pad / OZ_BN) + j / OZ_BN) * kt + k0 / OZ_KB) * (OZ_BN * OZ_KB) +
+                tile_off(j % OZ_BN, k8);
+#pragma unroll
+  for (int t = 0; t < OZ_S; ++t) {
+    __half v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = d[u][t];
+    store8(dst + t * plane, v);
   }
 }
 
@@ -161,14 +206,15 @@ struct OzParams {
   int M, N;                  // output rows and columns
   int m_pad, n_pad, k_pad;   // padded to 128 / 64 / 64
   int mt, nt;                // 128-row / 64-column tiles per matrix
-  int planeA, planeB;        // rows of one slice plane in the A / B tensor maps
+  const __half* sa;          // A tiles [OZ_S][batch][mt][kt][OZ_BM x OZ_KB]
+  const __half* sb;          // B tiles [OZ_S][batch][nt][kt][OZ_BN x OZ_KB]
+  size_t planeA, planeB;     // halves per slice plane
   const int* map;            // batch index -> matrix of C and D (null: identity)
   const int* e;              // [batch][m_pad] row exponents of A
   const int* f;              // [batch][n_pad] column exponents of B
   Mat D;                     // addend (may alias C; p null: none)
   int zr0, zr1;              // rows [zr0, zr1) of D read as zero
   MatOut C;
-  double alpha, beta;
   int* err;
 };
 
@@ -180,19 +226,22 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   lo = __fadd_rn(lo, e);
 }
 
-// One 128 x 64 output tile of one matrix per CTA. K blocks of 64 are loaded one at a time
-// (all slices of A and B: 168 KB); every 2 K blocks (a 128-wide exact chunk) the epilogue
-// drains the OZ_S level accumulators into float-float registers.
+// One 128 x 64 output tile of one matrix per CTA. K blocks of 32 (all slices of A and B: 84 KB)
+// go through a two-stage ring, so the copies of one block overlap the MMAs of the other; every
+// OZ_CHUNK blocks (a 128-wide exact chunk) the epilogue drains the OZ_S level accumulators into
+// float-float registers level by level, and the MMAs of the next chunk start on a level as
+// soon as it has been drained.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
+    oz_gemm_kernel(const __grid_constant__ OzParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGE);
-  uint64_t* full = bars;       // stage loaded
-  uint64_t* empty = bars + 1;  // stage consumed by the MMAs
-  uint64_t* accf = bars + 2;   // chunk accumulators ready
-  uint64_t* acce = bars + 3;   // chunk accumulators drained
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+  // (offset arithmetic on the shared array keeps the pointers in the shared address space)
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE);
+  uint64_t* full = bars;                   // [OZ_STAGES] stage loaded
+  uint64_t* empty = bars + OZ_STAGES;      // [OZ_STAGES] stage consumed by the MMAs
+  uint64_t* accf = bars + 2 * OZ_STAGES;   // chunk accumulators ready
+  uint64_t* acce = accf + 1;               // [OZ_S] level drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + OZ_S);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -200,17 +249,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int b = t / (p.mt * p.nt), rem = t % (p.mt * p.nt);  // b: index within the product batch
   const int mb = rem / p.nt, nbk = rem % p.nt;
   const int nkb = p.k_pad / OZ_KB;
-  const int nchunk = (nkb + 1) / 2;
+  const int nchunk = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    ptx::mbar_init(full, 1);
-    ptx::mbar_init(empty, 1);
+    for (int q = 0; q < OZ_STAGES; ++q) {
+      ptx::mbar_init(&full[q], 1);
+      ptx::mbar_init(&empty[q], 1);
+    }
     ptx::mbar_init(accf, 1);
-    ptx::mbar_init(acce, 4);
+    for (int L = 0; L < OZ_S; ++L) ptx::mbar_init(&acce[L], 4);
     ptx::fence_barrier_init();
-    ptx::tma_prefetch_desc(&tmA);
-    ptx::tma_prefetch_desc(&tmB);
   }
   if (warp == 1) {
     ptx::tmem_alloc(tslot, 512);
@@ -220,53 +269,63 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int rowA = b * p.m_pad + mb * OZ_BM;  // row of the (s = 0) slice plane
-  const int rowB = b * p.n_pad + nbk * OZ_BN;
+  const __half* tA = p.sa + (size_t(b) * p.mt + mb) * nkb * (OZ_BM * OZ_KB);  // slice 0, K block 0
+  const __half* tB = p.sb + (size_t(b) * p.nt + nbk) * nkb * (OZ_BN * OZ_KB);
 
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < nkb && !s_abort; ++kb) {
-        if (kb > 0 && !ptx::mbar_wait(empty, (kb - 1) & 1, OZ_WAIT_NS)) {
+        const int q = kb % OZ_STAGES, use = kb / OZ_STAGES;
+        if (use > 0 && !ptx::mbar_wait(&empty[q], (use - 1) & 1, OZ_WAIT_NS)) {
           atomicExch(p.err, 1);
           s_abort = 1;
           break;
         }
-        ptx::mbar_arrive_expect_tx(full, OZ_STAGE);
+        uint8_t* st = smem + q * OZ_STAGE;
+        ptx::mbar_arrive_expect_tx(&full[q], OZ_STAGE);
 #pragma unroll
         for (int s = 0; s < OZ_S; ++s) {
-          ptx::tma_load_2d(smem + s * OZ_A_BYTES, &tmA, full, kb * OZ_KB, s * p.planeA + rowA);
-          ptx::tma_load_2d(smem + OZ_S * OZ_A_BYTES + s * OZ_B_BYTES, &tmB, full, kb * OZ_KB, s * p.planeB + rowB);
+          ptx::bulk_load(st + s * OZ_A_BYTES, tA + s * p.planeA + size_t(kb) * (OZ_BM * OZ_KB), OZ_A_BYTES, &full[q]);
+          ptx::bulk_load(st + OZ_S * OZ_A_BYTES + s * OZ_B_BYTES, tB + s * p.planeB + size_t(kb) * (OZ_BN * OZ_KB),
+                         OZ_B_BYTES, &full[q]);
         }
         issued = kb + 1;
       }
-      if (issued > 0) ptx::mbar_wait(full, (issued - 1) & 1, OZ_WAIT_NS);  // the last copies landed
+      // every copy issued has landed before the CTA can exit
+      for (int kb = std::max(0, issued - OZ_STAGES); kb < issued; ++kb)
+        ptx::mbar_wait(&full[kb % OZ_STAGES], (kb / OZ_STAGES) & 1, OZ_WAIT_NS);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f16_f32(OZ_BM, OZ_BN);
       bool ok = true;
       for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int c = kb / 2;
-        const bool first = kb % 2 == 0, last = kb % 2 == 1 || kb == nkb - 1;
-        if (first && c > 0 && !ptx::mbar_wait(acce, (c - 1) & 1, OZ_WAIT_NS)) { ok = false; break; }
-        if (!ptx::mbar_wait(full, kb & 1, OZ_WAIT_NS)) { ok = false; break; }
+        const int q = kb % OZ_STAGES, use = kb / OZ_STAGES;
+        const int c = kb / OZ_CHUNK;
+        const bool first = kb % OZ_CHUNK == 0, last = kb % OZ_CHUNK == OZ_CHUNK - 1 || kb == nkb - 1;
+        if (!ptx::mbar_wait(&full[q], use & 1, OZ_WAIT_NS)) { ok = false; break; }
         ptx::tc_fence_after();
-        const uint32_t base = ptx::smem_u32(smem);
-        for (int L = 0; L < OZ_S; ++L) {
+        const uint32_t base = ptx::smem_u32(smem + q * OZ_STAGE);
+        for (int L = 0; L < OZ_S && ok; ++L) {
+          // the first block of a chunk overwrites level L: wait until the epilogue drained it
+          if (first && c > 0) {
+            if (!ptx::mbar_wait(&acce[L], (c - 1) & 1, OZ_WAIT_NS)) { ok = false; break; }
+            ptx::tc_fence_after();
+          }
           const uint32_t acc = tmem + L * OZ_BN;
           for (int s = 0; s <= L; ++s) {
-            const int tt = L - s;
-            const uint64_t dA = ptx::sw128_kmajor_desc(base + s * OZ_A_BYTES);
-            const uint64_t dB = ptx::sw128_kmajor_desc(base + OZ_S * OZ_A_BYTES + tt * OZ_B_BYTES);
+            const uint64_t dA = ptx::plain_kmajor_desc(base + s * OZ_A_BYTES, 128, 512);
+            const uint64_t dB = ptx::plain_kmajor_desc(base + OZ_S * OZ_A_BYTES + (L - s) * OZ_B_BYTES, 128, 512);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4;
+            for (int kk = 0; kk < OZ_KB / 16; ++kk) {
+              const uint64_t adv = uint64_t(kk * 256) >> 4;  // 16 K = two core matrices = 256 B
               ptx::mma_f16(acc, dA + adv, dB + adv, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
             }
           }
         }
-        ptx::mma_commit(empty);
+        if (!ok) break;
+        ptx::mma_commit(&empty[q]);
         if (last) ptx::mma_commit(accf);
       }
       if (!ok) {
@@ -277,6 +336,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else {
     // Thread = output row (TMEM lane); hi/lo hold the float-float running sum of its 64 columns.
     const int lane_base = 32 * (warp & 3);
+    {  // bring this thread's row of the addend tile into L2 while the MMAs run
+      const int i = mb * OZ_BM + lane_base + lane;
+      if (p.D.p && i < p.M && (i < p.zr0 || i >= p.zr1)) {
+        const double* drow = p.D.p + mat_of(p.map, b) * p.D.stride + int64_t(i) * p.D.ld + nbk * OZ_BN;
+        const int ncol = min(OZ_BN, p.N - nbk * OZ_BN);
+        for (int j = 0; j < ncol; j += 16) asm volatile("prefetch.global.L2 [%0];" ::"l"(drow + j));
+      }
+    }
     float hi[OZ_BN], lo[OZ_BN];
 #pragma unroll
     for (int j = 0; j < OZ_BN; ++j) hi[j] = lo[j] = 0.0f;
@@ -291,44 +358,71 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int h = 0; h < 2; ++h) {
           uint32_t r[32];
           ptx::tmem_ld_32x32b_x32(tmem + (uint32_t(lane_base) << 16) + uint32_t(L * OZ_BN + 32 * h), r);
+          if (h == 1) {  // level L is in registers: the MMAs of the next chunk may overwrite it
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&acce[L]);
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) ff_add(hi[32 * h + j], lo[32 * h + j], __fmul_rn(__uint_as_float(r[j]), sc));
         }
       }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(acce);
     }
     if (!ok) {
       atomicExch(p.err, 3);
     } else {
       // Every MMA has completed (the last accf phase), so the stage buffer is free: each warp
-      // stages its 32 rows x 64 columns of C there and writes them row by row, coalesced.
+      // stages its 32 rows x 64 columns there (hi, lo as floats; the addend tile in FP64) and
+      // writes C row by row, coalesced. C = (hi + lo) 2^(e_i + f_j - 14) + D: the scaled
+      // doubles come from the float bits, leaving one or two FP64 adds per element.
       const int cb = mat_of(p.map, b);
       const int i = mb * OZ_BM + lane_base + lane;
-      const double rs = pow2d((i < p.M ? p.e[size_t(b) * p.m_pad + i] : 0) - 14);  // row scale
-      double* stile = reinterpret_cast<double*>(smem) + (warp & 3) * 32 * (OZ_BN + 1);
+      const int ei = (i < p.M ? p.e[size_t(b) * p.m_pad + i] : 0) - 14;
+      float2* stile = reinterpret_cast<float2*>(smem) + (warp & 3) * 32 * (OZ_BN + 1);
+      double* sd = reinterpret_cast<double*>(smem + 4 * 32 * (OZ_BN + 1) * sizeof(float2)) + (warp & 3) * 32 * OZ_BN;
 #pragma unroll
-      for (int j = 0; j < OZ_BN; ++j) stile[lane * (OZ_BN + 1) + j] = (double(hi[j]) + double(lo[j])) * rs;
+      for (int j = 0; j < OZ_BN; ++j) stile[lane * (OZ_BN + 1) + j] = make_float2(hi[j], lo[j]);
+      if (p.D.p) {  // loads only, 8 rows in flight at a time (C may alias D)
+#pragma unroll 1
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+          double t[8][2];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const int ir = mb * OZ_BM + lane_base + r0 + r;
+            const bool use = ir < p.M && (ir < p.zr0 || ir >= p.zr1);
+            const double* drow = p.D.p + cb * p.D.stride + int64_t(ir) * p.D.ld;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int jj = nbk * OZ_BN + 32 * h + lane;
+              t[r][h] = (use && jj < p.N) ? drow[jj] : 0.0;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) sd[(r0 + r) * OZ_BN + 32 * h + lane] = t[r][h];
+        }
+      }
       __syncwarp();
-      double cs[2];  // column scales of this lane's two columns
+      int fj[2];  // column exponents of this lane's two columns
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int jj = nbk * OZ_BN + 32 * h + lane;
-        cs[h] = pow2d(jj < p.N ? p.f[size_t(b) * p.n_pad + jj] : 0) * p.alpha;
+        fj[h] = jj < p.N ? p.f[size_t(b) * p.n_pad + jj] : 0;
       }
+#pragma unroll 2
       for (int r = 0; r < 32; ++r) {
         const int ir = mb * OZ_BM + lane_base + r;
-        if (ir >= p.M) break;
-        double* crow = p.C.p + cb * p.C.stride + int64_t(ir) * p.C.ld;
-        const double* drow =
-            (p.D.p && (ir < p.zr0 || ir >= p.zr1)) ? p.D.p + cb * p.D.stride + int64_t(ir) * p.D.ld : nullptr;
+        const int er = __shfl_sync(0xffffffffu, ei, r);
+        if (ir < p.M) {
+          double* crow = p.C.p + cb * p.C.stride + int64_t(ir) * p.C.ld;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int jj = nbk * OZ_BN + 32 * h + lane;
-          if (jj < p.N) {
-            const double v = stile[r * (OZ_BN + 1) + 32 * h + lane] * cs[h];
-            crow[jj] = drow ? fma(p.beta, drow[jj], v) : v;
+          for (int h = 0; h < 2; ++h) {
+            const int jj = nbk * OZ_BN + 32 * h + lane;
+            const float2 v = stile[r * (OZ_BN + 1) + 32 * h + lane];
+            double c = f32_scaled_to_f64(v.x, er + fj[h]) + f32_scaled_to_f64(v.y, er + fj[h]);
+            if (p.D.p) c += sd[r * OZ_BN + 32 * h + lane];
+            if (jj < p.N) crow[jj] = c;
           }
         }
       }
@@ -361,10 +455,11 @@ namespace {
 struct Caps {
   size_t a, b, e, f;
 };
-// Room for square n x n products and for the rank-64 updates of an n x gjcols elimination.
+// Room for square n x n products and for the rank-64 updates of an n x gjcols elimination
+// (K padded to OZ_KB <= 64 <= the 64-padded n).
 Caps caps_for(int n, int nb, int gjcols) {
-  const size_t mp = pad_to(n, OZ_BM), np = pad_to(n, OZ_BN), gp = pad_to(std::max(gjcols, 1), OZ_BN);
-  return {size_t(OZ_S) * nb * mp * np, size_t(OZ_S) * nb * std::max(np * np, gp * OZ_KB), size_t(nb) * mp,
+  const size_t mp = pad_to(n, OZ_BM), np = pad_to(std::max(n, 64), OZ_BN), gp = pad_to(std::max(gjcols, 1), OZ_BN);
+  return {size_t(OZ_S) * nb * mp * np, size_t(OZ_S) * nb * std::max(np * np, gp * 64), size_t(nb) * mp,
           size_t(nb) * std::max(np, gp)};
 }
 }  // namespace
@@ -418,14 +513,13 @@ lem_status tc_gemm_create(int n, int nb, int gjcols, cudaStream_t st, TcGemm** o
   return LEM_OK;
 }
 
-// C[m] = alpha A[m] B[m] + beta D[m] (D rows [zr0, zr1) taken as zero) for m = map[q],
-// q < nbatch (map a device array, or null for m = q): A is M x K, B is K x N, C and D M x N,
-// all row-major FP64 with the given leading dimensions and batch strides. D may alias C
-// (each element is read before it is written by the same thread); C must not overlap A or B.
+// C[m] = A[m] B[m] + D[m] (D null: no addend; D rows [zr0, zr1) taken as zero) for
+// m = map[q], q < nbatch (map a device array, or null for m = q): A is M x K, B is K x N, C and
+// D M x N, all row-major FP64 with the given leading dimensions and batch strides. A and B are
+// sliced before the product runs, so C may overlap them; D may alias C.
 lem_status tc_gemm_ex(TcGemm* g, int nbatch, const int* map, int M, int N, int K, const double* A, int64_t lda,
                       int64_t sA, const double* B, int64_t ldb, int64_t sB, const double* D, int64_t ldd,
-                      int64_t sD, int zr0, int zr1, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
-                      cudaStream_t st) {
+                      int64_t sD, int zr0, int zr1, double* C, int64_t ldc, int64_t sC, cudaStream_t st) {
   if (nbatch <= 0 || M <= 0 || N <= 0) return LEM_OK;
   const int m_pad = pad_to(M, OZ_BM), n_pad = pad_to(N, OZ_BN), k_pad = pad_to(std::max(K, 1), OZ_KB);
   if (nbatch > g->nb || size_t(OZ_S) * g->nb * m_pad * k_pad > g->a_cap ||
@@ -435,17 +529,9 @@ lem_status tc_gemm_ex(TcGemm* g, int nbatch, const int* map, int M, int N, int K
   const Mat mA{A, lda, sA}, mB{B, ldb, sB};
   oz_slice_rows_kernel<<<dim3(m_pad, nbatch), 256, 0, st>>>(mA, M, K, m_pad, k_pad, g->nb, map, g->e, g->sa);
   oz_colexp_kernel<<<dim3((n_pad + 127) / 128, nbatch), 128, 0, st>>>(mB, K, N, n_pad, map, g->f);
-  oz_slice_cols_kernel<<<dim3(n_pad / 32, k_pad / 32, nbatch), 256, 0, st>>>(mB, K, N, k_pad, n_pad, g->nb, map,
+  oz_slice_cols_kernel<<<dim3(n_pad / 32, k_pad / 32, nbatch), 128, 0, st>>>(mB, K, N, k_pad, n_pad, g->nb, map,
                                                                               g->f, g->sb);
   LEM_CUDA_TRY(cudaGetLastError());
-  // slice planes: A [OZ_S][nb][m_pad][k_pad], B [OZ_S][nb][n_pad][k_pad] (fp16, K contiguous)
-  CUtensorMap tmA, tmB;
-  const cuuint64_t dimsA[2] = {cuuint64_t(k_pad), cuuint64_t(OZ_S) * g->nb * m_pad};
-  const cuuint64_t dimsB[2] = {cuuint64_t(k_pad), cuuint64_t(OZ_S) * g->nb * n_pad};
-  const cuuint64_t strides[1] = {cuuint64_t(k_pad) * 2};
-  const cuuint32_t boxA[2] = {OZ_KB, OZ_BM}, boxB[2] = {OZ_KB, OZ_BN};
-  LEM_TRY(encode_f16_map(&tmA, g->sa, 2, dimsA, strides, boxA, "A slices"));
-  LEM_TRY(encode_f16_map(&tmB, g->sb, 2, dimsB, strides, boxB, "B slices"));
   OzParams p{};
   p.M = M;
   p.N = N;
@@ -454,28 +540,28 @@ lem_status tc_gemm_ex(TcGemm* g, int nbatch, const int* map, int M, int N, int K
   p.k_pad = k_pad;
   p.mt = m_pad / OZ_BM;
   p.nt = n_pad / OZ_BN;
-  p.planeA = g->nb * m_pad;
-  p.planeB = g->nb * n_pad;
+  p.sa = g->sa;
+  p.sb = g->sb;
+  p.planeA = size_t(g->nb) * m_pad * k_pad;
+  p.planeB = size_t(g->nb) * n_pad * k_pad;
   p.map = map;
   p.e = g->e;
   p.f = g->f;
-  p.D = Mat{beta != 0.0 ? D : nullptr, ldd, sD};
+  p.D = Mat{D, ldd, sD};
   p.zr0 = zr0;
   p.zr1 = zr1;
   p.C = MatOut{C, ldc, sC};
-  p.alpha = alpha;
-  p.beta = beta;
   p.err = g->err;
-  oz_gemm_kernel<<<nbatch * p.mt * p.nt, OZ_THREADS, OZ_SMEM, st>>>(tmA, tmB, p);
+  oz_gemm_kernel<<<nbatch * p.mt * p.nt, OZ_THREADS, OZ_SMEM, st>>>(p);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
 }
 
 // Square n x n matrices stored back to back.
 lem_status tc_gemm(TcGemm* g, int n, int nbatch, const int* map, const double* A, const double* B, const double* D,
-                   double* C, double alpha, double beta, cudaStream_t st) {
+                   double* C, cudaStream_t st) {
   const int64_t nn = int64_t(n) * n;
-  return tc_gemm_ex(g, nbatch, map, n, n, n, A, n, nn, B, n, nn, D, n, nn, 0, 0, C, n, nn, alpha, beta, st);
+  return tc_gemm_ex(g, nbatch, map, n, n, n, A, n, nn, B, n, nn, D, n, nn, 0, 0, C, n, nn, st);
 }
 
 // Error flag of the workspace's products (reads it after synchronising st).

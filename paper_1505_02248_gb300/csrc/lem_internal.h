@@ -133,7 +133,7 @@ void split_destroy(lem_ctx* ctx);
 lem_status split_check_error(lem_ctx* ctx);
 bool split_eligible(const lem_ctx* ctx);
 lem_status encode_f16_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                          const cuuint32_t* box, const char* what);
+                          const cuuint32_t* box, const char* what, int swizzle_bytes = 128);
 // multi-problem split steps (one residual and one GEMM launch per step for a whole batch)
 struct SplitBatch;
 bool split_batch_eligible(lem_ctx* const* ctxs, int n);
@@ -149,14 +149,13 @@ struct TcGemm;
 size_t tc_gemm_bytes(int n, int nb, int gjcols);
 lem_status tc_gemm_create(int n, int nb, int gjcols, cudaStream_t st, TcGemm** out);
 void tc_gemm_destroy(TcGemm* g, cudaStream_t st);
-// C = alpha A B + beta D on strided batches of row-major FP64 matrices (A M x K, B K x N)
+// C = A B + D (D optional) on strided batches of row-major FP64 matrices (A M x K, B K x N)
 lem_status tc_gemm_ex(TcGemm* g, int nbatch, const int* map, int M, int N, int K, const double* A, int64_t lda,
                       int64_t sA, const double* B, int64_t ldb, int64_t sB, const double* D, int64_t ldd,
-                      int64_t sD, int zr0, int zr1, double* C, int64_t ldc, int64_t sC, double alpha, double beta,
-                      cudaStream_t st);
+                      int64_t sD, int zr0, int zr1, double* C, int64_t ldc, int64_t sC, cudaStream_t st);
 // the same for square n x n matrices stored back to back
 lem_status tc_gemm(TcGemm* g, int n, int nbatch, const int* map, const double* A, const double* B, const double* D,
-                   double* C, double alpha, double beta, cudaStream_t st);
+                   double* C, cudaStream_t st);
 lem_status tc_gemm_check(TcGemm* g, cudaStream_t st);
 // builder.cu: whether propagators of a precision tier are built with the tensor-core products
 bool builder_uses_tc(int prec);

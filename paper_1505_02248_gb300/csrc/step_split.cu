@@ -909,14 +909,17 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// FP16 tiled tensor map, 128-byte swizzle (the layout of every tcgen05 operand tile here)
+// FP16 tiled tensor map with a 128-byte (default) or 64-byte swizzle: the canonical K-major
+// layouts of the tcgen05 operand tiles
 lem_status encode_f16_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                          const cuuint32_t* box, const char* what) {
+                          const cuuint32_t* box, const char* what, int swizzle_bytes) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return fail(LEM_ECUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, cuuint32_t(rank), base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(LEM_ECUDA, std::string("cuTensorMapEncodeTiled failed for ") + what +
                                                     " (CUresult " + std::to_string(int(r)) + ")");

@@ -72,6 +72,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, uint64_
       : "memory");
 }
 
+// untiled bulk copy of `bytes` contiguous bytes (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // multicast variants (thread-block clusters): the copy lands at the same shared-memory
 // offset, and completes bytes on the barrier at the same offset, in every CTA of cta_mask
 __device__ __forceinline__ void tma_load_2d_mc(void* dst, const void* tmap, uint64_t* bar, int c0, int c1,
@@ -209,6 +217,29 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   d |= uint64_t(1024 >> 4) << 32;            // stride byte offset: 1024 B between 8-row atoms
   d |= uint64_t(1) << 46;                    // descriptor version for tcgen05
   d |= uint64_t(2) << 61;                    // swizzle: 128 B
+  return d;
+}
+
+// K-major operand without swizzle: 8-row x 16-byte core matrices (128 contiguous bytes each),
+// lbo bytes between core matrices along K, sbo bytes between core matrices along M / N.
+__device__ __forceinline__ uint64_t plain_kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);        // start address, bits 0-13
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;      // leading byte offset
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;      // stride byte offset
+  d |= uint64_t(1) << 46;                         // descriptor version for tcgen05
+  return d;                                       // swizzle field 0: none
+}
+
+// The same for the 64-byte swizzled K-major layout: rows of 64 B (32 fp16 along K), 8-row
+// atoms of 512 B, the tile 512-B aligned.
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);   // start address, bits 0-13
+  d |= uint64_t(1) << 16;                    // leading byte offset (16 B, unused)
+  d |= uint64_t(512 >> 4) << 32;             // stride byte offset: 512 B between 8-row atoms
+  d |= uint64_t(1) << 46;                    // descriptor version for tcgen05
+  d |= uint64_t(4) << 61;                    // swizzle: 64 B
   return d;
 }
 
