@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
     ap.add_argument("--vside", type=int, default=1024, help="vardiff2d: mesh side")
     ap.add_argument("--lanes", type=int, default=16, help="batch512: concurrent lanes in the graph")
+    ap.add_argument("--tile", type=int, nargs=2, default=[32, 32], metavar=("TY", "TX"),
+                    help="advdiff2d: tile shape (rows, columns)")
+    ap.add_argument("--overlap", type=int, nargs=2, default=[8, 8], metavar=("HY", "HX"),
+                    help="advdiff2d: overlap per side (rows, columns)")
+    ap.add_argument("--vel", type=float, nargs=2, default=[1.0, 0.5], metavar=("AX", "AY"),
+                    help="advdiff2d: velocity (h = 1, dt = 4: Courant numbers 4 a)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
@@ -137,12 +143,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(side, max_seconds=20.0):
+def advdiff_workload(a, seed=1):
+    """The advdiff2d workload of the command line, and its name for the JSON line."""
+    from paper_1505_02248_gb300 import workloads as W
+    wl = W.advdiff2d(side=a.side, tile=tuple(a.tile), overlap=tuple(a.overlap), a=tuple(a.vel), seed=seed)
+    if tuple(a.tile) == (32, 32) and tuple(a.overlap) == (8, 8) and tuple(a.vel) == (1.0, 0.5) and a.side == 2048:
+        return wl, WORKLOAD
+    return wl, (f"advdiff2d_{a.side}x{a.side}_periodic_tile{a.tile[0]}x{a.tile[1]}_H{a.overlap[0]}x{a.overlap[1]}"
+                f"_C{4 * a.vel[0]:g}x{4 * a.vel[1]:g}_phi")
+
+
+def oracle_sample(a, max_seconds=20.0):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload: the shared
     propagator build once, then LEM steps restricted to a subset of tiles."""
     import oracle as O
-    from paper_1505_02248_gb300 import workloads as W
-    wl = W.advdiff2d(side=side)
+    wl, _ = advdiff_workload(a)
     X = O.assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
     wins = O.decompose(wl["shape"], wl["bc"], wl["tile"], wl["overlap"])
     t0 = time.perf_counter()
@@ -267,14 +282,14 @@ def run_reference(a):
     per = []
     cb = None
     for _ in range(a.warmup + a.steps):
-        cb = oracle_sample(a.side, max_seconds=4.0)
+        cb = oracle_sample(a, max_seconds=4.0)
         per.append(cb["value"])
     v = statistics.median(per[a.warmup:]) if len(per) > a.warmup else per[-1]
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle on a tile sample"},
+            "config": {"workload": advdiff_workload(a)[1], "impl": "FP64 CPU oracle on a tile sample"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -641,7 +656,7 @@ def main():
     dev = torch.device(f"cuda:{local}")
     L.load()
 
-    wl = W.advdiff2d(side=a.side, seed=1 + rank)
+    wl, workload_name = advdiff_workload(a, seed=1 + rank)
     npts = wl["u0"].size
     stream = torch.cuda.current_stream(dev)
     ctx = L.Lem.from_workload(wl, prec=a.prec, device=local, stream=stream.cuda_stream)
@@ -731,7 +746,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         fms, fn = fast.get_timing()
-        flops4 = 4 * 2.0 * 1024 * 2304 * 4096 * (a.side / 2048) ** 2
+        inf = fast.info()
+        flops4 = 4 * 2.0 * inf["n_int"] * inf["n_loc"] * (npts // inf["n_int"])
         alt = {"split_fast": {"value": npts * a.steps * a.inner / (e0.elapsed_time(e1) * 1e-3),
                               "unit": METRIC, "rel_l2_vs_fp64_gpu": float(torch.linalg.vector_norm(w - v) /
                                                                           torch.linalg.vector_norm(v)),
@@ -747,6 +763,11 @@ def main():
     tflops_peak, hbm_peak, peak_src = peaks()
     khash = kernel_source_hash()
     value = npts * a.inner * a.steps * world / (dev_ms_max * 1e-3)
+    info = ctx.info()
+    ntiles = npts // info["n_int"]
+    # algorithmic flop of one FP16 product over all windows: 2 n_int n_loc per window
+    flops1 = 2.0 * info["n_int"] * info["n_loc"] * ntiles
+    path = L.APPLY_PATHS[info["apply_path"]]
     line = {
         "metric": METRIC,
         "value": value,
@@ -760,27 +781,29 @@ def main():
         "vs_baseline": None,
         "dtype": {"split": "f16x3-split/f32-acc", "split_fast": "f16x2-split/f32-acc"}.get(a.prec, "f64"),
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": npts, "tiles": 4096 if a.side == 2048 else None,
-                   "propagator": "1024x2304 phi_1 (shared)", "lem_steps_per_step": a.inner,
-                   "prec": a.prec, "l2": "256 MiB write between timed steps",
+        "config": {"workload": workload_name, "nodes": npts, "tiles": ntiles,
+                   "propagator": f"{info['n_int']}x{info['n_loc']} phi_1 (shared)", "lem_steps_per_step": a.inner,
+                   "prec": a.prec, "apply_path": path, "l2": "256 MiB write between timed steps",
                    "parallelism": f"replicas x{world}", "build_ms": round(build_ms, 1)},
         # split: FP64->float-float, max|r| pass, (residual + GEMM) per LEM step, float-float->FP64;
         # FP64: residual, gather, GEMM, scatter per LEM step
-        "gpu_launches": a.steps * (3 + 2 * a.inner) if a.prec != "fp64" else a.steps * a.inner * 4,
+        "gpu_launches": a.steps * ((3 + 2 * a.inner) if path == "tc_split" else
+                                   a.inner * (2 if "gemv" in path else 4)),
     }
     if gemm_launches:
         avg_ms = gemm_ms / gemm_launches
-        if a.prec != "fp64":
+        if path == "tc_split":
             nprod = 6 if a.prec == "split" else 4  # FP16 products per split GEMM
-            flops = nprod * 2.0 * 1024 * 2304 * 4096 * (a.side / 2048) ** 2
+            flops = nprod * flops1
             line["roofline"] = {"kernel": "split_gemm_kernel (tcgen05 kind::f16)", "bound": "tensor",
                                 "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": tflops_peak,
                                 "unit": "TFLOP/s", "frac": flops / (avg_ms * 1e-3) / 1e12 / tflops_peak,
-                                "traffic": ncu_traffic(khash), "avg_launch_us": avg_ms * 1e3,
+                                "traffic": ncu_traffic(khash) if workload_name == WORKLOAD else None,
+                                "avg_launch_us": avg_ms * 1e3,
                                 "launches": gemm_launches, "peak_source": f"{peak_src} bf16 dense (fp16 same rate)",
                                 "kernel_hash": khash}
         else:
-            flops = 2.0 * 1024 * 2304 * 4096 * (a.side / 2048) ** 2
+            flops = flops1
             line["roofline"] = {"kernel": "dgemm_kernel (FP64 apply)", "bound": "alu",
                                 "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": 1.196, "unit": "TFLOP/s",
                                 "frac": flops / (avg_ms * 1e-3) / 1e12 / 1.196, "traffic": None,
@@ -798,7 +821,7 @@ def main():
             d["gemm_frac_of_peak"] = d["gemm_tflops"] / tflops_peak
         line["alt_tiers"] = alt
     if world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(a.side)
+        line["cpu_baseline"] = oracle_sample(a)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

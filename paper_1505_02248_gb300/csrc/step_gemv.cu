@@ -8,6 +8,7 @@
 //
 // Jacobi update: all tiles must read u^n, so in EXP mode the source is a copy of u^n and in
 // PHI mode the residual array (computed from u^n before this launch).
+#include <algorithm>
 #include <type_traits>
 
 #include "lem_internal.h"
@@ -65,11 +66,13 @@ template <typename PT>
 __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
                                                          const TileDesc* __restrict__ tiles,
                                                          const double* __restrict__ src, double* __restrict__ u,
-                                                         int64_t ny, int64_t nx, int accumulate) {
+                                                         int64_t ny, int64_t nx, int accumulate, int rsplit) {
   // the tile's window values, converted once to the propagator's precision
   extern __shared__ __align__(16) unsigned char wraw[];
   PT* w = reinterpret_cast<PT*>(wraw);
-  const int t = blockIdx.x;
+  // rsplit blocks share a tile, each taking a contiguous share of its owner rows: several
+  // waves of short blocks instead of one wave of long ones (a shorter tail)
+  const int t = blockIdx.x / rsplit, part = blockIdx.x % rsplit;
   const TileDesc td = tiles[t];
   const int wl = td.wext[0] * td.wext[1];
   for (int k = threadIdx.x; k < wl; k += blockDim.x) {
@@ -81,7 +84,9 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   }
   __syncthreads();
   const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
-  const int ie = td.iext[0] * td.iext[1];
+  const int ie_all = td.iext[0] * td.iext[1];
+  const int rows_per = (ie_all + rsplit - 1) / rsplit;
+  const int ib = part * rows_per, ie = min(ie_all, ib + rows_per);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   const int grp = lane / 8, gl = lane % 8;
   constexpr int V = 16 / sizeof(PT);
@@ -89,7 +94,7 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   const bool vec = (n_loc % V) == 0 && (wl % V) == 0;
   using Acc = typename std::conditional<sizeof(PT) == 8, AccD, AccF>::type;
   // every lane runs the same number of row iterations (the shuffles need the whole warp)
-  for (int i0 = warp * 4; i0 < ie; i0 += nw * 4) {
+  for (int i0 = ib + warp * 4; i0 < ie; i0 += nw * 4) {
     const int i = i0 + grp;
     const bool live = i < ie;
     const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
@@ -156,14 +161,19 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
   const unsigned nt = unsigned(ctx->tiles.size());
+  // about four waves of blocks (8 resident per SM), at least 32 owner rows per block
+  static int nsm = 0;
+  if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) nsm = 152;
+  const int rmax = std::max<int>(1, int(ctx->n_int / 32));
+  const int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
   if (f32)
-    gemv_tiles_kernel<float><<<nt, 256, smem, st>>>(ctx->d_P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, src, d_u,
-                                                    ctx->ny, ctx->nx, phi ? 1 : 0);
+    gemv_tiles_kernel<float><<<nt * rsplit, 256, smem, st>>>(ctx->d_P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, src,
+                                                             d_u, ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
   else
-    gemv_tiles_kernel<double><<<nt, 256, smem, st>>>(ctx->d_P, ctx->n_int, ctx->n_loc, ctx->d_tiles, src, d_u,
-                                                     ctx->ny, ctx->nx, phi ? 1 : 0);
+    gemv_tiles_kernel<double><<<nt * rsplit, 256, smem, st>>>(ctx->d_P, ctx->n_int, ctx->n_loc, ctx->d_tiles, src,
+                                                              d_u, ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
   ctx->timing_end(stop);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;

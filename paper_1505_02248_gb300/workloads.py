@@ -109,14 +109,17 @@ def heat1d(n: int = 1024, tile: int = 64, overlap: int = 16, mu: float = 10.0,
                 u0=u0, amps=amps, mu=mu, reaction=False)
 
 
-def advdiff2d(side: int = 2048, tile: int = 32, overlap: int = 8, nu: float = 5.0,
+def advdiff2d(side: int = 2048, tile=32, overlap=8, nu: float = 5.0,
               a=(1.0, 0.5), dt: float = 4.0, ell: float = 16.0, seed: int = 1) -> dict:
-    """a = (a_x, a_y); h = 1, so mu = nu dt = 20 and (C_x, C_y) = dt a = (4, 2) by default."""
+    """a = (a_x, a_y); h = 1, so mu = nu dt = 20 and (C_x, C_y) = dt a = (4, 2) by default.
+    ``tile`` and ``overlap`` take one value for both axes or a (y, x) pair (anisotropic
+    windows, e.g. a larger overlap along a fast vertical flow)."""
     coef = stencil_advdiff_2d(nu, a[0], a[1], 1.0)
     u0 = grf_2d((side, side), ell, seed).ravel()
+    tile = (tile, tile) if np.isscalar(tile) else tuple(tile)
+    overlap = (overlap, overlap) if np.isscalar(overlap) else tuple(overlap)
     return dict(name=f"advdiff2d_{side}", shape=(side, side), bc=("periodic", "periodic"),
-                coef=coef, dt=dt, tile=(tile, tile), overlap=(overlap, overlap), u0=u0,
-                reaction=False)
+                coef=coef, dt=dt, tile=tile, overlap=overlap, u0=u0, reaction=False)
 
 
 def vardiff2d(side: int = 1024, tile: int = 16, overlap: int = 6, ell_k: float = 32.0,

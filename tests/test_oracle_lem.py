@@ -247,3 +247,31 @@ def test_reaction_jacobian_is_derivative_of_residual():
         e = np.zeros(42); e[j] = eps
         fd = (residual(Xg, u + e, 0.4, True) - residual(Xg, u - e, 0.4, True)) / (2 * eps)
         assert np.allclose(J[:, j], fd, atol=1e-8)
+
+
+def test_column_windows_win_at_high_vertical_courant_number():
+    """Sec. 1 and Sec. 4.3: at a vertical Courant number far above the horizontal one, a
+    decomposition into whole columns (overlap only across columns), or windows that extend
+    further vertically, keeps LEM closer to the global step than square windows with more
+    nodes. The same windows lose once the flow turns horizontal, so the gain comes from
+    matching the overlap to the direction of transport. Reference: the periodic FFT step."""
+    from oracle import periodic2d_fft_step
+    side = 48
+    u0 = W.grf_2d((side, side), 6.0, 7).ravel()
+    cases = {"square": ((16, 16), (8, 8)), "tall": ((16, 16), (12, 4)), "columns": ((side, 8), (0, 4))}
+
+    def errors(cx, cy):
+        coef = W.stencil_advdiff_2d(2.0, cx, cy, 1.0)
+        X = assemble_operator((side, side), ("periodic", "periodic"), coef, 1.0)
+        ref = periodic2d_fft_step(u0.reshape(side, side), coef, 10).ravel()
+        out = {}
+        for k, (tile, H) in cases.items():
+            wins = decompose((side, side), ("periodic", "periodic"), tile, H)
+            out[k] = (rel_l2(lem_run(X, u0, wins, 10, "phi"), ref), max(len(w.M) for w in wins))
+        return out
+
+    v = errors(0.5, 6.0)
+    assert v["tall"][1] < v["square"][1] and v["columns"][1] < v["square"][1]
+    assert v["tall"][0] < v["square"][0] / 3 and v["columns"][0] < v["square"][0] / 2
+    h = errors(6.0, 0.5)
+    assert h["tall"][0] > 3 * h["square"][0] and h["columns"][0] > 3 * h["square"][0]
