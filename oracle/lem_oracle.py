@@ -16,7 +16,7 @@ What is here, in the paper's order and notation (dt-scaled throughout, X = dt*A)
   (Sec. 1 and Sec. 4 name the method; the degree 13 / theta_13 choice is Higham's 2005
   algorithm, stated here as a reading because the paper gives no degree or norm rule).
 * ``phi1`` -- phi_1(X) = (e^X - I) X^{-1} (Sec. 2, phi_k definition with the sum to k-1),
-  taken as the top-right block of exp([[X, I], [0, 0]]).
+  taken as the top-right block of exp([[X, I], [0, 0]]); ``phik`` the same for any k.
 * ``local_propagators`` / ``lem_step`` -- the LEM exponential-Euler step (Eq. lem and
   steps 1-3 of Sec. 3): each window advances its restricted problem (Eq. local_pb) and only
   the owner rows D_i are written back. Two readings of the artificial-boundary data:
@@ -25,6 +25,12 @@ What is here, in the paper's order and notation (dt-scaled throughout, X = dt*A)
   (variation-of-constants identity, Sec. 2), by dense matrices (small N),
   ``heat1d_dst_modes`` (1D Dirichlet Laplacian, closed form) and ``periodic2d_fft_step``
   (constant-coefficient periodic 2D operator, closed form via its Fourier symbol).
+
+* ``lem_step_rb3`` / ``lem_run_rb3`` -- a third-order exponential Rosenbrock step in LEM
+  form. Sec. 4.2 runs its nonlinear tests with a third-order exponential Rosenbrock method
+  without writing it out; the scheme taken is exprb32 (Hochbruck, Ostermann and Schweitzer,
+  2009): a phi_1 stage and a phi_3 correction, both applied window by window.
+  ``global_step_rb3`` / ``global_run_rb3`` are the same scheme on the whole mesh.
 
 Parity status: every function above is pinned in ``tests/test_oracle_*.py``.
 The reaction (u - u^3) Rosenbrock variant is pinned only by invariants and by agreement
@@ -40,9 +46,10 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = [
-    "THETA13", "pade13_coefficients", "squaring_count", "expm_pade13", "phi1",
+    "THETA13", "pade13_coefficients", "squaring_count", "expm_pade13", "phi1", "phik",
     "assemble_operator", "Window", "decompose", "local_propagators", "residual",
     "jacobian", "lem_step", "lem_run", "global_step", "global_run",
+    "rb3_defect", "lem_step_rb3", "lem_run_rb3", "global_step_rb3", "global_run_rb3",
     "heat1d_dst_modes", "heat1d_eigenvalues", "periodic2d_symbol", "periodic2d_fft_step",
     "rel_l2",
 ]
@@ -108,6 +115,20 @@ def phi1(X: np.ndarray) -> np.ndarray:
     Z[:n, :n] = X
     Z[:n, n:] = np.eye(n)
     return expm_pade13(Z)[:n, n:]
+
+
+def phik(X: np.ndarray, k: int) -> np.ndarray:
+    """phi_k(X) = sum_j X^j / (j + k)! (Sec. 2 phi_k, sum to k - 1): the top-right block of
+    exp(Z), Z the (k + 1) x (k + 1) block matrix with X in the top-left corner, identity
+    blocks on the first block superdiagonal and zeros elsewhere (the top block row of exp(Z)
+    is e^X, phi_1(X), ..., phi_k(X))."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    Z = np.zeros(((k + 1) * n, (k + 1) * n))
+    Z[:n, :n] = X
+    for j in range(k):
+        Z[j * n:(j + 1) * n, (j + 1) * n:(j + 2) * n] = np.eye(n)
+    return expm_pade13(Z)[:n, k * n:]
 
 
 # --------------------------------------------------------------------------- operator
@@ -217,7 +238,8 @@ def local_propagators(Xg: sp.csr_matrix, windows, mode: str = "phi", tiles=None)
 
     X_{M_i} is the principal submatrix of the dt-scaled global operator on M_i (the
     restriction with Dirichlet conditions at the artificial boundary). f = phi_1 for
-    mode 'phi' (the step applies it to the dt-scaled residual) and f = exp for mode 'exp'.
+    mode 'phi' (the step applies it to the dt-scaled residual), f = phi_3 for mode 'phi3'
+    (the correction stage of the third-order Rosenbrock step) and f = exp for mode 'exp'.
     Windows with identical local matrices reuse one result (memoisation only).
     ``tiles`` restricts the work to a subset of window indices (others are None).
     """
@@ -231,7 +253,12 @@ def local_propagators(Xg: sp.csr_matrix, windows, mode: str = "phi", tiles=None)
         key = (XM.shape, XM.indptr.tobytes(), XM.indices.tobytes(), XM.data.tobytes(),
                w.d_pos.tobytes())
         if key not in cache:
-            F = phi1(XM.toarray()) if mode == "phi" else expm_pade13(XM.toarray())
+            if mode == "phi":
+                F = phi1(XM.toarray())
+            elif mode == "phi3":
+                F = phik(XM.toarray(), 3)
+            else:
+                F = expm_pade13(XM.toarray())
             cache[key] = F[w.d_pos, :]
         out[i] = cache[key]
     return out
@@ -291,6 +318,42 @@ def lem_run(Xg, u0, windows, nsteps: int, mode: str = "phi", dt: float = 0.0,
     return u
 
 
+def rb3_defect(u, U, um, dt: float):
+    """dt (G(U) - G(u)) with G(v) = F(v) - J(u_m) v, the part of F(v) = A v + v - v^3 that the
+    frozen Jacobian J(u_m) = A + diag(1 - 3 u_m^2) leaves out. The linear parts cancel, so
+    the defect is pointwise: dt [(U - U^3) - (u - u^3) - (1 - 3 u_m^2)(U - u)]."""
+    return dt * ((U - U ** 3) - (u - u ** 3) - (1.0 - 3.0 * um ** 2) * (U - u))
+
+
+def lem_step_rb3(Xg, u, windows, props1, props3, dt: float, um):
+    """exprb32 in LEM form, with X_m = dt J(u_m) (the Jacobian at the last refresh):
+        U       = u + phi_1(X_m) dt F(u)               window by window, owner rows (Eq. lem)
+        u^{n+1} = U + 2 phi_3(X_m) dt (G(U) - G(u))   window by window, owner rows
+    Both stages read the whole previous stage (Jacobi, as in Sec. 3)."""
+    u = np.asarray(u, dtype=np.float64)
+    U = lem_step(Xg, u, windows, props1, "phi", dt, True)
+    d = rb3_defect(u, U, um, dt)
+    out = U.copy()
+    for i, w in enumerate(windows):
+        out[w.D] = U[w.D] + 2.0 * (props3[i] @ d[w.M])
+    return out
+
+
+def lem_run_rb3(Xg, u0, windows, nsteps: int, dt: float, refresh: int = 0):
+    """nsteps exprb32 LEM steps; the Jacobian (and both propagator sets) are rebuilt from
+    the current state every ``refresh`` steps (0 = only at the first step)."""
+    u = np.asarray(u0, dtype=np.float64).copy()
+    props1 = props3 = um = None
+    for n in range(nsteps):
+        if props1 is None or (refresh > 0 and n % refresh == 0):
+            um = u.copy()
+            J = jacobian(Xg, um, dt, True)
+            props1 = local_propagators(J, windows, "phi")
+            props3 = local_propagators(J, windows, "phi3")
+        u = lem_step_rb3(Xg, u, windows, props1, props3, dt, um)
+    return u
+
+
 # --------------------------------------------------------------------------- global reference
 def global_step(Xg, u, dt: float = 0.0, reaction: bool = False, J=None):
     """Global exponential-Euler step u + phi_1(J) dt F(u) with dense phi_1 (small N only).
@@ -313,6 +376,23 @@ def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, ref
         if J is None or (refresh > 0 and n % refresh == 0):
             J = jacobian(Xg, u, dt, reaction)
         u = global_step(Xg, u, dt, reaction, J=J)
+    return u
+
+
+def global_step_rb3(Xg, u, dt: float, um):
+    """exprb32 on the whole mesh with dense phi_1 and phi_3 of dt J(u_m) (small N only)."""
+    Jd = jacobian(Xg, um, dt, True).toarray()
+    U = u + phi1(Jd) @ residual(Xg, u, dt, True)
+    return U + 2.0 * (phik(Jd, 3) @ rb3_defect(u, U, um, dt))
+
+
+def global_run_rb3(Xg, u0, nsteps: int, dt: float, refresh: int = 0):
+    u = np.asarray(u0, dtype=np.float64).copy()
+    um = None
+    for n in range(nsteps):
+        if um is None or (refresh > 0 and n % refresh == 0):
+            um = u.copy()
+        u = global_step_rb3(Xg, u, dt, um)
     return u
 
 

@@ -471,7 +471,7 @@ lem_status lem_server_create(size_t hbm_budget_bytes, int device, lem_server** o
   s->budget = int64_t(hbm_budget_bytes ? hbm_budget_bytes : kDefaultBudget);
   {
     // request states come from the device's stream-ordered pool; keep freed blocks in it
-    // (up to the budget) instead of returning them to the driver at every synchronisation
+    // (up to the budget) instead of returning them to the CUDA driver at every synchronisation
     lem::DeviceGuard g(device);
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
