@@ -70,6 +70,16 @@ typedef enum { LEM_MODE_PHI = 0, LEM_MODE_EXP = 1 } lem_mode;
  * shared propagator runs the FP64 path. lem_get_info reports the path taken. */
 typedef enum { LEM_PREC_FP64 = 0, LEM_PREC_SPLIT = 1, LEM_PREC_SPLIT_FAST = 2 } lem_prec;
 
+/* LEM_SCHEME_EULER: one window-local phi_1 stage per step (Eq. lem; with the reaction the
+ * exponential Euler-Rosenbrock step of Sec. 4).
+ * LEM_SCHEME_RB3: the third-order exponential Rosenbrock step exprb32 (Sec. 4.2 uses a
+ * third-order exponential Rosenbrock method; Hochbruck, Ostermann and Schweitzer 2009):
+ *   U = u + phi_1(dt J_m) dt F(u),  u' = U + 2 phi_3(dt J_m) dt (G(U) - G(u)),  G = F - J_m,
+ * both stages window by window with per-class phi_1 and phi_3 propagators built together
+ * (J_m: the Jacobian at the last refresh). PHI mode only; runs on the batched GEMV (FP64
+ * propagators, or FP32 with LEM_PREC_SPLIT_FAST). */
+typedef enum { LEM_SCHEME_EULER = 0, LEM_SCHEME_RB3 = 1 } lem_scheme;
+
 /* How lem_step applies the propagators (lem_info.apply_path). */
 typedef enum {
   LEM_APPLY_FP64_GEMM = 0,   /* FP64, one gathered GEMM per class of tiles */
@@ -94,6 +104,7 @@ typedef struct {
   int prec;               /* lem_prec */
   int refresh;            /* reaction only: rebuild the Jacobian propagators every
                              `refresh` steps (0: build once at the first step) */
+  int scheme;             /* lem_scheme (0: the exponential Euler step of Eq. lem) */
 } lem_problem_desc;
 
 typedef struct lem_ctx lem_ctx;
@@ -143,6 +154,10 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
  * memory h_out. Rows follow the tile's owner nodes in row-major order, columns the window
  * nodes in row-major order. Errors: LEM_ENOTREADY (not built), LEM_EINVAL. */
 lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out);
+
+/* The same for the phi_3 propagator of class `cls` (LEM_SCHEME_RB3 contexts only; LEM_EINVAL
+ * otherwise): R_D phi_3(dt J_M), the correction stage of the third-order Rosenbrock step. */
+lem_status lem_get_propagator_phi3(lem_ctx* ctx, int64_t cls, double* h_out);
 
 /* Class of tile `tile` (row-major over the tile grid) or -1 on a bad index. */
 /* Load every class's propagator from host memory (FP64, nclasses x n_int x n_loc, the layout

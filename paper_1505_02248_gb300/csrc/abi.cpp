@@ -99,6 +99,10 @@ void free_ctx(lem_ctx* c) {
   cudaFree(c->d_class_order);
   cudaFree(c->d_P);
   cudaFree(c->d_P32);
+  cudaFree(c->d_P3);
+  cudaFree(c->d_P3_32);
+  cudaFree(c->d_um);
+  cudaFree(c->d_u0);
   cudaFree(c->d_r);
   cudaFree(c->d_U);
   cudaFree(c->d_Y);
@@ -139,6 +143,7 @@ lem_status adopt_propagators(lem_ctx* dst, lem_ctx* src, cudaEvent_t built) {
   const ClassDesc &a = dst->classes[0], &b = src->classes[0];
   const lem_problem_desc &da = dst->desc, &db = src->desc;
   bool same = da.ndim == db.ndim && da.mode == db.mode && da.dt == db.dt && da.reaction == 0 && db.reaction == 0 &&
+              da.scheme == LEM_SCHEME_EULER && db.scheme == LEM_SCHEME_EULER &&
               da.coef_stride == 0 && db.coef_stride == 0 && dst->n_loc == src->n_loc && dst->n_int == src->n_int;
   for (int k = 0; k < da.ndim && same; ++k)  // per mesh axis (a 1D problem has one)
     same = da.tile[k] == db.tile[k] && da.overlap[k] == db.overlap[k] && da.bc[k] == db.bc[k] &&
@@ -227,6 +232,11 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_class_order), sizeof(int32_t) * nt);
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_P), sizeof(double) * nc * c->n_int * c->n_loc);
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_r), sizeof(double) * c->npts);
+  if (s == LEM_OK && desc->scheme == LEM_SCHEME_RB3) {
+    s = dev_alloc(c, reinterpret_cast<void**>(&c->d_P3), sizeof(double) * nc * c->n_int * c->n_loc);
+    if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_um), sizeof(double) * c->npts);
+    if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_u0), sizeof(double) * c->npts);
+  }
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
   if (s != LEM_OK) { free_ctx(c); return s; }
   if (!desc->coef_stride) c->h_coef = hc;
@@ -240,7 +250,9 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   const bool many_classes = c->classes.size() * 8 > c->tiles.size();
   c->build_tc = builder_uses_tc(desc->prec);
   const bool split_tier = desc->prec == LEM_PREC_SPLIT || desc->prec == LEM_PREC_SPLIT_FAST;
-  if (split_tier && split_eligible(c)) {
+  if (desc->scheme == LEM_SCHEME_RB3) {  // two propagator sets per class: the batched GEMV
+    c->apply_path = desc->prec == LEM_PREC_SPLIT_FAST ? LEM_APPLY_F32_GEMV : LEM_APPLY_FP64_GEMV;
+  } else if (split_tier && split_eligible(c)) {
     c->apply_path = LEM_APPLY_TC_SPLIT;
     s = split_prepare(c);
     if (s != LEM_OK) { free_ctx(c); return s; }
@@ -308,8 +320,21 @@ lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out) {
   return LEM_OK;
 }
 
+lem_status lem_get_propagator_phi3(lem_ctx* ctx, int64_t cls, double* h_out) {
+  if (!ctx || !h_out) return fail(LEM_EINVAL, "NULL argument");
+  if (!ctx->d_P3) return fail(LEM_EINVAL, "no phi_3 propagators (scheme is not LEM_SCHEME_RB3)");
+  if (cls < 0 || cls >= int64_t(ctx->classes.size())) return fail(LEM_EINVAL, "class out of range");
+  if (!ctx->built) return fail(LEM_ENOTREADY, "propagators not built");
+  DeviceGuard g(ctx->device);
+  LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  LEM_CUDA_TRY(cudaMemcpy(h_out, ctx->d_P3 + cls * ctx->n_int * ctx->n_loc,
+                          sizeof(double) * ctx->n_int * ctx->n_loc, cudaMemcpyDeviceToHost));
+  return LEM_OK;
+}
+
 lem_status lem_set_propagators(lem_ctx* ctx, const double* h_P, const int* h_squarings) {
   if (!ctx || !h_P) return fail(LEM_EINVAL, "NULL argument");
+  if (ctx->d_P3) return fail(LEM_EINVAL, "a third-order Rosenbrock context builds both propagator sets itself");
   DeviceGuard g(ctx->device);
   const size_t n = size_t(ctx->classes.size()) * size_t(ctx->n_int) * size_t(ctx->n_loc);
   LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

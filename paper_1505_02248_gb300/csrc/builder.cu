@@ -315,6 +315,44 @@ struct TcGuard {
 };
 }  // namespace
 
+// Gauss-Jordan elimination of G = [Q | RHS] (nb matrices of n x gjcols): on exit the RHS
+// columns hold Q^{-1} RHS. With a tensor-core workspace the blocked form (FP64 panels,
+// rank-GJ_KB trailing products on tcgen05); otherwise one FP64 pivot step at a time.
+static lem_status solve_gj(lem_ctx* ctx, TcGemm* tcg, double* G, int n, int gjcols, int nb, Buf& ybuf, Buf& pivbuf) {
+  cudaStream_t st = ctx->stream;
+  if (tcg) {
+    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&ybuf.p), sizeof(double) * nb * n * GJ_KB, st));
+    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&pivbuf.p), sizeof(int) * nb * GJ_KB, st));
+    double* Y = ybuf.p;
+    int* piv = reinterpret_cast<int*>(pivbuf.p);
+    for (int k0 = 0; k0 < n; k0 += GJ_KB) {
+      const int kb = std::min(GJ_KB, n - k0);
+      LEM_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * nb * n * GJ_KB, st));
+      for (int c = 0; c < kb; ++c) {
+        bgj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y, piv, ctx->d_status);
+        bgj_elim_kernel<<<dim3((n + 3) / 4, nb), 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y);
+      }
+      const int m_r = gjcols - (k0 + kb);
+      bgj_swap_kernel<<<dim3((m_r + 255) / 256, nb), 256, 0, st>>>(G, n, gjcols, k0, kb, piv);
+      LEM_CUDA_TRY(cudaGetLastError());
+      double* T = G + (k0 + kb);  // trailing columns
+      const int64_t sG = int64_t(n) * gjcols;
+      LEM_TRY(tc_gemm_ex(tcg, nb, nullptr, n, m_r, kb, Y, GJ_KB, int64_t(n) * GJ_KB,  // A = Y
+                         T + int64_t(k0) * gjcols, gjcols, sG,                         // B = pivot rows
+                         T, gjcols, sG, k0, k0 + kb,                                   // D, rows K zero
+                         T, gjcols, sG, st));
+    }
+  } else {
+    for (int k = 0; k < n; ++k) {
+      gj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k, ctx->d_status);
+      int bx = std::max(1, std::min(8, (gjcols - k - 1 + 255) / 256));
+      gj_update_kernel<<<dim3(bx, n, nb), 256, 0, st>>>(G, n, gjcols, k);
+    }
+  }
+  LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
 // Build the propagators of classes [c0, c0 + nb) into P (nb x n_int x n_loc).
 static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_state) {
   cudaStream_t st = ctx->stream;
@@ -451,36 +489,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   }
   LEM_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   Buf ybuf, pivbuf;  // freed after the final synchronisation
-  if (tc.g) {
-    // blocked elimination: FP64 panels, rank-GJ_KB trailing updates on the tensor cores
-    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&ybuf.p), sizeof(double) * nb * n * GJ_KB, st));
-    LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&pivbuf.p), sizeof(int) * nb * GJ_KB, st));
-    double* Y = ybuf.p;
-    int* piv = reinterpret_cast<int*>(pivbuf.p);
-    for (int k0 = 0; k0 < n; k0 += GJ_KB) {
-      const int kb = std::min(GJ_KB, n - k0);
-      LEM_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * nb * n * GJ_KB, st));
-      for (int c = 0; c < kb; ++c) {
-        bgj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y, piv, ctx->d_status);
-        bgj_elim_kernel<<<dim3((n + 3) / 4, nb), 256, 0, st>>>(G, n, gjcols, k0, c, kb, Y);
-      }
-      const int m_r = gjcols - (k0 + kb);
-      bgj_swap_kernel<<<dim3((m_r + 255) / 256, nb), 256, 0, st>>>(G, n, gjcols, k0, kb, piv);
-      LEM_CUDA_TRY(cudaGetLastError());
-      double* T = G + (k0 + kb);                            // trailing columns
-      const int64_t sG = int64_t(n) * gjcols;
-      LEM_TRY(tc_gemm_ex(tc.g, nb, nullptr, n, m_r, kb, Y, GJ_KB, int64_t(n) * GJ_KB,  // A = Y
-                         T + int64_t(k0) * gjcols, gjcols, sG,                         // B = pivot rows
-                         T, gjcols, sG, k0, k0 + kb,                                   // D, rows K zero
-                         T, gjcols, sG, st));
-    }
-  } else {
-    for (int k = 0; k < n; ++k) {
-      gj_pivot_kernel<<<nb, 256, 0, st>>>(G, n, gjcols, k, ctx->d_status);
-      int bx = std::max(1, std::min(8, (gjcols - k - 1 + 255) / 256));
-      gj_update_kernel<<<dim3(bx, n, nb), 256, 0, st>>>(G, n, gjcols, k);
-    }
-  }
+  LEM_TRY(solve_gj(ctx, tc.g, G, n, gjcols, nb, ybuf, pivbuf));
   LEM_CUDA_TRY(cudaGetLastError());
   // R_T -> RT2 (ping) ; R_B -> B2 (ping) ; squarings per class (s differs per class:
   // classes that need fewer squarings are squared by a masked update; simplest: square each
@@ -565,6 +574,258 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   return LEM_OK;
 }
 
+// ---------------------------------------------------------------- phi_1 and phi_3 together
+// For the third-order Rosenbrock step each class needs phi_1(X) and phi_3(X). Both are blocks
+// of exp(Z), Z = [[X, I, 0, 0], [0, 0, I, 0], [0, 0, 0, I], [0, 0, 0, 0]] (top block row:
+// e^X, phi_1, phi_2, phi_3). Every polynomial in Z, and its inverse, has the form
+//   [[T, B0, B1, B2], [0, b0 I, b1 I, b2 I], [0, 0, b0 I, b1 I], [0, 0, 0, b0 I]]
+// (an "augmented" element: T and B_j n x n, b a scalar upper-triangular Toeplitz part), with
+//   (A C).T = A.T C.T,  (A C).B_j = A.T C.B_j + sum_{a <= j} c.b_{j-a} A.B_a,  b = a.b * c.b.
+// The scaling is moved onto the functions: with Xs = X / 2^s, the Pade-13 approximant runs on
+// Z(Xs) (unit identity blocks, so every weight and the Toeplitz parts are the same for every
+// class), and s doublings 2^k phi_k(2Y) = e^Y phi_k(Y) + sum_{j=1..k} phi_j(Y) / (k - j)!
+// bring phi_k(Xs) back to phi_k(X). s follows the same rule as the phi_1 build (the 1-norm of
+// the augmented matrix is max(|X|_1, 1)).
+struct Aug {
+  double* m[4];  // T, B0, B1, B2
+  double b[3];   // Toeplitz part (class independent)
+};
+
+static lem_status build_batch_phi3(lem_ctx* ctx, int c0, int nb, const double* d_state) {
+  cudaStream_t st = ctx->stream;
+  const int n = int(ctx->n_loc);
+  const int64_t nn = int64_t(n) * n;
+  std::vector<BatchClass> hbc(nb);
+  for (int b = 0; b < nb; ++b) {
+    const ClassDesc& c = ctx->classes[c0 + b];
+    hbc[b].rep = ctx->tiles[c.rep_tile];
+    hbc[b].whole[0] = c.whole[0];
+    hbc[b].whole[1] = c.whole[1];
+  }
+  constexpr int NAUG = 10;  // Z, Z2, Z4, Z6, W, W3, U, V, R, Rn
+  const int gjcols = 5 * n;
+  Buf scratch, bcbuf, normbuf, scalebuf, ybuf, pivbuf, mapbuf;
+  const size_t bytes = sizeof(double) * (size_t(NAUG) * 4 * nn + size_t(n) * gjcols) * nb;
+  LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scratch.p), bytes, st));
+  LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bcbuf.p), sizeof(BatchClass) * nb, st));
+  LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&normbuf.p), sizeof(double) * nb, st));
+  LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&scalebuf.p), sizeof(double) * nb, st));
+  BatchClass* d_bc = reinterpret_cast<BatchClass*>(bcbuf.p);
+  LEM_CUDA_TRY(cudaMemcpyAsync(d_bc, hbc.data(), sizeof(BatchClass) * nb, cudaMemcpyHostToDevice, st));
+  double* S = scratch.p;
+  auto aug = [&](int i) {
+    Aug a;
+    for (int q = 0; q < 4; ++q) a.m[q] = S + (size_t(i) * 4 + q) * nn * nb;
+    a.b[0] = a.b[1] = a.b[2] = 0.0;
+    return a;
+  };
+  Aug Z = aug(0), Z2 = aug(1), Z4 = aug(2), Z6 = aug(3), W = aug(4), W3 = aug(5), U = aug(6), V = aug(7),
+      R = aug(8), Rn = aug(9);
+  double* G = S + size_t(NAUG) * 4 * nn * nb;
+
+  // X = dt J_M, the 1-norms, s per class
+  const double* u = ctx->desc.reaction ? d_state : nullptr;
+  assemble_local_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(
+      Z.m[0], n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u, ctx->desc.dt);
+  LEM_CUDA_TRY(cudaMemsetAsync(normbuf.p, 0, sizeof(double) * nb, st));
+  norm1_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(Z.m[0], n,
+                                                           reinterpret_cast<unsigned long long*>(normbuf.p));
+  LEM_CUDA_TRY(cudaGetLastError());
+  std::vector<double> norms(nb), scales(nb);
+  LEM_CUDA_TRY(cudaMemcpyAsync(norms.data(), normbuf.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  LEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int> s(nb);
+  int smax = 0;
+  for (int b = 0; b < nb; ++b) {
+    const double nz = std::max(norms[b], 1.0);
+    int sb = 0;
+    while (nz > kTheta13 * std::ldexp(1.0, sb)) ++sb;
+    s[b] = sb;
+    smax = std::max(smax, sb);
+    ctx->squarings[c0 + b] = sb;
+    scales[b] = std::ldexp(1.0, -sb);
+  }
+  LEM_CUDA_TRY(cudaMemcpyAsync(scalebuf.p, scales.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+
+  const dim3 gsq = grid1(nn, nb);
+  auto lin = [&](double* out, std::initializer_list<std::pair<const double*, double>> terms, double diag,
+                 const double* wscale0) -> lem_status {
+    Lin L{};
+    L.nin = 0;
+    for (auto& t : terms) {
+      if (t.second == 0.0) continue;  // never read a buffer that is not needed (it may be unset)
+      L.in[L.nin] = t.first;
+      L.w[L.nin] = t.second;
+      ++L.nin;
+    }
+    L.diag = diag;
+    L.dscale = nullptr;
+    L.wscale0 = wscale0;
+    lincomb_kernel<<<gsq, 256, 0, st>>>(out, n, n, n, L);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LEM_OK : cuda_fail(e, "lincomb_kernel");
+  };
+  TcGuard tc;
+  tc.st = st;
+  if (ctx->build_tc) LEM_TRY(tc_gemm_create(n, nb, gjcols, st, &tc.g));
+  auto mm = [&](const double* A, const double* B, double* C, const double* D) -> lem_status {
+    if (tc.g) return tc_gemm(tc.g, n, nb, nullptr, A, B, D, C, st);
+    if (D && D != C) LEM_CUDA_TRY(cudaMemcpyAsync(C, D, sizeof(double) * nn * nb, cudaMemcpyDeviceToDevice, st));
+    LEM_CUDA_TRY(dgemm_sq(n, nb, A, B, C, 1.0, D ? 1.0 : 0.0, st));
+    return LEM_OK;
+  };
+  // C = A * B (C distinct from A and B)
+  auto amul = [&](const Aug& A, const Aug& B, Aug& C) -> lem_status {
+    LEM_TRY(mm(A.m[0], B.m[0], C.m[0], nullptr));
+    for (int j = 0; j < 3; ++j) {
+      LEM_TRY(mm(A.m[0], B.m[1 + j], C.m[1 + j], nullptr));
+      const double w0 = B.b[j], w1 = j >= 1 ? B.b[j - 1] : 0.0, w2 = j >= 2 ? B.b[j - 2] : 0.0;
+      if (w0 != 0.0 || w1 != 0.0 || w2 != 0.0)  // + sum_{a <= j} B.b[j - a] A.B_a
+        LEM_TRY(lin(C.m[1 + j], {{C.m[1 + j], 1.0}, {A.m[1], w0}, {A.m[2], w1}, {A.m[3], w2}}, 0.0, nullptr));
+    }
+    for (int j = 0; j < 3; ++j) {
+      double v = 0.0;
+      for (int a = 0; a <= j; ++a) v += A.b[a] * B.b[j - a];
+      C.b[j] = v;
+    }
+    return LEM_OK;
+  };
+  // C = sum w_i A_i + d I (C may be one of the A_i)
+  auto alin = [&](Aug& C, std::initializer_list<std::pair<const Aug*, double>> terms, double d) -> lem_status {
+    double nb3[3] = {d, 0.0, 0.0};
+    for (int q = 0; q < 4; ++q) {
+      Lin L{};
+      L.nin = 0;
+      for (auto& t : terms) {
+        L.in[L.nin] = t.first->m[q];
+        L.w[L.nin] = t.second;
+        ++L.nin;
+      }
+      L.diag = q == 0 ? d : 0.0;
+      lincomb_kernel<<<gsq, 256, 0, st>>>(C.m[q], n, n, n, L);
+    }
+    LEM_CUDA_TRY(cudaGetLastError());
+    for (auto& t : terms)
+      for (int j = 0; j < 3; ++j) nb3[j] += t.second * t.first->b[j];
+    for (int j = 0; j < 3; ++j) C.b[j] = nb3[j];
+    return LEM_OK;
+  };
+
+  // Z(Xs): T = X / 2^s, B = (I, 0, 0), Toeplitz part N (b = (0, 1, 0))
+  LEM_TRY(lin(Z.m[0], {{Z.m[0], 1.0}}, 0.0, scalebuf.p));
+  LEM_TRY(lin(Z.m[1], {}, 1.0, nullptr));
+  LEM_CUDA_TRY(cudaMemsetAsync(Z.m[2], 0, sizeof(double) * nn * nb, st));
+  LEM_CUDA_TRY(cudaMemsetAsync(Z.m[3], 0, sizeof(double) * nn * nb, st));
+  Z.b[0] = 0.0; Z.b[1] = 1.0; Z.b[2] = 0.0;
+  double bj[14];
+  for (int j = 0; j < 14; ++j) bj[j] = kPadeInt[j] / kPadeInt[0];
+  LEM_TRY(amul(Z, Z, Z2));
+  LEM_TRY(amul(Z2, Z2, Z4));
+  LEM_TRY(amul(Z4, Z2, Z6));
+  // U = Z (Z6 (b13 Z6 + b11 Z4 + b9 Z2) + b7 Z6 + b5 Z4 + b3 Z2 + b1 I)
+  LEM_TRY(alin(W, {{&Z6, bj[13]}, {&Z4, bj[11]}, {&Z2, bj[9]}}, 0.0));
+  LEM_TRY(amul(Z6, W, W3));
+  LEM_TRY(alin(W3, {{&W3, 1.0}, {&Z6, bj[7]}, {&Z4, bj[5]}, {&Z2, bj[3]}}, bj[1]));
+  LEM_TRY(amul(Z, W3, U));
+  // V = Z6 (b12 Z6 + b10 Z4 + b8 Z2) + b6 Z6 + b4 Z4 + b2 Z2 + b0 I
+  LEM_TRY(alin(W, {{&Z6, bj[12]}, {&Z4, bj[10]}, {&Z2, bj[8]}}, 0.0));
+  LEM_TRY(amul(Z6, W, V));
+  LEM_TRY(alin(V, {{&V, 1.0}, {&Z6, bj[6]}, {&Z4, bj[4]}, {&Z2, bj[2]}}, bj[0]));
+  // R = (V - U)^{-1} (V + U). With M = V - U = [[Ma, Mc], [0, Md]] and P = V + U likewise:
+  // R.T = Ma^{-1} Pa, R.B = Ma^{-1} (Pc - Mc g), g = Md^{-1} Pd (a Toeplitz solve).
+  LEM_TRY(alin(W, {{&V, 1.0}, {&U, -1.0}}, 0.0));   // M
+  LEM_TRY(alin(W3, {{&V, 1.0}, {&U, 1.0}}, 0.0));   // P
+  double g[3];
+  g[0] = W3.b[0] / W.b[0];
+  g[1] = (W3.b[1] - W.b[1] * g[0]) / W.b[0];
+  g[2] = (W3.b[2] - W.b[1] * g[1] - W.b[2] * g[0]) / W.b[0];
+  for (int j = 0; j < 3; ++j) {  // Pc_j - sum_{a <= j} Mc_a g_{j-a}
+    const double w0 = g[j], w1 = j >= 1 ? g[j - 1] : 0.0, w2 = j >= 2 ? g[j - 2] : 0.0;
+    LEM_TRY(lin(W3.m[1 + j], {{W3.m[1 + j], 1.0}, {W.m[1], -w0}, {W.m[2], -w1}, {W.m[3], -w2}}, 0.0, nullptr));
+  }
+  copy_cols_kernel<<<gsq, 256, 0, st>>>(G, gjcols, 0, W.m[0], n, 0, n, n);
+  for (int q = 0; q < 4; ++q) copy_cols_kernel<<<gsq, 256, 0, st>>>(G, gjcols, (1 + q) * n, W3.m[q], n, 0, n, n);
+  LEM_CUDA_TRY(cudaGetLastError());
+  LEM_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  LEM_TRY(solve_gj(ctx, tc.g, G, n, gjcols, nb, ybuf, pivbuf));
+  for (int q = 0; q < 4; ++q) copy_cols_kernel<<<gsq, 256, 0, st>>>(R.m[q], n, 0, G, gjcols, (1 + q) * n, n, n);
+  LEM_CUDA_TRY(cudaGetLastError());
+
+  // s doublings of (E, phi_1, phi_2, phi_3) per class. The scaled copies H_k = phi_k / 2^k and
+  // the addends D_k go to free scratch first, then phi_k' = E H_k + D_k and E' = E E.
+  double* H1 = Z2.m[0]; double* H2 = Z2.m[1]; double* H3 = Z2.m[2];
+  double* D2 = Z4.m[0]; double* D3 = Z4.m[1];
+  auto prep = [&](const Aug& X) -> lem_status {  // on every class (harmless for finished ones)
+    LEM_TRY(lin(H1, {{X.m[1], 0.5}}, 0.0, nullptr));
+    LEM_TRY(lin(H2, {{X.m[2], 0.25}}, 0.0, nullptr));
+    LEM_TRY(lin(H3, {{X.m[3], 0.125}}, 0.0, nullptr));
+    LEM_TRY(lin(D2, {{X.m[1], 0.25}, {X.m[2], 0.25}}, 0.0, nullptr));
+    LEM_TRY(lin(D3, {{X.m[1], 0.0625}, {X.m[2], 0.125}, {X.m[3], 0.125}}, 0.0, nullptr));
+    return LEM_OK;
+  };
+  std::vector<int> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s[a] > s[b]; });
+  const bool uniform = s[order.front()] == s[order.back()];
+  if (tc.g) {
+    const int* d_map = nullptr;
+    if (!uniform) {
+      LEM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&mapbuf.p), sizeof(int) * nb, st));
+      LEM_CUDA_TRY(cudaMemcpyAsync(mapbuf.p, order.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+      d_map = reinterpret_cast<const int*>(mapbuf.p);
+    }
+    for (int q = 0; q < smax; ++q) {
+      int nact = 0;
+      while (nact < nb && s[order[nact]] > q) ++nact;
+      LEM_TRY(prep(R));
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, R.m[0], H1, H1, Rn.m[1], st));
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, R.m[0], H2, D2, Rn.m[2], st));
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, R.m[0], H3, D3, Rn.m[3], st));
+      LEM_TRY(tc_gemm(tc.g, n, nact, d_map, R.m[0], R.m[0], nullptr, Rn.m[0], st));
+      std::swap(R, Rn);
+    }
+    for (int b = 0; b < nb; ++b) {  // classes that stopped an odd number of steps early
+      if ((smax - s[b]) % 2 == 0) continue;
+      for (int q = 0; q < 4; ++q)
+        LEM_CUDA_TRY(cudaMemcpyAsync(R.m[q] + b * nn, Rn.m[q] + b * nn, sizeof(double) * nn,
+                                     cudaMemcpyDeviceToDevice, st));
+    }
+  } else {
+    for (int q = 0; q < smax; ++q) {
+      LEM_TRY(prep(R));
+      for (int b = 0; b < nb; ++b) {
+        if (s[b] <= q) {  // finished: carry it into the other buffer
+          for (int k = 0; k < 4; ++k)
+            LEM_CUDA_TRY(cudaMemcpyAsync(Rn.m[k] + b * nn, R.m[k] + b * nn, sizeof(double) * nn,
+                                         cudaMemcpyDeviceToDevice, st));
+          continue;
+        }
+        const int64_t o = b * nn;
+        LEM_CUDA_TRY(cudaMemcpyAsync(Rn.m[1] + o, H1 + o, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+        LEM_CUDA_TRY(cudaMemcpyAsync(Rn.m[2] + o, D2 + o, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+        LEM_CUDA_TRY(cudaMemcpyAsync(Rn.m[3] + o, D3 + o, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
+        LEM_CUDA_TRY(dgemm_sq(n, 1, R.m[0] + o, H1 + o, Rn.m[1] + o, 1.0, 1.0, st));
+        LEM_CUDA_TRY(dgemm_sq(n, 1, R.m[0] + o, H2 + o, Rn.m[2] + o, 1.0, 1.0, st));
+        LEM_CUDA_TRY(dgemm_sq(n, 1, R.m[0] + o, H3 + o, Rn.m[3] + o, 1.0, 1.0, st));
+        LEM_CUDA_TRY(dgemm_sq(n, 1, R.m[0] + o, R.m[0] + o, Rn.m[0] + o, 1.0, 0.0, st));
+      }
+      std::swap(R, Rn);
+    }
+  }
+  const size_t pc = size_t(ctx->n_int) * ctx->n_loc;
+  extract_rows_kernel<<<grid1(ctx->n_int * ctx->n_loc, nb), 256, 0, st>>>(ctx->d_P + size_t(c0) * pc, ctx->n_int,
+                                                                         ctx->n_loc, R.m[1], n, n, 0, d_bc);
+  extract_rows_kernel<<<grid1(ctx->n_int * ctx->n_loc, nb), 256, 0, st>>>(ctx->d_P3 + size_t(c0) * pc, ctx->n_int,
+                                                                         ctx->n_loc, R.m[3], n, n, 0, d_bc);
+  LEM_CUDA_TRY(cudaGetLastError());
+  int status = 0;
+  LEM_CUDA_TRY(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status != 0) return fail(LEM_ENUMERIC, "singular Pade denominator (V - U) in the propagator build");
+  if (tc.g) LEM_TRY(tc_gemm_check(tc.g, st));
+  return LEM_OK;
+}
+
 lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state);
 
 lem_status build_propagators(lem_ctx* ctx, const double* d_state) {
@@ -578,17 +839,22 @@ lem_status build_propagators_impl(lem_ctx* ctx, const double* d_state) {
   if (ctx->desc.reaction && !d_state) return fail(LEM_EINVAL, "the reaction Jacobian needs the state");
   const int64_t nc = int64_t(ctx->classes.size());
   const int64_t n = ctx->n_loc;
-  const int nmat = ctx->desc.mode == LEM_MODE_PHI ? 19 : 11;
+  const bool rb3 = ctx->desc.scheme == LEM_SCHEME_RB3;
+  const int nmat = rb3 ? 45 : ctx->desc.mode == LEM_MODE_PHI ? 19 : 11;
   // batch size from a scratch budget of 8 GiB
-  const int gjc = ctx->desc.mode == LEM_MODE_PHI ? 3 * int(n) : 2 * int(n);
+  const int gjc = rb3 ? 5 * int(n) : ctx->desc.mode == LEM_MODE_PHI ? 3 * int(n) : 2 * int(n);
   const double per = double(nmat) * n * n * sizeof(double) +
                      (ctx->build_tc ? double(tc_gemm_bytes(int(n), 1, gjc)) + sizeof(double) * n * GJ_KB : 0.0);
   int64_t bmax = std::max<int64_t>(1, int64_t((8.0 * (1ull << 30)) / per));
   bmax = std::min<int64_t>(bmax, 65535);
   for (int64_t c0 = 0; c0 < nc; c0 += bmax) {
     int nb = int(std::min<int64_t>(bmax, nc - c0));
-    LEM_TRY(build_batch(ctx, int(c0), nb, d_state));
+    LEM_TRY(rb3 ? build_batch_phi3(ctx, int(c0), nb, d_state) : build_batch(ctx, int(c0), nb, d_state));
   }
+  // the third-order Rosenbrock step evaluates its defect with the Jacobian's state
+  if (rb3 && ctx->desc.reaction)
+    LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_um, d_state, sizeof(double) * ctx->npts, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
   ctx->built = true;
   ctx->build_gen++;
   ctx->steps_since_build = 0;

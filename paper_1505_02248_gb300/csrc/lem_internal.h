@@ -96,6 +96,10 @@ struct lem_ctx {
   lem::TileDesc* d_tiles = nullptr;
   int32_t* d_class_order = nullptr;
   double* d_P = nullptr;               // nclasses * n_int * n_loc
+  double* d_P3 = nullptr;              // third-order Rosenbrock: the phi_3 propagators, same layout
+  float* d_P3_32 = nullptr;            // FP32 copy of d_P3 for the reduced-precision GEMV
+  double* d_um = nullptr;              // third-order Rosenbrock: the state of the last Jacobian
+  double* d_u0 = nullptr;              // third-order Rosenbrock: u^n kept across the two stages
   float* d_P32 = nullptr;              // FP32 copy for the reduced-precision GEMV
   int p32_gen = -1;                    // build_gen the FP32 copy was made from
   int apply_path = 0;                  // lem_apply_path: how lem_step applies the propagators

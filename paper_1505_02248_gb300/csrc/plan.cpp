@@ -30,6 +30,9 @@ lem_status validate(const lem_problem_desc* d) {
   if (d->reaction != 0 && d->reaction != 1) return fail(LEM_EINVAL, "reaction must be 0 or 1");
   if (d->reaction && d->mode != LEM_MODE_PHI) return fail(LEM_EINVAL, "the reaction needs LEM_MODE_PHI");
   if (d->refresh < 0) return fail(LEM_EINVAL, "refresh must be >= 0");
+  if (d->scheme != LEM_SCHEME_EULER && d->scheme != LEM_SCHEME_RB3) return fail(LEM_EINVAL, "bad scheme");
+  if (d->scheme == LEM_SCHEME_RB3 && d->mode != LEM_MODE_PHI)
+    return fail(LEM_EINVAL, "the third-order Rosenbrock scheme needs LEM_MODE_PHI");
   return LEM_OK;
 }
 

@@ -83,6 +83,7 @@ std::string make_key(const lem_problem_desc& d, const std::vector<double>* coef,
   h = fnv1a(d.overlap, sizeof d.overlap, h);
   h = fnv1a(&d.mode, sizeof d.mode, h);
   h = fnv1a(&d.refresh, sizeof d.refresh, h);
+  h = fnv1a(&d.scheme, sizeof d.scheme, h);
   for (int k = 0; k < 5; ++k)
     if (!coef[k].empty()) h = fnv1a(coef[k].data(), coef[k].size() * sizeof(double), h);
   return std::to_string(h);

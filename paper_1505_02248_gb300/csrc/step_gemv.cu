@@ -127,6 +127,17 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   }
 }
 
+// The defect of the third-order Rosenbrock step, times two: 2 dt (G(U) - G(u)) with
+// G(v) = F(v) - J(u_m) v. The linear parts cancel, so it is pointwise:
+// 2 dt [(U - U^3) - (u - u^3) - (1 - 3 u_m^2)(U - u)].
+__global__ void rb3_defect_kernel(const double* __restrict__ U, const double* __restrict__ u,
+                                  const double* __restrict__ um, double dt, double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double Ui = U[i], ui = u[i], mi = um[i];
+    d[i] = 2.0 * dt * ((Ui - Ui * Ui * Ui) - (ui - ui * ui * ui) - (1.0 - 3.0 * mi * mi) * (Ui - ui));
+  }
+}
+
 __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     b[i] = __double2float_rn(a[i]);
@@ -141,6 +152,10 @@ lem_status gemv_prepare_f32(lem_ctx* ctx) {
   const int64_t n = int64_t(ctx->classes.size()) * ctx->n_int * ctx->n_loc;
   if (!ctx->d_P32) LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_P32), sizeof(float) * n));
   f64_to_f32_kernel<<<1024, 256, 0, ctx->stream>>>(ctx->d_P, ctx->d_P32, n);
+  if (ctx->d_P3) {
+    if (!ctx->d_P3_32) LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_P3_32), sizeof(float) * n));
+    f64_to_f32_kernel<<<1024, 256, 0, ctx->stream>>>(ctx->d_P3, ctx->d_P3_32, n);
+  }
   LEM_CUDA_TRY(cudaGetLastError());
   ctx->p32_gen = ctx->build_gen;
   return LEM_OK;
@@ -150,6 +165,9 @@ lem_status gemv_prepare_f32(lem_ctx* ctx) {
 lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   cudaStream_t st = ctx->stream;
   const bool phi = ctx->desc.mode == LEM_MODE_PHI;
+  const bool rb3 = ctx->desc.scheme == LEM_SCHEME_RB3 && ctx->desc.reaction;  // (linear: the defect is 0)
+  if (rb3)
+    LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_u0, d_u, sizeof(double) * ctx->npts, cudaMemcpyDeviceToDevice, st));
   const double* src;
   if (phi) {
     LEM_CUDA_TRY(launch_residual_fp64(ctx, ctx->d_r, d_u));
@@ -168,12 +186,19 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   const int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
-  if (f32)
-    gemv_tiles_kernel<float><<<nt * rsplit, 256, smem, st>>>(ctx->d_P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, src,
-                                                             d_u, ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
-  else
-    gemv_tiles_kernel<double><<<nt * rsplit, 256, smem, st>>>(ctx->d_P, ctx->n_int, ctx->n_loc, ctx->d_tiles, src,
-                                                              d_u, ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
+  auto gemv = [&](const double* P64, const float* P32, const double* x) {
+    if (f32)
+      gemv_tiles_kernel<float><<<nt * rsplit, 256, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x, d_u,
+                                                               ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
+    else
+      gemv_tiles_kernel<double><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x, d_u,
+                                                                ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
+  };
+  gemv(ctx->d_P, ctx->d_P32, src);
+  if (rb3) {  // second stage: u^{n+1} = U + 2 phi_3(dt J_m) dt (G(U) - G(u^n)), window by window
+    rb3_defect_kernel<<<1024, 256, 0, st>>>(d_u, ctx->d_u0, ctx->d_um, ctx->desc.dt, ctx->d_r, ctx->npts);
+    gemv(ctx->d_P3, ctx->d_P3_32, ctx->d_r);
+  }
   ctx->timing_end(stop);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;

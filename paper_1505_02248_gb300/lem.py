@@ -19,6 +19,7 @@ LEM_OK, LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA, LEM_EBUSY, LEM_ENOTREADY, LEM_ETIMEOU
 BC = {"dirichlet": 0, "periodic": 1}
 MODE = {"phi": 0, "exp": 1}
 PREC = {"fp64": 0, "split": 1, "split_fast": 2}
+SCHEME = {"euler": 0, "rb3": 1}
 
 
 class LemError(RuntimeError):
@@ -41,6 +42,7 @@ class ProblemDesc(C.Structure):
         ("mode", C.c_int),
         ("prec", C.c_int),
         ("refresh", C.c_int),
+        ("scheme", C.c_int),
     ]
 
 
@@ -75,6 +77,7 @@ SIGNATURES = [
     ("lem_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lem_step_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     ("lem_get_propagator", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    ("lem_get_propagator_phi3", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
     ("lem_set_propagators", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("lem_tile_class", C.c_int64, [C.c_void_p, C.c_int64]),
     ("lem_class_squarings", C.c_int, [C.c_void_p, C.c_int64]),
@@ -131,7 +134,7 @@ def check(status: int, what: str = "") -> None:
 
 
 def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec="fp64",
-              reaction=False, refresh=0):
+              reaction=False, refresh=0, scheme="euler"):
     """Build a ProblemDesc; returns (desc, keepalive) -- keep the second alive while used."""
     shape = tuple(int(s) for s in shape)
     nd = len(shape)
@@ -158,6 +161,7 @@ def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec=
     d.mode = MODE[mode]
     d.prec = PREC[prec]
     d.refresh = int(refresh)
+    d.scheme = SCHEME[scheme]
     return d, keep
 
 
@@ -176,10 +180,10 @@ class Lem:
     """One LEM context (lem_create ... lem_destroy) on a CUDA device."""
 
     def __init__(self, shape, bc, coef, dt, tile, overlap, mode="phi", prec="fp64",
-                 reaction=False, refresh=0, device=0, stream=None):
+                 reaction=False, refresh=0, device=0, stream=None, scheme="euler"):
         lib = load()
         self._lib = lib
-        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, prec, reaction, refresh)
+        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, prec, reaction, refresh, scheme)
         self.shape = tuple(int(s) for s in shape)
         self.npts = int(np.prod(self.shape))
         h = C.c_void_p()
@@ -241,6 +245,14 @@ class Lem:
         out = np.zeros((inf["n_int"], inf["n_loc"]))
         check(self._lib.lem_get_propagator(self._h, int(cls), out.ctypes.data_as(C.c_void_p)),
               "lem_get_propagator")
+        return out
+
+    def propagator_phi3(self, cls: int) -> np.ndarray:
+        """The phi_3 propagator of a class (third-order Rosenbrock contexts)."""
+        inf = self.info()
+        out = np.zeros((inf["n_int"], inf["n_loc"]))
+        check(self._lib.lem_get_propagator_phi3(self._h, int(cls), out.ctypes.data_as(C.c_void_p)),
+              "lem_get_propagator_phi3")
         return out
 
     def set_propagators(self, P: np.ndarray, squarings=None):
