@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--drain", type=float, default=120.0, help="serve: seconds to wait for completions")
     ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
     ap.add_argument("--vside", type=int, default=1024, help="vardiff2d: mesh side")
+    ap.add_argument("--scheme", default="euler", choices=["euler", "rb3"],
+                    help="vardiff2d: exponential Euler-Rosenbrock (phi_1) or the third-order exprb32 (phi_1 + phi_3)")
     ap.add_argument("--lanes", type=int, default=16, help="batch512: concurrent lanes in the graph")
     ap.add_argument("--tile", type=int, nargs=2, default=[32, 32], metavar=("TY", "TX"),
                     help="advdiff2d: tile shape (rows, columns)")
@@ -568,8 +570,11 @@ def run_small(a):
         wl, prec, name = W.heat1d(), "fp64", "heat1d_N1024_dirichlet_tile64_H16_fp64"
     else:
         wl, prec, name = W.vardiff2d(side=a.vside), a.prec, f"vardiff2d_{a.vside}_dirichlet_tile16_H6_reaction"
+        if a.scheme == "rb3":
+            name += "_rb3"
     npts = wl["u0"].size
-    ctx = L.Lem.from_workload(wl, prec=prec, stream=stream.cuda_stream)
+    ctx = L.Lem.from_workload(wl, prec=prec, stream=stream.cuda_stream,
+                              scheme=a.scheme if a.workload == "vardiff2d" else "euler")
     u = torch.tensor(wl["u0"], device=dev)
     t0 = time.perf_counter()
     ctx.build(u)
@@ -608,14 +613,17 @@ def run_small(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if path.startswith("fp64") else "f32-gemv/ff-acc",
             "data": "synthetic",
             "config": {"workload": name, "nodes": npts, "lem_steps_per_step": a.inner, "apply_path": path,
+                       "scheme": a.scheme if a.workload == "vardiff2d" else "euler",
                        "propagator_classes": info["nclasses"], "n_loc": info["n_loc"], "n_int": info["n_int"],
                        "build_s": round(build_s, 2), "l2": "256 MiB write between timed steps"},
-            "gpu_launches": a.steps * a.inner * (2 if "gemv" in path else 4),
+            "gpu_launches": a.steps * a.inner * ((2 if "gemv" in path else 4) + (3 if a.scheme == "rb3" else 0)),
             "e2e": {"value": npts * a.inner / (statistics.median(e2e) * 1e-3), "unit": METRIC,
                     "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts},
             "clocks": clk.summary()}
     if k_n and "gemv" in path:
         pbytes = (4 if path == "f32_gemv" else 8) * info["nclasses"] * info["n_int"] * info["n_loc"]
+        if a.scheme == "rb3":
+            pbytes *= 2  # phi_1 and phi_3 propagators, one GEMV each per step (timed together)
         ach = pbytes / (k_ms / k_n * 1e-3) / 1e9
         line["roofline"] = {"kernel": f"gemv_tiles_kernel ({path})", "bound": "hbm", "achieved": ach,
                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
