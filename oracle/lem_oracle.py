@@ -60,6 +60,13 @@ THETA13 = 5.371920351148152
 PADE_DEGREE = 13
 
 
+def _fp(x) -> np.ndarray:
+    """x as FP64, real or complex (complex problems, e.g. the Schroedinger test of Sec. 4.1,
+    run through the same functions)."""
+    x = np.asarray(x)
+    return x.astype(np.complex128 if np.iscomplexobj(x) else np.float64)
+
+
 def pade13_coefficients(m: int = PADE_DEGREE) -> list[float]:
     """Coefficients b_j of the numerator p_m(x) = sum_j b_j x^j of the [m/m] Pade
     approximant to e^x; the denominator is p_m(-x).
@@ -88,7 +95,7 @@ def expm_pade13(X: np.ndarray) -> np.ndarray:
     3. U (odd part) and V (even part) of p_13 from X^2, X^4, X^6;
     4. solve (V - U) R = (V + U); 5. square R s times.
     """
-    X = np.asarray(X, dtype=np.float64)
+    X = _fp(X)
     n = X.shape[0]
     s = squaring_count(float(np.abs(X).sum(axis=0).max()) if n else 0.0)
     X = X / (2.0 ** s)
@@ -109,9 +116,9 @@ def expm_pade13(X: np.ndarray) -> np.ndarray:
 
 def phi1(X: np.ndarray) -> np.ndarray:
     """phi_1(X) = sum_k X^k / (k+1)!: the top-right block of exp([[X, I], [0, 0]])."""
-    X = np.asarray(X, dtype=np.float64)
+    X = _fp(X)
     n = X.shape[0]
-    Z = np.zeros((2 * n, 2 * n))
+    Z = np.zeros((2 * n, 2 * n), dtype=X.dtype)
     Z[:n, :n] = X
     Z[:n, n:] = np.eye(n)
     return expm_pade13(Z)[:n, n:]
@@ -122,9 +129,9 @@ def phik(X: np.ndarray, k: int) -> np.ndarray:
     exp(Z), Z the (k + 1) x (k + 1) block matrix with X in the top-left corner, identity
     blocks on the first block superdiagonal and zeros elsewhere (the top block row of exp(Z)
     is e^X, phi_1(X), ..., phi_k(X))."""
-    X = np.asarray(X, dtype=np.float64)
+    X = _fp(X)
     n = X.shape[0]
-    Z = np.zeros(((k + 1) * n, (k + 1) * n))
+    Z = np.zeros(((k + 1) * n, (k + 1) * n), dtype=X.dtype)
     Z[:n, :n] = X
     for j in range(k):
         Z[j * n:(j + 1) * n, (j + 1) * n:(j + 2) * n] = np.eye(n)
@@ -133,7 +140,7 @@ def phik(X: np.ndarray, k: int) -> np.ndarray:
 
 # --------------------------------------------------------------------------- operator
 def _as_field(v, shape):
-    a = np.asarray(v, dtype=np.float64)
+    a = _fp(v)
     return np.broadcast_to(a, shape) if a.ndim == 0 else a.reshape(shape)
 
 
@@ -288,7 +295,7 @@ def lem_step(Xg, u, windows, props, mode: str = "phi", dt: float = 0.0,
     Only the owner rows D_i are written (buffer values discarded). ``tiles`` limits the
     update to a subset of windows; other entries of the result keep u^n.
     """
-    u = np.asarray(u, dtype=np.float64)
+    u = _fp(u)
     out = u.copy()
     sel = range(len(windows)) if tiles is None else tiles
     if mode == "phi":
@@ -309,7 +316,7 @@ def lem_run(Xg, u0, windows, nsteps: int, mode: str = "phi", dt: float = 0.0,
     computed at the first step only). With the reaction, the Jacobian and its propagators
     are rebuilt from the current state every ``refresh`` steps (0 = never after step 0):
     the exponential Euler-Rosenbrock step with a frozen Jacobian (Sec. 4)."""
-    u = np.asarray(u0, dtype=np.float64).copy()
+    u = _fp(u0).copy()
     props = None
     for n in range(nsteps):
         if props is None or (reaction and refresh > 0 and n % refresh == 0):
@@ -330,7 +337,7 @@ def lem_step_rb3(Xg, u, windows, props1, props3, dt: float, um):
         U       = u + phi_1(X_m) dt F(u)               window by window, owner rows (Eq. lem)
         u^{n+1} = U + 2 phi_3(X_m) dt (G(U) - G(u))   window by window, owner rows
     Both stages read the whole previous stage (Jacobi, as in Sec. 3)."""
-    u = np.asarray(u, dtype=np.float64)
+    u = _fp(u)
     U = lem_step(Xg, u, windows, props1, "phi", dt, True)
     d = rb3_defect(u, U, um, dt)
     out = U.copy()
@@ -342,7 +349,7 @@ def lem_step_rb3(Xg, u, windows, props1, props3, dt: float, um):
 def lem_run_rb3(Xg, u0, windows, nsteps: int, dt: float, refresh: int = 0):
     """nsteps exprb32 LEM steps; the Jacobian (and both propagator sets) are rebuilt from
     the current state every ``refresh`` steps (0 = only at the first step)."""
-    u = np.asarray(u0, dtype=np.float64).copy()
+    u = _fp(u0).copy()
     props1 = props3 = um = None
     for n in range(nsteps):
         if props1 is None or (refresh > 0 and n % refresh == 0):
@@ -365,7 +372,7 @@ def global_step(Xg, u, dt: float = 0.0, reaction: bool = False, J=None):
 
 
 def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, refresh: int = 0):
-    u = np.asarray(u0, dtype=np.float64).copy()
+    u = _fp(u0).copy()
     if not reaction:
         E = expm_pade13(Xg.toarray())
         for _ in range(nsteps):
@@ -387,7 +394,7 @@ def global_step_rb3(Xg, u, dt: float, um):
 
 
 def global_run_rb3(Xg, u0, nsteps: int, dt: float, refresh: int = 0):
-    u = np.asarray(u0, dtype=np.float64).copy()
+    u = _fp(u0).copy()
     um = None
     for n in range(nsteps):
         if um is None or (refresh > 0 and n % refresh == 0):
@@ -433,7 +440,7 @@ def periodic2d_fft_step(u2d: np.ndarray, coef_dt: dict, nsteps: int = 1) -> np.n
 
 def rel_l2(a, b) -> float:
     """||a - b||_2 / ||b||_2."""
-    a = np.asarray(a, dtype=np.float64).ravel()
-    b = np.asarray(b, dtype=np.float64).ravel()
+    a = _fp(a).ravel()
+    b = _fp(b).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))

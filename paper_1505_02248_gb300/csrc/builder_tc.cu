@@ -479,12 +479,9 @@ void tc_gemm_destroy(TcGemm* g, cudaStream_t st) {
 
 lem_status tc_gemm_create(int n, int nb, int gjcols, cudaStream_t st, TcGemm** out) {
   *out = nullptr;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM) != cudaSuccess)
-      return cuda_fail(cudaGetLastError(), "oz_gemm_kernel attributes");
-    attr_set = true;
-  }
+  // the shared-memory attribute is per device (cheap to set again)
+  if (cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "oz_gemm_kernel attributes");
   TcGemm* g = new TcGemm();
   const Caps c = caps_for(n, nb, gjcols);
   g->nb = nb;

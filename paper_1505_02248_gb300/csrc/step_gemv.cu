@@ -180,8 +180,8 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
   const unsigned nt = unsigned(ctx->tiles.size());
   // about four waves of blocks (8 resident per SM), at least 32 owner rows per block
-  static int nsm = 0;
-  if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) nsm = 152;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm < 1) nsm = 152;
   const int rmax = std::max<int>(1, int(ctx->n_int / 32));
   const int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
   cudaEvent_t stop;

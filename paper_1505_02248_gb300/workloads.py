@@ -152,3 +152,19 @@ def batch_problems(n: int = 512, seed: int = 3, side_max: int = 512) -> list:
         out.append(dict(name=f"batch{i}_{side}_t{tile}_H{H}", shape=(side, side), bc=("periodic", "periodic"),
                         coef=coef, dt=1.0, tile=(tile, tile), overlap=(H, H), u0=u0, reaction=False))
     return out
+
+
+def schrodinger1d(n: int = 400, L: float = 10.0, kappa: float = 10.0, mu: float = 2.0, tile: int = 80,
+                  overlap: int = 20, x0: float = -1.0, sigma: float = 0.5, seed: int = 5) -> dict:
+    """1D Schroedinger equation with a harmonic potential, c_t = (i/2) c_xx - i (kappa/2) x^2 c,
+    periodic on [-L/2, L/2) with n nodes, h = L / n, x_j = -L/2 + j h, centred second
+    differences (Sec. 4.1). Complex stencil: C = -i/h^2 - i kappa x^2 / 2 (per node),
+    W = E = i / (2 h^2). mu = dt / (2 h^2) is the stability parameter of the i/2 c_xx term, so
+    dt = 2 mu h^2. u0 = a Gaussian of width sigma centred at x0 (real; seed unused, kept for a
+    uniform generator signature)."""
+    h = L / n
+    x = -L / 2 + h * np.arange(n)
+    coef = {"C": -1j / h ** 2 - 1j * kappa * x ** 2 / 2, "W": 1j / (2 * h ** 2) + 0 * x, "E": 1j / (2 * h ** 2) + 0 * x}
+    u0 = np.exp(-(x - x0) ** 2 / (2 * sigma ** 2)).astype(np.complex128)
+    return dict(name=f"schrodinger1d_{n}", shape=(n,), bc=("periodic",), coef=coef, dt=2 * mu * h * h,
+                tile=(tile,), overlap=(overlap,), u0=u0, reaction=False, x=x, h=h)
