@@ -43,7 +43,8 @@ def parse():
                          "pieces (four products); fp64: the plain FP64 GPU path")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=2048)
-    ap.add_argument("--workload", default="advdiff2d", choices=["advdiff2d", "batch512", "serve", "heat1d", "vardiff2d"],
+    ap.add_argument("--workload", default="advdiff2d",
+                    choices=["advdiff2d", "batch512", "serve", "heat1d", "vardiff2d", "schrodinger1d"],
                     help="advdiff2d: one 2048^2 problem (default); batch512: 512 uneven problems under one "
                          "CUDA graph; serve: a Poisson stream of advance requests through the server")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
@@ -51,6 +52,7 @@ def parse():
     ap.add_argument("--drain", type=float, default=120.0, help="serve: seconds to wait for completions")
     ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
     ap.add_argument("--vside", type=int, default=1024, help="vardiff2d: mesh side")
+    ap.add_argument("--sn", type=int, default=400, help="schrodinger1d: mesh points (the paper's test: 400)")
     ap.add_argument("--scheme", default="euler", choices=["euler", "rb3"],
                     help="vardiff2d: exponential Euler-Rosenbrock (phi_1) or the third-order exprb32 (phi_1 + phi_3)")
     ap.add_argument("--lanes", type=int, default=16, help="batch512: concurrent lanes in the graph")
@@ -568,6 +570,11 @@ def run_small(a):
     stream = torch.cuda.current_stream(dev)
     if a.workload == "heat1d":
         wl, prec, name = W.heat1d(), "fp64", "heat1d_N1024_dirichlet_tile64_H16_fp64"
+    elif a.workload == "schrodinger1d":
+        # the Sec. 4.1 equation at the paper's size (400 points, 5 subdomains, buffer 20) or on a
+        # finer mesh over the same interval (same mu: smaller dt), tiles of 80 + 20
+        wl = W.schrodinger1d(n=a.sn)
+        prec, name = a.prec, f"schrodinger1d_{a.sn}_periodic_kappa10_mu2_tile80_H20"
     else:
         wl, prec, name = W.vardiff2d(side=a.vside), a.prec, f"vardiff2d_{a.vside}_dirichlet_tile16_H6_reaction"
         if a.scheme == "rb3":
@@ -610,7 +617,9 @@ def run_small(a):
     _, hbm_peak, peak_src = peaks()
     line = {"metric": METRIC, "value": npts * a.inner * a.steps / (dev_ms * 1e-3), "unit": METRIC, "n_gpus": 1,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if path.startswith("fp64") else "f32-gemv/ff-acc",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("c128 (real-embedded f64)" if ctx.complex else "f64") if path.startswith("fp64") else
+                     ("c64 (real-embedded f32)/ff-acc" if ctx.complex else "f32-gemv/ff-acc"),
             "data": "synthetic",
             "config": {"workload": name, "nodes": npts, "lem_steps_per_step": a.inner, "apply_path": path,
                        "scheme": a.scheme if a.workload == "vardiff2d" else "euler",
@@ -618,7 +627,8 @@ def run_small(a):
                        "build_s": round(build_s, 2), "l2": "256 MiB write between timed steps"},
             "gpu_launches": a.steps * a.inner * ((2 if "gemv" in path else 4) + (3 if a.scheme == "rb3" else 0)),
             "e2e": {"value": npts * a.inner / (statistics.median(e2e) * 1e-3), "unit": METRIC,
-                    "h2d_bytes_per_step": 8 * npts, "d2h_bytes_per_step": 8 * npts},
+                    "h2d_bytes_per_step": (16 if ctx.complex else 8) * npts,
+                    "d2h_bytes_per_step": (16 if ctx.complex else 8) * npts},
             "clocks": clk.summary()}
     if k_n and "gemv" in path:
         pbytes = (4 if path == "f32_gemv" else 8) * info["nclasses"] * info["n_int"] * info["n_loc"]
@@ -628,7 +638,8 @@ def run_small(a):
         line["roofline"] = {"kernel": f"gemv_tiles_kernel ({path})", "bound": "hbm", "achieved": ach,
                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
                             "avg_launch_us": k_ms / k_n * 1e3, "launches": k_n,
-                            "algorithmic_bytes": "propagators streamed once per step (n_int x n_loc per tile)",
+                            "algorithmic_bytes": "propagators streamed once per step (n_int x n_loc per tile; complex: the real "
+                                 "embedding, 2 n_int x 2 n_loc)",
                             "peak_source": f"{peak_src} HBM copy"}
     elif k_n:
         line["roofline"] = {"kernel": "dgemm_kernel (FP64 apply)", "bound": "alu", "avg_launch_us": k_ms / k_n * 1e3,
@@ -638,7 +649,7 @@ def run_small(a):
 
 def main():
     a = parse()
-    if a.workload in ("heat1d", "vardiff2d") and a.impl == "ours":
+    if a.workload in ("heat1d", "vardiff2d", "schrodinger1d") and a.impl == "ours":
         run_small(a)
         return
     if a.workload == "serve" and a.impl == "ours":

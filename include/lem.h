@@ -105,6 +105,13 @@ typedef struct {
   int refresh;            /* reaction only: rebuild the Jacobian propagators every
                              `refresh` steps (0: build once at the first step) */
   int scheme;             /* lem_scheme (0: the exponential Euler step of Eq. lem) */
+  int complex_values;     /* 1: complex coefficients and states (e.g. the Schroedinger test of
+                             Sec. 4.1). coef[k] then holds the real parts and coef_im[k] the
+                             imaginary parts (NULL: zero); states are interleaved (re, im)
+                             FP64 pairs, 2 * n[0] * n[1] doubles. Linear problems only, scheme
+                             0; the apply runs on the batched GEMV with each class's propagator
+                             stored as its real embedding [[Re P, -Im P], [Im P, Re P]]. */
+  const double* coef_im[5];
 } lem_problem_desc;
 
 typedef struct lem_ctx lem_ctx;

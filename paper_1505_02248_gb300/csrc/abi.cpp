@@ -220,18 +220,27 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   c->device = device;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   DeviceGuard g(device);
-  // dt-scaled coefficients
+  // dt-scaled coefficients (complex: the five real parts, then the five imaginary parts)
   const int64_t per = desc->coef_stride ? c->npts : 1;
-  std::vector<double> hc(5 * per, 0.0);
+  c->cplx = desc->complex_values ? 1 : 0;
+  std::vector<double> hc((c->cplx ? 10 : 5) * per, 0.0);
   const int ncoef = desc->ndim == 1 ? 3 : 5;
   for (int k = 0; k < ncoef; ++k)
-    for (int64_t i = 0; i < per; ++i) hc[k * per + i] = desc->dt * desc->coef[k][i];
+    for (int64_t i = 0; i < per; ++i) {
+      hc[k * per + i] = desc->dt * desc->coef[k][i];
+      if (c->cplx && desc->coef_im[k]) hc[(5 + k) * per + i] = desc->dt * desc->coef_im[k][i];
+    }
+  if (c->cplx) {  // propagators of the real embedding: twice the rows and columns
+    c->n_loc *= 2;
+    c->n_int *= 2;
+  }
+  const int64_t vals = (c->cplx ? 2 : 1) * c->npts;  // doubles per state
   const size_t nt = c->tiles.size(), nc = c->classes.size();
   s = dev_alloc(c, reinterpret_cast<void**>(&c->d_coef), sizeof(double) * hc.size());
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_tiles), sizeof(TileDesc) * nt);
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_class_order), sizeof(int32_t) * nt);
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_P), sizeof(double) * nc * c->n_int * c->n_loc);
-  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_r), sizeof(double) * c->npts);
+  if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_r), sizeof(double) * vals);
   if (s == LEM_OK && desc->scheme == LEM_SCHEME_RB3) {
     s = dev_alloc(c, reinterpret_cast<void**>(&c->d_P3), sizeof(double) * nc * c->n_int * c->n_loc);
     if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_um), sizeof(double) * c->npts);
@@ -250,7 +259,7 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   const bool many_classes = c->classes.size() * 8 > c->tiles.size();
   c->build_tc = builder_uses_tc(desc->prec);
   const bool split_tier = desc->prec == LEM_PREC_SPLIT || desc->prec == LEM_PREC_SPLIT_FAST;
-  if (desc->scheme == LEM_SCHEME_RB3) {  // two propagator sets per class: the batched GEMV
+  if (desc->scheme == LEM_SCHEME_RB3 || c->cplx) {  // two propagator sets / complex: the batched GEMV
     c->apply_path = desc->prec == LEM_PREC_SPLIT_FAST ? LEM_APPLY_F32_GEMV : LEM_APPLY_FP64_GEMV;
   } else if (split_tier && split_eligible(c)) {
     c->apply_path = LEM_APPLY_TC_SPLIT;
@@ -299,9 +308,8 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   if (!h_state) return fail(LEM_EINVAL, "state is NULL");
   DeviceGuard g(ctx->device);
-  if (!ctx->d_state_tmp)
-    LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_state_tmp), sizeof(double) * ctx->npts));
-  const size_t bytes = sizeof(double) * ctx->npts;
+  const size_t bytes = sizeof(double) * ctx->npts * (ctx->cplx ? 2 : 1);
+  if (!ctx->d_state_tmp) LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_state_tmp), bytes));
   LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_state_tmp, h_state, bytes, cudaMemcpyHostToDevice, ctx->stream));
   LEM_TRY(lem_step(ctx, ctx->d_state_tmp, nsteps));
   LEM_CUDA_TRY(cudaMemcpyAsync(h_state, ctx->d_state_tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));

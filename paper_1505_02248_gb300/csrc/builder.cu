@@ -80,6 +80,49 @@ __global__ void assemble_local_kernel(double* X, int n, const BatchClass* bc, in
   }
 }
 
+// Complex problems: the real embedding [[Re X, -Im X], [Im X, Re X]] of X = dt A_M (n = twice
+// the window nodes): row k carries the real part of node k's equation, row n/2 + k the
+// imaginary part. Coefficients: real parts at coef[w], imaginary parts at coef[5 + w].
+__global__ void assemble_local_complex_kernel(double* X, int n, const BatchClass* bc, int nb, const double* coef,
+                                              int64_t cstride, int64_t ny, int64_t nx, int ndim) {
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = n / 2;
+  if (b >= nb || k >= h) return;
+  double* rr = X + (int64_t(b) * n + k) * n;
+  double* ri = X + (int64_t(b) * n + h + k) * n;
+  for (int j = 0; j < n; ++j) rr[j] = ri[j] = 0.0;
+  const BatchClass c = bc[b];
+  const int wy = c.rep.wext[0], wx = c.rep.wext[1];
+  if (k >= wy * wx) return;  // padding node
+  const int a = k / wx, bb = k % wx;
+  int64_t gy = (int64_t(c.rep.org[0]) + a) % ny;
+  if (gy < 0) gy += ny;
+  int64_t gx = (int64_t(c.rep.org[1]) + bb) % nx;
+  if (gx < 0) gx += nx;
+  const int64_t p = gy * nx + gx, npts = ny * nx;
+  auto add = [&](int col, int w) {
+    const int64_t o = cstride ? p : 0;
+    const double cr = coef[int64_t(w) * (cstride ? npts : 1) + o];
+    const double ci = coef[int64_t(5 + w) * (cstride ? npts : 1) + o];
+    rr[col] += cr;
+    rr[h + col] -= ci;
+    ri[col] += ci;
+    ri[h + col] += cr;
+  };
+  add(k, 0);
+  if (bb >= 1) add(k - 1, 1);
+  else if (c.whole[1]) add(k + wx - 1, 1);
+  if (bb + 1 < wx) add(k + 1, 2);
+  else if (c.whole[1]) add(k + 1 - wx, 2);
+  if (ndim == 2) {
+    if (a >= 1) add(k - wx, 3);
+    else if (c.whole[0]) add(k + (wy - 1) * wx, 3);
+    if (a + 1 < wy) add(k + wx, 4);
+    else if (c.whole[0]) add(k - (wy - 1) * wx, 4);
+  }
+}
+
 // column 1-norms -> per-matrix max (non-negative doubles order like their bit patterns)
 __global__ void norm1_kernel(const double* X, int n, unsigned long long* out) {
   const int b = blockIdx.y;
@@ -283,6 +326,27 @@ __global__ void extract_rows_kernel(double* P, int64_t n_int, int64_t n_loc, con
   P[int64_t(b) * n_int * n_loc + e] = v;
 }
 
+// Complex problems: owner rows of the embedded result R (n x n, n = 2 x window nodes) into P
+// (n_int x n_loc, both embedded sizes): rows [0, n_int/2) the real parts, [n_int/2, n_int) the
+// imaginary parts of the owner nodes; columns as in R (real parts, then imaginary parts).
+__global__ void extract_rows_complex_kernel(double* P, int64_t n_int, int64_t n_loc, const double* R, int n,
+                                            const BatchClass* bc) {
+  const int b = blockIdx.y;
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n_int * n_loc) return;
+  const int i = int(e / n_loc), k = int(e % n_loc);
+  const int hi = int(n_int / 2), hn = n / 2;
+  const int comp = i / hi, io = i % hi;
+  const BatchClass c = bc[b];
+  const int ie = c.rep.iext[0] * c.rep.iext[1];
+  double v = 0.0;
+  if (io < ie && k < n) {
+    const int row = (c.rep.iofs[0] + io / c.rep.iext[1]) * c.rep.wext[1] + c.rep.iofs[1] + io % c.rep.iext[1];
+    v = R[int64_t(b) * n * n + int64_t(comp * hn + row) * n + k];
+  }
+  P[int64_t(b) * n_int * n_loc + e] = v;
+}
+
 __global__ void copy_cols_kernel(double* dst, int64_t ldd, int dcol0, const double* src, int64_t lds,
                                  int scol0, int n, int ncols) {
   const int b = blockIdx.y;
@@ -388,9 +452,13 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
 
   // X = dt A_M (+ reaction Jacobian)
   const double* u = ctx->desc.reaction ? d_state : nullptr;
-  assemble_local_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(
-      Xs, n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u,
-      ctx->desc.dt);
+  if (ctx->cplx)  // the real embedding of the complex window matrix
+    assemble_local_complex_kernel<<<dim3((n / 2 + 127) / 128, nb), 128, 0, st>>>(
+        Xs, n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim);
+  else
+    assemble_local_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(
+        Xs, n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u,
+        ctx->desc.dt);
   LEM_CUDA_TRY(cudaGetLastError());
   // exact 1-norms -> s per class (host decides, same rule as theta_13 scaling)
   LEM_CUDA_TRY(cudaMemsetAsync(normbuf.p, 0, sizeof(double) * nb, st));
@@ -561,8 +629,12 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   }
   const double* R = phi ? RB : RT;
   double* Pout = ctx->d_P + size_t(c0) * ctx->n_int * ctx->n_loc;
-  extract_rows_kernel<<<grid1(ctx->n_int * ctx->n_loc, nb), 256, 0, st>>>(
-      Pout, ctx->n_int, ctx->n_loc, R, n, n, 0, d_bc);
+  if (ctx->cplx)
+    extract_rows_complex_kernel<<<grid1(ctx->n_int * ctx->n_loc, nb), 256, 0, st>>>(Pout, ctx->n_int, ctx->n_loc, R,
+                                                                                    n, d_bc);
+  else
+    extract_rows_kernel<<<grid1(ctx->n_int * ctx->n_loc, nb), 256, 0, st>>>(
+        Pout, ctx->n_int, ctx->n_loc, R, n, n, 0, d_bc);
   LEM_CUDA_TRY(cudaGetLastError());
   int status = 0;
   LEM_CUDA_TRY(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -89,6 +89,8 @@ struct lem_ctx {
   int64_t n_loc = 0, n_int = 0;        // padded window / tile sizes
   bool built = false;
   bool build_tc = false;               // propagator products on the tensor cores (split tiers)
+  int cplx = 0;                        // complex problem: interleaved states, n_loc / n_int are the
+                                       // real-embedding sizes (2 x window / tile nodes)
   int build_gen = 0;                   // incremented by every propagator build
   int steps_since_build = 0;
   // device buffers (owned)

@@ -33,6 +33,9 @@ lem_status validate(const lem_problem_desc* d) {
   if (d->scheme != LEM_SCHEME_EULER && d->scheme != LEM_SCHEME_RB3) return fail(LEM_EINVAL, "bad scheme");
   if (d->scheme == LEM_SCHEME_RB3 && d->mode != LEM_MODE_PHI)
     return fail(LEM_EINVAL, "the third-order Rosenbrock scheme needs LEM_MODE_PHI");
+  if (d->complex_values != 0 && d->complex_values != 1) return fail(LEM_EINVAL, "complex_values must be 0 or 1");
+  if (d->complex_values && (d->reaction || d->scheme != LEM_SCHEME_EULER))
+    return fail(LEM_EINVAL, "complex problems are linear, with the exponential Euler scheme");
   return LEM_OK;
 }
 

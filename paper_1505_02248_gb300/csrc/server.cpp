@@ -492,6 +492,7 @@ lem_status lem_submit(lem_server* s, const lem_problem_desc* desc, double tol, d
   if (nsteps < 0) return lem::fail(LEM_EINVAL, "nsteps < 0");
   if (!(tol > 0.0)) return lem::fail(LEM_EINVAL, "tol must be > 0");
   LEM_TRY(lem::validate(desc));
+  if (desc->complex_values) return lem::fail(LEM_EINVAL, "the server takes real problems");
   if (s->stop.load()) return lem::fail(LEM_EBUSY, "server is stopping");
   auto r = std::make_shared<Request>();
   r->desc = *desc;

@@ -39,6 +39,39 @@ __global__ void residual_fp64_kernel(double* __restrict__ r, const double* __res
   }
 }
 
+// Complex problems: r = X u with interleaved (re, im) states; coefficient w's real part at
+// coef[w], its imaginary part at coef[5 + w] (per node when cstride).
+__global__ void residual_complex_kernel(double* __restrict__ r, const double* __restrict__ u,
+                                        const double* __restrict__ coef, int64_t cstride, int64_t ny, int64_t nx,
+                                        int ndim, int pery, int perx) {
+  const int64_t npts = ny * nx;
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npts;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t y = p / nx, x = p % nx;
+    double ar = 0.0, ai = 0.0;
+    auto mac = [&](int w, int64_t q) {
+      const double a = cstride ? coef[int64_t(w) * npts + p] : coef[w];
+      const double b = cstride ? coef[int64_t(5 + w) * npts + p] : coef[5 + w];
+      const double xr = u[2 * q], xi = u[2 * q + 1];
+      ar = fma(a, xr, fma(-b, xi, ar));
+      ai = fma(a, xi, fma(b, xr, ai));
+    };
+    mac(0, p);
+    if (x > 0) mac(1, p - 1);
+    else if (perx) mac(1, p + nx - 1);
+    if (x + 1 < nx) mac(2, p + 1);
+    else if (perx) mac(2, p + 1 - nx);
+    if (ndim == 2) {
+      if (y > 0) mac(3, p - nx);
+      else if (pery) mac(3, p + (ny - 1) * nx);
+      if (y + 1 < ny) mac(4, p + nx);
+      else if (pery) mac(4, p - (ny - 1) * nx);
+    }
+    r[2 * p] = ar;
+    r[2 * p + 1] = ai;
+  }
+}
+
 // U[t][k] = src(window node k of tile t), zero beyond the window (padding)
 __global__ void gather_fp64_kernel(double* __restrict__ U, const double* __restrict__ src,
                                    const TileDesc* __restrict__ tiles, int64_t n_loc, int64_t ny,
@@ -80,6 +113,12 @@ __global__ void scatter_fp64_kernel(double* __restrict__ u, const double* __rest
 cudaError_t launch_residual_fp64(const lem_ctx* ctx, double* r, const double* u) {
   const lem_problem_desc& d = ctx->desc;
   int blocks = int(std::min<int64_t>((ctx->npts + 255) / 256, 152 * 16));
+  if (ctx->cplx) {
+    residual_complex_kernel<<<blocks, 256, 0, ctx->stream>>>(r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx,
+                                                             d.ndim, ctx->bcy == LEM_BC_PERIODIC,
+                                                             ctx->bcx == LEM_BC_PERIODIC);
+    return cudaGetLastError();
+  }
   residual_fp64_kernel<<<blocks, 256, 0, ctx->stream>>>(
       r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx, d.ndim, ctx->bcy == LEM_BC_PERIODIC,
       ctx->bcx == LEM_BC_PERIODIC, d.reaction, d.dt);

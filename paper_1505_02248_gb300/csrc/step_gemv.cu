@@ -62,7 +62,10 @@ __device__ __forceinline__ double group_reduce(AccF& a) {
 // length a multiple of the vector width, rows 16-byte aligned) each lane streams its row in
 // 16-byte loads, four in flight; else scalar loads. Several rows in flight per warp keep the
 // load pipe busy through each row's reduction and owner update.
-template <typename PT>
+// CPLX: complex states (interleaved re, im) with real-embedded propagators: the window is
+// staged as [re parts | im parts] (n_loc / 2 nodes each, zero padded), row i < ie of the tile's
+// owner rows gives the real part and row n_int / 2 + i the imaginary part of owner node i.
+template <typename PT, bool CPLX>
 __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
                                                          const TileDesc* __restrict__ tiles,
                                                          const double* __restrict__ src, double* __restrict__ u,
@@ -74,17 +77,25 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   // waves of short blocks instead of one wave of long ones (a shorter tail)
   const int t = blockIdx.x / rsplit, part = blockIdx.x % rsplit;
   const TileDesc td = tiles[t];
-  const int wl = td.wext[0] * td.wext[1];
+  const int wn = td.wext[0] * td.wext[1];  // window nodes
+  const int hn = int(n_loc / 2);            // CPLX: padded window nodes
+  const int wl = CPLX ? int(n_loc) : wn;    // staged window values
   for (int k = threadIdx.x; k < wl; k += blockDim.x) {
-    const int a = k / td.wext[1], b = k % td.wext[1];
+    const int node = CPLX ? k % hn : k, comp = CPLX ? k / hn : 0;
+    if (node >= wn) {
+      w[k] = PT(0);
+      continue;
+    }
+    const int a = node / td.wext[1], b = node % td.wext[1];
     int64_t gy = int64_t(td.org[0]) + a, gx = int64_t(td.org[1]) + b;
     gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
     gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-    w[k] = PT(src[gy * nx + gx]);
+    w[k] = PT(CPLX ? src[2 * (gy * nx + gx) + comp] : src[gy * nx + gx]);
   }
   __syncthreads();
   const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
-  const int ie_all = td.iext[0] * td.iext[1];
+  const int ien = td.iext[0] * td.iext[1];  // owner nodes
+  const int ie_all = CPLX ? 2 * ien : ien;  // output rows of this tile
   const int rows_per = (ie_all + rsplit - 1) / rsplit;
   const int ib = part * rows_per, ie = min(ie_all, ib + rows_per);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -97,7 +108,8 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   for (int i0 = ib + warp * 4; i0 < ie; i0 += nw * 4) {
     const int i = i0 + grp;
     const bool live = i < ie;
-    const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
+    const int prow = CPLX && i >= ien ? int(n_int / 2) + (i - ien) : i;  // row of P
+    const PT* row = Pt + int64_t(live ? prow : 0) * n_loc;
     Acc acc;
     if (vec) {
       const int nv = wl / V;
@@ -121,8 +133,10 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
     }
     const double y = group_reduce(acc);
     if (live && gl == 0) {
-      const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
-      u[p] = accumulate ? u[p] + y : y;
+      const int o = CPLX ? i % ien : i, comp = CPLX ? i / ien : 0;
+      const int64_t p = int64_t(td.t0[0] + o / td.iext[1]) * nx + td.t0[1] + o % td.iext[1];
+      const int64_t q = CPLX ? 2 * p + comp : p;
+      u[q] = accumulate ? u[q] + y : y;
     }
   }
 }
@@ -173,7 +187,8 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
     LEM_CUDA_TRY(launch_residual_fp64(ctx, ctx->d_r, d_u));
     src = ctx->d_r;
   } else {
-    LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_r, d_u, sizeof(double) * ctx->npts, cudaMemcpyDeviceToDevice, st));
+    LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_r, d_u, sizeof(double) * ctx->npts * (ctx->cplx ? 2 : 1),
+                                 cudaMemcpyDeviceToDevice, st));
     src = ctx->d_r;
   }
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
@@ -187,12 +202,21 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
   auto gemv = [&](const double* P64, const float* P32, const double* x) {
-    if (f32)
-      gemv_tiles_kernel<float><<<nt * rsplit, 256, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x, d_u,
-                                                               ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
-    else
-      gemv_tiles_kernel<double><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x, d_u,
-                                                                ctx->ny, ctx->nx, phi ? 1 : 0, rsplit);
+    const int acc = phi ? 1 : 0;
+    if (ctx->cplx) {
+      if (f32)
+        gemv_tiles_kernel<float, true><<<nt * rsplit, 256, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+                                                                       d_u, ctx->ny, ctx->nx, acc, rsplit);
+      else
+        gemv_tiles_kernel<double, true><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+                                                                        d_u, ctx->ny, ctx->nx, acc, rsplit);
+    } else if (f32) {
+      gemv_tiles_kernel<float, false><<<nt * rsplit, 256, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+                                                                      d_u, ctx->ny, ctx->nx, acc, rsplit);
+    } else {
+      gemv_tiles_kernel<double, false><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+                                                                       d_u, ctx->ny, ctx->nx, acc, rsplit);
+    }
   };
   gemv(ctx->d_P, ctx->d_P32, src);
   if (rb3) {  // second stage: u^{n+1} = U + 2 phi_3(dt J_m) dt (G(U) - G(u^n)), window by window
@@ -207,8 +231,14 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
 lem_status gemv_set_smem(lem_ctx* ctx) {
   const int bytes = int(sizeof(double) * ctx->n_loc);
   if (bytes > 48 * 1024) {
-    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      bytes));
+    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      bytes));
+    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      bytes));
+    LEM_CUDA_TRY(cudaFuncSetAttribute(gemv_tiles_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      bytes));
   }
   return LEM_OK;
 }

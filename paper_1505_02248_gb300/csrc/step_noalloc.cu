@@ -54,6 +54,8 @@ extern "C" lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int n
   if (!d_state) return lem::fail(LEM_EINVAL, "state is NULL");
   if (nsteps < 0) return lem::fail(LEM_EINVAL, "nsteps < 0");
   if (ctx->desc.prec != LEM_PREC_FP64) return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc needs an LEM_PREC_FP64 context");
+  if (ctx->cplx || ctx->desc.scheme != LEM_SCHEME_EULER)
+    return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc covers real problems with the exponential Euler scheme");
   if (!ctx->built) return lem::fail(LEM_ENOTREADY, "build the propagators (lem_build_propagators) before the allocation-free step");
   if (ctx->desc.reaction && ctx->desc.refresh > 0)
     return lem::fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators, which allocates; use refresh = 0");

@@ -43,6 +43,8 @@ class ProblemDesc(C.Structure):
         ("prec", C.c_int),
         ("refresh", C.c_int),
         ("scheme", C.c_int),
+        ("complex_values", C.c_int),
+        ("coef_im", C.POINTER(C.c_double) * 5),
     ]
 
 
@@ -147,15 +149,22 @@ def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec=
         d.overlap[a] = int(overlap[a]) if a < nd else 0
     keep = []
     names = ["C", "W", "E", "S", "N"][: 3 if nd == 1 else 5]
-    arrays = [np.ascontiguousarray(np.asarray(coef[k], dtype=np.float64).ravel()) for k in names]
+    raw = [np.asarray(coef[k]).ravel() for k in names]
+    cplx = any(np.iscomplexobj(a) for a in raw)
+    arrays = [np.ascontiguousarray(a.real, dtype=np.float64) for a in raw]
+    imags = [np.ascontiguousarray(a.imag, dtype=np.float64) if np.iscomplexobj(a) else np.zeros(a.size)
+             for a in raw]
     stride = 0 if all(a.size == 1 for a in arrays) else 1
     npts = int(np.prod(shape))
-    for k, a in enumerate(arrays):
+    for k, (a, b) in enumerate(zip(arrays, imags)):
         if stride == 1 and a.size == 1:
-            a = np.full(npts, float(a[0]))
-        keep.append(a)
+            a, b = np.full(npts, float(a[0])), np.full(npts, float(b[0]))
+        keep += [a, b]
         d.coef[k] = a.ctypes.data_as(C.POINTER(C.c_double))
+        if cplx:
+            d.coef_im[k] = b.ctypes.data_as(C.POINTER(C.c_double))
     d.coef_stride = stride
+    d.complex_values = 1 if cplx else 0
     d.reaction = 1 if reaction else 0
     d.dt = float(dt)
     d.mode = MODE[mode]
@@ -189,6 +198,7 @@ class Lem:
         h = C.c_void_p()
         st = C.c_void_p(stream) if stream is not None else None
         check(lib.lem_create(C.byref(d), int(device), st, C.byref(h)), "lem_create")
+        self.complex = bool(d.complex_values)
         del keep
         self._h = h
 
@@ -222,8 +232,10 @@ class Lem:
         check(self._lib.lem_build_propagators(self._h, ptr), "lem_build_propagators")
 
     def step(self, state, nsteps: int):
-        """Advance a CUDA float64 tensor (contiguous, npts values) in place."""
-        assert state.is_cuda and state.dtype.itemsize == 8 and state.is_contiguous()
+        """Advance a CUDA tensor in place: float64 (npts values), or complex128 (npts values,
+        interleaved re/im) for a complex problem."""
+        assert state.is_cuda and state.is_contiguous()
+        assert state.dtype.itemsize == (16 if self.complex else 8) and state.is_complex() == self.complex
         assert state.numel() == self.npts
         check(self._lib.lem_step(self._h, C.c_void_p(state.data_ptr()), int(nsteps)), "lem_step")
 
@@ -235,8 +247,10 @@ class Lem:
               "lem_step_fp64_noalloc")
 
     def step_host(self, state: np.ndarray, nsteps: int):
-        """Advance a host float64 array in place (copies in and out inside the call)."""
-        assert state.dtype == np.float64 and state.flags.c_contiguous and state.size == self.npts
+        """Advance a host float64 (complex128 for a complex problem) array in place (copies in
+        and out inside the call)."""
+        assert state.dtype == (np.complex128 if self.complex else np.float64)
+        assert state.flags.c_contiguous and state.size == self.npts
         check(self._lib.lem_step_host(self._h, state.ctypes.data_as(C.c_void_p), int(nsteps)),
               "lem_step_host")
 
