@@ -632,14 +632,16 @@ def run_small(a):
             "clocks": clk.summary()}
     if k_n and "gemv" in path:
         pbytes = (4 if path == "f32_gemv" else 8) * info["nclasses"] * info["n_int"] * info["n_loc"]
+        if ctx.complex:
+            pbytes //= 2  # the Re and Im rows of each owner, left halves of the stored embedding
         if a.scheme == "rb3":
             pbytes *= 2  # phi_1 and phi_3 propagators, one GEMV each per step (timed together)
         ach = pbytes / (k_ms / k_n * 1e-3) / 1e9
         line["roofline"] = {"kernel": f"gemv_tiles_kernel ({path})", "bound": "hbm", "achieved": ach,
                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
                             "avg_launch_us": k_ms / k_n * 1e3, "launches": k_n,
-                            "algorithmic_bytes": "propagators streamed once per step (n_int x n_loc per tile; complex: the real "
-                                 "embedding, 2 n_int x 2 n_loc)",
+                            "algorithmic_bytes": "propagators streamed once per step (n_int x n_loc per tile; complex: its Re and "
+                                 "Im planes, n_int x n_loc / 2 of the stored real embedding)",
                             "peak_source": f"{peak_src} HBM copy"}
     elif k_n:
         line["roofline"] = {"kernel": "dgemm_kernel (FP64 apply)", "bound": "alu", "avg_launch_us": k_ms / k_n * 1e3,

@@ -62,9 +62,9 @@ __device__ __forceinline__ double group_reduce(AccF& a) {
 // length a multiple of the vector width, rows 16-byte aligned) each lane streams its row in
 // 16-byte loads, four in flight; else scalar loads. Several rows in flight per warp keep the
 // load pipe busy through each row's reduction and owner update.
-// CPLX: complex states (interleaved re, im) with real-embedded propagators: the window is
-// staged as [re parts | im parts] (n_loc / 2 nodes each, zero padded), row i < ie of the tile's
-// owner rows gives the real part and row n_int / 2 + i the imaginary part of owner node i.
+// CPLX: complex states (interleaved re, im) with real-embedded propagators
+// [[Re P, -Im P], [Im P, Re P]]: the window is staged as [re parts | im parts] (n_loc / 2 nodes
+// each, zero padded); each owner's Re and Im rows are read once, left halves only.
 template <typename PT, bool CPLX>
 __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
                                                          const TileDesc* __restrict__ tiles,
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   __syncthreads();
   const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
   const int ien = td.iext[0] * td.iext[1];  // owner nodes
-  const int ie_all = CPLX ? 2 * ien : ien;  // output rows of this tile
+  const int ie_all = ien;                   // owner nodes of this tile (CPLX: one group does both parts)
   const int rows_per = (ie_all + rsplit - 1) / rsplit;
   const int ib = part * rows_per, ie = min(ie_all, ib + rows_per);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -104,12 +104,70 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
   constexpr int U = 4;  // 16-byte loads in flight per lane
   const bool vec = (n_loc % V) == 0 && (wl % V) == 0;
   using Acc = typename std::conditional<sizeof(PT) == 8, AccD, AccF>::type;
+  if constexpr (CPLX) {
+    // complex: a row group per owner node o, reading its Re row (row o) and Im row (row
+    // n_int / 2 + o) of the stored embedding, left halves only (the right halves repeat them):
+    //   y_re = Re w_re - Im w_im,   y_im = Im w_re + Re w_im
+    const int hl = hn;  // window columns per part
+    const bool cvec = (n_loc % V) == 0 && (hl % V) == 0;
+    for (int o0 = ib + warp * 4; o0 < ie; o0 += nw * 4) {
+      const int o = o0 + grp;
+      const bool live = o < ie;
+      const PT* rre = Pt + int64_t(live ? o : 0) * n_loc;
+      const PT* rim = Pt + int64_t(live ? int(n_int / 2) + o : 0) * n_loc;
+      Acc are, aim;
+      if (cvec) {
+        const int nv = hl / V;
+        const int4* a4 = reinterpret_cast<const int4*>(rre);
+        const int4* b4 = reinterpret_cast<const int4*>(rim);
+        for (int j = gl; j < nv; j += 8 * 2) {
+          int4 qa[2], qb[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const bool ok = live && j + 8 * k < nv;
+            qa[k] = ok ? __ldcs(a4 + j + 8 * k) : make_int4(0, 0, 0, 0);
+            qb[k] = ok ? __ldcs(b4 + j + 8 * k) : make_int4(0, 0, 0, 0);
+          }
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (j + 8 * k >= nv) break;
+            const PT* pa = reinterpret_cast<const PT*>(&qa[k]);
+            const PT* pb = reinterpret_cast<const PT*>(&qb[k]);
+            const int4 wr4 = *reinterpret_cast<const int4*>(w + (j + 8 * k) * V);
+            const int4 wi4 = *reinterpret_cast<const int4*>(w + hl + (j + 8 * k) * V);
+            const PT* wr = reinterpret_cast<const PT*>(&wr4);
+            const PT* wi = reinterpret_cast<const PT*>(&wi4);
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+              are.add(pa[h], wr[h]);
+              are.add(-pb[h], wi[h]);
+              aim.add(pb[h], wr[h]);
+              aim.add(pa[h], wi[h]);
+            }
+          }
+        }
+      } else if (live) {
+        for (int k = gl; k < hl; k += 8) {
+          are.add(rre[k], w[k]);
+          are.add(-rim[k], w[hl + k]);
+          aim.add(rim[k], w[k]);
+          aim.add(rre[k], w[hl + k]);
+        }
+      }
+      const double yr = group_reduce(are), yi = group_reduce(aim);
+      if (live && gl == 0) {
+        const int64_t p = int64_t(td.t0[0] + o / td.iext[1]) * nx + td.t0[1] + o % td.iext[1];
+        u[2 * p] = accumulate ? u[2 * p] + yr : yr;
+        u[2 * p + 1] = accumulate ? u[2 * p + 1] + yi : yi;
+      }
+    }
+    return;
+  }
   // every lane runs the same number of row iterations (the shuffles need the whole warp)
   for (int i0 = ib + warp * 4; i0 < ie; i0 += nw * 4) {
     const int i = i0 + grp;
     const bool live = i < ie;
-    const int prow = CPLX && i >= ien ? int(n_int / 2) + (i - ien) : i;  // row of P
-    const PT* row = Pt + int64_t(live ? prow : 0) * n_loc;
+    const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
     Acc acc;
     if (vec) {
       const int nv = wl / V;
@@ -133,13 +191,12 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
     }
     const double y = group_reduce(acc);
     if (live && gl == 0) {
-      const int o = CPLX ? i % ien : i, comp = CPLX ? i / ien : 0;
-      const int64_t p = int64_t(td.t0[0] + o / td.iext[1]) * nx + td.t0[1] + o % td.iext[1];
-      const int64_t q = CPLX ? 2 * p + comp : p;
-      u[q] = accumulate ? u[q] + y : y;
+      const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
+      u[p] = accumulate ? u[p] + y : y;
     }
   }
 }
+
 
 // The defect of the third-order Rosenbrock step, times two: 2 dt (G(U) - G(u)) with
 // G(v) = F(v) - J(u_m) v. The linear parts cancel, so it is pointwise:
