@@ -294,6 +294,14 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
   NvtxRange range("lem_step");
   if (!ctx->built) LEM_TRY(build_propagators(ctx, d_state));
   if (ctx->split) return split_step(ctx, d_state, nsteps);
+  if (ctx->apply_path == LEM_APPLY_FP64_GEMV || ctx->apply_path == LEM_APPLY_F32_GEMV) {
+    bool done = false;  // small linear problems: every step in one persistent launch
+    LEM_TRY(step_gemv_multi(ctx, d_state, nsteps, ctx->apply_path == LEM_APPLY_F32_GEMV, &done));
+    if (done) {
+      ctx->steps_since_build += nsteps;
+      return LEM_OK;
+    }
+  }
   for (int k = 0; k < nsteps; ++k) {
     if (ctx->desc.reaction && ctx->desc.refresh > 0 && ctx->steps_since_build >= ctx->desc.refresh)
       LEM_TRY(build_propagators(ctx, d_state));

@@ -131,6 +131,8 @@ lem_status build_propagators(lem_ctx* ctx, const double* d_state);
 lem_status step_fp64(lem_ctx* ctx, double* d_u);
 // step_gemv.cu
 lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32);
+// nsteps of a small linear problem in one cooperative launch; *done false: not eligible
+lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool* done);
 lem_status gemv_set_smem(lem_ctx* ctx);
 // step_split.cu
 lem_status split_prepare(lem_ctx* ctx);

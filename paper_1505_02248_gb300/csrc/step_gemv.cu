@@ -9,7 +9,10 @@
 // Jacobi update: all tiles must read u^n, so in EXP mode the source is a copy of u^n and in
 // PHI mode the residual array (computed from u^n before this launch).
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "lem_internal.h"
 
@@ -229,6 +232,136 @@ lem_status gemv_prepare_f32(lem_ctx* ctx) {
   }
   LEM_CUDA_TRY(cudaGetLastError());
   ctx->p32_gen = ctx->build_gen;
+  return LEM_OK;
+}
+
+// ---------------------------------------------------------------- persistent multi-step
+// Small problems (config 1: 16 tiles of a 1024-node mesh) are bound by launch latency, two
+// launches per step. This cooperative kernel runs all nsteps in one launch. Per step every
+// block takes its tiles: it forms the window's source straight from u^n (the residual dt A u^n
+// at each window node in PHI mode, u^n in EXP mode) in shared memory, applies the tile's
+// propagator (four rows per warp) and writes the owner values of u^{n+1} into the other state
+// buffer; one grid barrier ends the step. Linear real problems on the GEMV path only (no
+// Jacobian refresh, one scheme stage).
+template <typename PT>
+__global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
+                                                              const TileDesc* __restrict__ tiles, int ntiles,
+                                                              const double* __restrict__ coef, int64_t cstride,
+                                                              int64_t ny, int64_t nx, int ndim, int pery, int perx,
+                                                              int phi, double* __restrict__ src,
+                                                              double* __restrict__ u, int nsteps) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char wraw[];
+  PT* w = reinterpret_cast<PT*>(wraw);
+  const int64_t npts = ny * nx;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int grp = lane / 8, gl = lane % 8;
+  using Acc = typename std::conditional<sizeof(PT) == 8, AccD, AccF>::type;
+  // u^n and u^{n+1} alternate between u and src (every node has exactly one owner tile, so
+  // each step writes the whole of the other buffer); one grid barrier per step
+  double* cur = u;
+  double* nxt = src;
+  for (int step = 0; step < nsteps; ++step) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TileDesc td = tiles[t];
+      const int wl = td.wext[0] * td.wext[1];
+      // the window's source from u^n: the residual dt A u^n at each window node (PHI), or u^n
+      for (int k = threadIdx.x; k < wl; k += blockDim.x) {
+        const int a = k / td.wext[1], b = k % td.wext[1];
+        int64_t gy = int64_t(td.org[0]) + a, gx = int64_t(td.org[1]) + b;
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+        const int64_t p = gy * nx + gx;
+        double v = cur[p];
+        if (phi) {
+          auto cf = [&](int c) { return cstride ? coef[int64_t(c) * npts + p] : coef[c]; };
+          double acc = cf(0) * v;
+          if (gx > 0) acc = fma(cf(1), cur[p - 1], acc);
+          else if (perx) acc = fma(cf(1), cur[p + nx - 1], acc);
+          if (gx + 1 < nx) acc = fma(cf(2), cur[p + 1], acc);
+          else if (perx) acc = fma(cf(2), cur[p + 1 - nx], acc);
+          if (ndim == 2) {
+            if (gy > 0) acc = fma(cf(3), cur[p - nx], acc);
+            else if (pery) acc = fma(cf(3), cur[p + (ny - 1) * nx], acc);
+            if (gy + 1 < ny) acc = fma(cf(4), cur[p + nx], acc);
+            else if (pery) acc = fma(cf(4), cur[p - (ny - 1) * nx], acc);
+          }
+          v = acc;
+        }
+        w[k] = PT(v);
+      }
+      __syncthreads();
+      const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
+      const int ie = td.iext[0] * td.iext[1];
+      for (int i0 = warp * 4; i0 < ie; i0 += nw * 4) {
+        const int i = i0 + grp;
+        const bool live = i < ie;
+        const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
+        Acc acc;
+        if (live)
+          for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
+        const double y = group_reduce(acc);
+        if (live && gl == 0) {
+          const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
+          nxt[p] = phi ? cur[p] + y : y;
+        }
+      }
+      __syncthreads();  // the window buffer is reused by the block's next tile
+    }
+    grid.sync();  // u^{n+1} complete before any block reads it
+    double* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (cur != u)  // an odd number of steps ended in the scratch buffer
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npts; p += int64_t(gridDim.x) * blockDim.x)
+      u[p] = cur[p];
+}
+
+// Whether lem_step may run its steps in one persistent launch, and with how many blocks.
+static int persistent_blocks(lem_ctx* ctx, bool f32, int nsteps) {
+  const lem_problem_desc& d = ctx->desc;
+  if (nsteps < 2 || d.reaction || d.scheme != LEM_SCHEME_EULER || ctx->cplx) return 0;
+  if (ctx->npts > (int64_t(1) << 20) || ctx->tiles.size() > 4096) return 0;
+  if (std::getenv("LEM_NO_PERSISTENT")) return 0;  // switch for comparisons
+  int dev_coop = 0, nsm = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&dev_coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess || !dev_coop ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t smem = sizeof(double) * size_t(ctx->n_loc);
+  cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<float>, 256, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<double>, 256, smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  // one block per tile, within what the device holds at once
+  return int(std::min<int64_t>(int64_t(per_sm) * nsm, int64_t(ctx->tiles.size())));
+}
+
+lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool* done) {
+  *done = false;
+  const int blocks = persistent_blocks(ctx, f32, nsteps);
+  if (blocks < 1) return LEM_OK;
+  if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
+  const lem_problem_desc& d = ctx->desc;
+  const size_t smem = sizeof(double) * size_t(ctx->n_loc);
+  int ntiles = int(ctx->tiles.size()), ndim = d.ndim, pery = ctx->bcy == LEM_BC_PERIODIC,
+      perx = ctx->bcx == LEM_BC_PERIODIC, phi = d.mode == LEM_MODE_PHI;
+  int64_t n_int = ctx->n_int, n_loc = ctx->n_loc, cstride = d.coef_stride, ny = ctx->ny, nx = ctx->nx;
+  const void* P = f32 ? static_cast<const void*>(ctx->d_P32) : static_cast<const void*>(ctx->d_P);
+  void* args[] = {&P, &n_int, &n_loc, &ctx->d_tiles, &ntiles, &ctx->d_coef, &cstride, &ny, &nx,
+                  &ndim, &pery, &perx, &phi, &ctx->d_r, &d_u, &nsteps};
+  cudaEvent_t stop;
+  LEM_CUDA_TRY(ctx->timing_begin(&stop));
+  const void* fn = f32 ? reinterpret_cast<const void*>(gemv_persistent_kernel<float>)
+                       : reinterpret_cast<const void*>(gemv_persistent_kernel<double>);
+  LEM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, smem, ctx->stream));
+  ctx->timing_end(stop);
+  *done = true;
   return LEM_OK;
 }
 
