@@ -294,13 +294,28 @@ __global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restri
       __syncthreads();
       const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
       const int ie = td.iext[0] * td.iext[1];
+      constexpr int V = 16 / sizeof(PT);
+      const bool vec = (n_loc % V) == 0 && (wl % V) == 0;
       for (int i0 = warp * 4; i0 < ie; i0 += nw * 4) {
         const int i = i0 + grp;
         const bool live = i < ie;
         const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
+        // the same partition of a row over the 8 lanes, and the same order, as gemv_tiles_kernel
+        // (16-byte chunks j = lane, lane + 8, ... when rows allow them): bit-identical results
         Acc acc;
-        if (live)
-          for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
+        if (live) {
+          if (vec) {
+            const int4* r4 = reinterpret_cast<const int4*>(row);
+            for (int j = gl; j < wl / V; j += 8) {
+              const int4 q = __ldcs(r4 + j);
+              const PT* pq = reinterpret_cast<const PT*>(&q);
+#pragma unroll
+              for (int h = 0; h < V; ++h) acc.add(pq[h], w[j * V + h]);
+            }
+          } else {
+            for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
+          }
+        }
         const double y = group_reduce(acc);
         if (live && gl == 0) {
           const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];

@@ -158,3 +158,20 @@ def test_full_size_advdiff2d_fp64_sampled():
     for t in sample:
         D = wins[t].D
         assert rel_l2(got[D], ref[D]) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["phi", "exp"])
+def test_persistent_launch_is_bit_identical(mode, monkeypatch):
+    """Small linear problems run a call's steps in one cooperative launch; the result equals the
+    per-step kernels bit for bit (same lane partition and summation order)."""
+    wl = W.heat1d()
+    a = L.Lem.from_workload(wl, mode=mode)
+    ua = torch.tensor(wl["u0"], dtype=torch.float64, device="cuda")
+    a.step(ua, 7)
+    a.sync()
+    monkeypatch.setenv("LEM_NO_PERSISTENT", "1")
+    ub = torch.tensor(wl["u0"], dtype=torch.float64, device="cuda")
+    a.step(ub, 7)
+    a.sync()
+    a.close()
+    assert torch.equal(ua, ub)
