@@ -13,7 +13,8 @@
  * Conventions used by every entry point
  * -------------------------------------
  * - Meshes are 1D (n[0] = N) or 2D (n[0] = ny rows, n[1] = nx columns); states are
- *   contiguous row-major [y][x] arrays of double, one value per interior mesh node.
+ *   contiguous row-major [y][x] arrays of double, one value per interior mesh node
+ *   (complex problems: one interleaved (re, im) pair of doubles per node).
  * - The operator A is a 3-point (1D) or 5-point (2D) stencil given by its entries in
  *   the order C (diagonal), W (x-1), E (x+1), S (y-1), N (y+1); NOT multiplied by dt.
  *   Homogeneous Dirichlet walls drop the outside neighbour (g = 0); periodic axes wrap.
@@ -54,7 +55,10 @@ typedef enum {
 typedef enum { LEM_BC_DIRICHLET0 = 0, LEM_BC_PERIODIC = 1 } lem_bc;
 typedef enum { LEM_MODE_PHI = 0, LEM_MODE_EXP = 1 } lem_mode;
 /* LEM_PREC_FP64: propagators, residual and apply in IEEE binary64.
- * LEM_PREC_SPLIT: propagators built in FP64, then applied in reduced precision within
+ * Propagators of the split tiers are built with tensor-core products (every Pade product,
+ * squaring and elimination update an exact sum of FP16 slice products, about 2^-45 of the
+ * operands' scale; the environment variable LEM_BUILD_PRODUCTS=fp64 forces FP64 products).
+ * LEM_PREC_SPLIT: propagators applied in reduced precision within
  * 1e-6 relative L2 of the FP64 result after 100 steps, also for fields that decay by orders
  * of magnitude over the run. When every window shares one propagator (2D periodic, constant
  * coefficients, no reaction, tiles dividing the mesh, tile_x a multiple of 8, window width
@@ -120,8 +124,9 @@ typedef struct lem_ctx lem_ctx;
 typedef struct {
   int64_t ntiles;         /* number of owner tiles D_i */
   int64_t nclasses;       /* distinct local operators (propagators) */
-  int64_t n_loc;          /* padded window size (max |M_i|) */
-  int64_t n_int;          /* padded tile size (max |D_i|) */
+  int64_t n_loc;          /* padded window size (max |M_i|; complex: twice that, the real
+                             embedding of the propagator) */
+  int64_t n_int;          /* padded tile size (max |D_i|; complex: twice that) */
   int squarings_max;      /* largest scaling-and-squaring count s over the classes */
   int built;              /* 1 once propagators exist */
   int split_path;         /* 1 if lem_step runs the tcgen05 split-precision kernel */
@@ -138,18 +143,22 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
 
 /* Build every class's local propagator on the device (Sec. 3 step 2 with Pade
  * approximation and scaling-and-squaring, Sec. 1 / Sec. 4): P = R_D phi_1(dt A_M)
- * (PHI) or R_D exp(dt A_M) (EXP), degree-13 Pade, s from the exact 1-norm,
- * FP64 products and LU with partial pivoting.
+ * (PHI) or R_D exp(dt A_M) (EXP), degree-13 Pade, s from the exact 1-norm, Gauss-Jordan
+ * elimination with partial pivoting for the denominator. FP64 tier: FP64 products; split
+ * tiers: tensor-core slice products and a blocked elimination (see lem_prec).
+ * LEM_SCHEME_RB3 builds phi_1 and phi_3 together; complex problems build the real embedding.
  * d_state (device, FP64, may be NULL for linear problems) is the state at which the
  * reaction Jacobian is taken. Synchronises the context stream before returning.
  * Errors: LEM_EINVAL (reaction without state), LEM_ENUMERIC (singular denominator),
  * LEM_ECUDA. */
 lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state);
 
-/* Advance the device state d_state (FP64, row-major, in/out) by nsteps LEM steps
- * (Sec. 3 steps 1-3). Builds the propagators first if they do not exist; with the
- * reaction it rebuilds them every `refresh` steps. Work is enqueued on the context
- * stream; the call returns after enqueueing (no synchronisation) unless a rebuild is due.
+/* Advance the device state d_state (FP64, row-major, in/out; complex: interleaved pairs) by
+ * nsteps LEM steps (Sec. 3 steps 1-3). Builds the propagators first if they do not exist;
+ * with the reaction it rebuilds them every `refresh` steps. Small linear real problems on
+ * the GEMV paths run all nsteps in one cooperative launch (identical results). Work is
+ * enqueued on the context stream; the call returns after enqueueing (no synchronisation)
+ * unless a rebuild is due.
  * Errors: LEM_EINVAL (nsteps < 0, NULL state), LEM_ECUDA. */
 lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps);
 
@@ -159,7 +168,9 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
 
 /* Copy class `cls`'s propagator (n_int x n_loc, row-major, FP64, zero padded) into host
  * memory h_out. Rows follow the tile's owner nodes in row-major order, columns the window
- * nodes in row-major order. Errors: LEM_ENOTREADY (not built), LEM_EINVAL. */
+ * nodes in row-major order. Complex problems: the real embedding [[Re P, -Im P],
+ * [Im P, Re P]] (owner rows real parts then imaginary parts; window columns likewise).
+ * Errors: LEM_ENOTREADY (not built), LEM_EINVAL. */
 lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out);
 
 /* The same for the phi_3 propagator of class `cls` (LEM_SCHEME_RB3 contexts only; LEM_EINVAL
@@ -191,7 +202,8 @@ lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t
 
 /* Per-kernel timing of the dominant propagator-apply kernel (for benchmarks).
  * lem_set_timing(ctx, 1) makes later lem_step calls bracket every launch of the apply
- * kernel (the tcgen05 split GEMM, or the FP64 apply GEMMs) with CUDA events recorded on the
+ * kernel (the tcgen05 split GEMM, the FP64 apply GEMMs, the GEMV -- with LEM_SCHEME_RB3 both
+ * stages of a step together -- or the persistent multi-step GEMV) with CUDA events on the
  * context stream; lem_get_timing synchronises, adds the elapsed times of all recorded
  * launches since the last call to *total_ms and their count to *launches, and resets them.
  * Errors: LEM_EINVAL, LEM_ECUDA. */
