@@ -9,8 +9,10 @@ imports nothing from the product.
 Modules
 -------
 ``lem_oracle``   operator assembly (Eq. spacedisc), decomposition (Sec. 3), Pade-13
-                 scaling-and-squaring expm and phi_1 (Sec. 2 / Sec. 4), the LEM step
-                 (Eq. lem, Sec. 3 steps 1-3) and the global exponential step it approximates.
+                 scaling-and-squaring expm, phi_1 and phi_k (Sec. 2 / Sec. 4), the LEM step
+                 (Eq. lem, Sec. 3 steps 1-3), a third-order exponential Rosenbrock LEM step
+                 (Sec. 4.2) and the global steps they approximate; real or complex inputs
+                 (the Schroedinger test of Sec. 4.1).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms, invariants,
 an independent library (scipy), arbitrary precision (mpmath) or brute force.
