@@ -67,6 +67,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(local_ms: float) -> float:
+    """The slowest rank's time (every rank gets it): an all-reduce MAX when a process group
+    is up (a CUDA tensor for NCCL, a CPU tensor for gloo), else the local time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -414,10 +432,7 @@ def run_batch(a):
     if world > 1:
         dist.barrier()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
-    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
+    dev_ms_max = max_over_ranks(dev_ms)
     total = sum(npts)
 
     # end to end: every problem's state from pinned host memory, one graph launch, back to host
@@ -462,7 +477,7 @@ def run_batch(a):
             dist.destroy_process_group()
         return
     tflops_peak, _, peak_src = peaks()
-    value = total * a.inner * a.steps * world / (dev_ms_max * 1e-3)
+    value = job_rate(total * a.inner * a.steps, world, dev_ms_max)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": dev_ms_max / a.steps, "higher_is_better": True,
@@ -777,10 +792,7 @@ def main():
     if world > 1:
         dist.barrier()
     dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, stops))
-    t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_ms_max = float(t.item())
+    dev_ms_max = max_over_ranks(dev_ms)
     total_lem_steps = a.warmup * a.inner + a.steps * a.inner
 
     # end to end through the public host API: pinned host state, H2D + steps + D2H per call
@@ -846,7 +858,7 @@ def main():
 
     tflops_peak, hbm_peak, peak_src = peaks()
     khash = kernel_source_hash()
-    value = npts * a.inner * a.steps * world / (dev_ms_max * 1e-3)
+    value = job_rate(npts * a.inner * a.steps, world, dev_ms_max)
     info = ctx.info()
     ntiles = npts // info["n_int"]
     # algorithmic flop of one FP16 product over all windows: 2 n_int n_loc per window
