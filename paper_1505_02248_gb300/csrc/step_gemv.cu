@@ -243,7 +243,8 @@ lem_status gemv_prepare_f32(lem_ctx* ctx) {
 // propagator (four rows per warp) and writes the owner values of u^{n+1} into the other state
 // buffer; one grid barrier ends the step. Linear real problems on the GEMV path only (no
 // Jacobian refresh, one scheme stage).
-template <typename PT>
+// SMEMP: one tile per block, its propagator kept in shared memory for all steps.
+template <typename PT, bool SMEMP>
 __global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restrict__ P, int64_t n_int, int64_t n_loc,
                                                               const TileDesc* __restrict__ tiles, int ntiles,
                                                               const double* __restrict__ coef, int64_t cstride,
@@ -258,6 +259,13 @@ __global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restri
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   const int grp = lane / 8, gl = lane % 8;
   using Acc = typename std::conditional<sizeof(PT) == 8, AccD, AccF>::type;
+  // SMEMP: the block's tile propagator (n_int x n_loc) after the window buffer
+  PT* Ps = reinterpret_cast<PT*>(wraw + ((sizeof(double) * size_t(n_loc) + 15) & ~size_t(15)));
+  if (SMEMP) {
+    const PT* src_p = P + int64_t(tiles[blockIdx.x].cls) * n_int * n_loc;
+    for (int64_t e = threadIdx.x; e < n_int * n_loc; e += blockDim.x) Ps[e] = src_p[e];
+    __syncthreads();
+  }
   // u^n and u^{n+1} alternate between u and src (every node has exactly one owner tile, so
   // each step writes the whole of the other buffer); one grid barrier per step
   double* cur = u;
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restri
         w[k] = PT(v);
       }
       __syncthreads();
-      const PT* Pt = P + int64_t(td.cls) * n_int * n_loc;
+      const PT* Pt = SMEMP ? Ps : P + int64_t(td.cls) * n_int * n_loc;
       const int ie = td.iext[0] * td.iext[1];
       constexpr int V = 16 / sizeof(PT);
       const bool vec = (n_loc % V) == 0 && (wl % V) == 0;
@@ -307,7 +315,7 @@ __global__ void __launch_bounds__(256) gemv_persistent_kernel(const PT* __restri
           if (vec) {
             const int4* r4 = reinterpret_cast<const int4*>(row);
             for (int j = gl; j < wl / V; j += 8) {
-              const int4 q = __ldcs(r4 + j);
+              const int4 q = SMEMP ? r4[j] : __ldcs(r4 + j);
               const PT* pq = reinterpret_cast<const PT*>(&q);
 #pragma unroll
               for (int h = 0; h < V; ++h) acc.add(pq[h], w[j * V + h]);
@@ -347,8 +355,8 @@ static int persistent_blocks(lem_ctx* ctx, bool f32, int nsteps) {
     return 0;
   }
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
-  cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<float>, 256, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<double>, 256, smem);
+  cudaError_t e = f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<float, false>, 256, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_persistent_kernel<double, false>, 256, smem);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     return 0;
@@ -363,7 +371,27 @@ lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool
   if (blocks < 1) return LEM_OK;
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
   const lem_problem_desc& d = ctx->desc;
-  const size_t smem = sizeof(double) * size_t(ctx->n_loc);
+  // one tile per block with a propagator small enough for shared memory: keep it there
+  const size_t wbytes = (sizeof(double) * size_t(ctx->n_loc) + 15) & ~size_t(15);
+  const size_t pbytes = (f32 ? sizeof(float) : sizeof(double)) * size_t(ctx->n_int) * size_t(ctx->n_loc);
+  bool smemp = blocks == int(ctx->tiles.size()) && wbytes + pbytes <= 200 * 1024 &&
+               std::getenv("LEM_NO_SMEM_P") == nullptr;
+  const void* fn_s = f32 ? reinterpret_cast<const void*>(gemv_persistent_kernel<float, true>)
+                         : reinterpret_cast<const void*>(gemv_persistent_kernel<double, true>);
+  if (smemp) {  // every block must still be co-resident with the larger footprint
+    int per_sm = 0, nsm = 0;
+    if (cudaFuncSetAttribute(fn_s, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wbytes + pbytes)) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn_s, 256, wbytes + pbytes) != cudaSuccess ||
+        int64_t(per_sm) * nsm < blocks) {
+      cudaGetLastError();
+      smemp = false;
+    }
+  }
+  const size_t smem = smemp ? wbytes + pbytes : sizeof(double) * size_t(ctx->n_loc);
+  const void* fn = smemp ? fn_s
+                         : (f32 ? reinterpret_cast<const void*>(gemv_persistent_kernel<float, false>)
+                                : reinterpret_cast<const void*>(gemv_persistent_kernel<double, false>));
   int ntiles = int(ctx->tiles.size()), ndim = d.ndim, pery = ctx->bcy == LEM_BC_PERIODIC,
       perx = ctx->bcx == LEM_BC_PERIODIC, phi = d.mode == LEM_MODE_PHI;
   int64_t n_int = ctx->n_int, n_loc = ctx->n_loc, cstride = d.coef_stride, ny = ctx->ny, nx = ctx->nx;
@@ -372,8 +400,6 @@ lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool
                   &ndim, &pery, &perx, &phi, &ctx->d_r, &d_u, &nsteps};
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
-  const void* fn = f32 ? reinterpret_cast<const void*>(gemv_persistent_kernel<float>)
-                       : reinterpret_cast<const void*>(gemv_persistent_kernel<double>);
   LEM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, smem, ctx->stream));
   ctx->timing_end(stop);
   *done = true;
