@@ -124,3 +124,4 @@ def test_server_create_without_device_reports_cuda_error(lib):
     h = L.C.c_void_p()
     st = lib.lem_server_create(0, 0, L.C.byref(h))
     assert st in (L.LEM_ECUDA, L.LEM_EINVAL) and not h.value
+
