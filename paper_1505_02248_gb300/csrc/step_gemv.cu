@@ -42,6 +42,13 @@ struct AccF {
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(e, pe));
   }
+  // adds a partial sum already rounded to FP32
+  __device__ __forceinline__ void add1(float x) {
+    float s, e;
+    two_sum_d(hi, x, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
 };
 
 // Reduction over the 8 lanes of a row group (lanes 8g .. 8g + 7).
@@ -120,19 +127,22 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
       const PT* rim = Pt + int64_t(live ? int(n_int / 2) + o : 0) * n_loc;
       Acc are, aim;
       if (cvec) {
+        // FP32 rows: four 16-byte loads per lane and row in flight, so a window of up to 128
+        // nodes takes one round trip per row pair; FP64 rows are bound by the FP64 pipe.
+        constexpr int CU = sizeof(PT) == 4 ? 4 : 2;
         const int nv = hl / V;
         const int4* a4 = reinterpret_cast<const int4*>(rre);
         const int4* b4 = reinterpret_cast<const int4*>(rim);
-        for (int j = gl; j < nv; j += 8 * 2) {
-          int4 qa[2], qb[2];
+        for (int j = gl; j < nv; j += 8 * CU) {
+          int4 qa[CU], qb[CU];
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
+          for (int k = 0; k < CU; ++k) {
             const bool ok = live && j + 8 * k < nv;
             qa[k] = ok ? __ldcs(a4 + j + 8 * k) : make_int4(0, 0, 0, 0);
             qb[k] = ok ? __ldcs(b4 + j + 8 * k) : make_int4(0, 0, 0, 0);
           }
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
+          for (int k = 0; k < CU; ++k) {
             if (j + 8 * k >= nv) break;
             const PT* pa = reinterpret_cast<const PT*>(&qa[k]);
             const PT* pb = reinterpret_cast<const PT*>(&qb[k]);
@@ -140,12 +150,28 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
             const int4 wi4 = *reinterpret_cast<const int4*>(w + hl + (j + 8 * k) * V);
             const PT* wr = reinterpret_cast<const PT*>(&wr4);
             const PT* wi = reinterpret_cast<const PT*>(&wi4);
+            if constexpr (sizeof(PT) == 4) {
+              // FP32 rows: a chunk's eight products per part are summed by FMA in FP32 and the
+              // chunk sum enters the float-float accumulator (an exact product split for each of
+              // the four products an element takes part in would make the launch ALU-bound)
+              float sr = 0.0f, si = 0.0f;
 #pragma unroll
-            for (int h = 0; h < V; ++h) {
-              are.add(pa[h], wr[h]);
-              are.add(-pb[h], wi[h]);
-              aim.add(pb[h], wr[h]);
-              aim.add(pa[h], wi[h]);
+              for (int h = 0; h < V; ++h) {
+                sr = fmaf(pa[h], wr[h], sr);
+                sr = fmaf(-pb[h], wi[h], sr);
+                si = fmaf(pb[h], wr[h], si);
+                si = fmaf(pa[h], wi[h], si);
+              }
+              are.add1(sr);
+              aim.add1(si);
+            } else {
+#pragma unroll
+              for (int h = 0; h < V; ++h) {
+                are.add(pa[h], wr[h]);
+                are.add(-pb[h], wi[h]);
+                aim.add(pb[h], wr[h]);
+                aim.add(pa[h], wi[h]);
+              }
             }
           }
         }
