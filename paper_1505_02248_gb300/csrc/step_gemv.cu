@@ -461,8 +461,8 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   auto gemv = [&](const double* P64, const float* P32, const double* x) {
     const int acc = phi ? 1 : 0;
     if (ctx->cplx) {
-      if (f32)
-        gemv_tiles_kernel<float, true><<<nt * rsplit, 256, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+      if (f32)  // short rows, little work per block: 128 threads, more blocks resident per SM
+        gemv_tiles_kernel<float, true><<<nt * rsplit, 128, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
                                                                        d_u, ctx->ny, ctx->nx, acc, rsplit);
       else
         gemv_tiles_kernel<double, true><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
