@@ -88,7 +88,8 @@ typedef enum { LEM_SCHEME_EULER = 0, LEM_SCHEME_RB3 = 1 } lem_scheme;
 typedef enum {
   LEM_APPLY_FP64_GEMM = 0,   /* FP64, one gathered GEMM per class of tiles */
   LEM_APPLY_FP64_GEMV = 1,   /* FP64, one batched GEMV over all tiles (many classes) */
-  LEM_APPLY_F32_GEMV = 2,    /* FP32 propagators, float-float accumulation */
+  LEM_APPLY_F32_GEMV = 2,    /* FP32 propagators, float-float accumulation (complex: of FP32
+                                FMA sums over 16-byte chunks of a row) */
   LEM_APPLY_TC_SPLIT = 3     /* shared propagator on the tcgen05 tensor cores */
 } lem_apply_path;
 

@@ -4,7 +4,8 @@
 // row's result is written straight into its owner node (u_D += y, or u_D = y in EXP mode).
 // The launch is bound by the propagator bytes in HBM (n_int x n_loc per tile), so the
 // reduced-precision variant stores propagators in FP32 (half the bytes) and accumulates the
-// products in float-float; the FP64 variant is the plain reference arithmetic.
+// products in float-float (complex rows: per-chunk FMA sums); the FP64 variant is the plain
+// reference arithmetic.
 //
 // Jacobi update: all tiles must read u^n, so in EXP mode the source is a copy of u^n and in
 // PHI mode the residual array (computed from u^n before this launch).
