@@ -452,18 +452,26 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
   const unsigned nt = unsigned(ctx->tiles.size());
-  // about four waves of blocks (8 resident per SM), at least 32 owner rows per block
+  // about four waves of blocks (8 resident per SM), at least 32 owner rows per block, each
+  // block's share a whole number of passes (a pass: 4 rows per warp), so that no pass runs
+  // part empty (512^2 variable diffusion: 4 blocks of 64 rows per tile, not 5 of 52)
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm < 1) nsm = 152;
   const int rmax = std::max<int>(1, int(ctx->n_int / 32));
-  const int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
+  int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
+  const int threads = (ctx->cplx && f32) ? 128 : 256;
+  {
+    const int owners = int(ctx->cplx ? ctx->n_int / 2 : ctx->n_int), pass = threads / 8;
+    const int rows = ((owners + rsplit - 1) / rsplit + pass - 1) / pass * pass;
+    rsplit = std::max(1, (owners + rows - 1) / rows);
+  }
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
   auto gemv = [&](const double* P64, const float* P32, const double* x) {
     const int acc = phi ? 1 : 0;
     if (ctx->cplx) {
       if (f32)  // short rows, little work per block: 128 threads, more blocks resident per SM
-        gemv_tiles_kernel<float, true><<<nt * rsplit, 128, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
+        gemv_tiles_kernel<float, true><<<nt * rsplit, threads, smem, st>>>(P32, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
                                                                        d_u, ctx->ny, ctx->nx, acc, rsplit);
       else
         gemv_tiles_kernel<double, true><<<nt * rsplit, 256, smem, st>>>(P64, ctx->n_int, ctx->n_loc, ctx->d_tiles, x,
