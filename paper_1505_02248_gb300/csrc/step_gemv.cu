@@ -452,7 +452,7 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
   const unsigned nt = unsigned(ctx->tiles.size());
-  // about four waves of blocks (8 resident per SM), at least 32 owner rows per block, each
+  // about four waves of blocks (6 to 8 resident per SM), at least 32 owner rows per block, each
   // block's share a whole number of passes (a pass: 4 rows per warp), so that no pass runs
   // part empty (512^2 variable diffusion: 4 blocks of 64 rows per tile, not 5 of 52)
   int nsm = 0;
