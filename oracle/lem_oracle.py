@@ -32,6 +32,10 @@ What is here, in the paper's order and notation (dt-scaled throughout, X = dt*A)
   2009): a phi_1 stage and a phi_3 correction, both applied window by window.
   ``global_step_rb3`` / ``global_run_rb3`` are the same scheme on the whole mesh.
 
+* ``porous_m`` (``residual``, ``jacobian``, the step and run functions) -- the porous-medium
+  equation c_t = (c^m)_xx of Sec. 4.2 (Eq. porous): dt F(u) = X phi(u), dt F'(u) =
+  X diag(phi'(u)) with phi(u) = |u|^(m-1) u; ``barenblatt1d`` its closed-form solution.
+
 Parity status: every function above is pinned in ``tests/test_oracle_*.py``.
 The reaction (u - u^3) Rosenbrock variant is pinned only by invariants and by agreement
 with the global step as H grows (no closed form exists for it).
@@ -50,7 +54,7 @@ __all__ = [
     "assemble_operator", "Window", "decompose", "local_propagators", "residual",
     "jacobian", "lem_step", "lem_run", "global_step", "global_run",
     "rb3_defect", "lem_step_rb3", "lem_run_rb3", "global_step_rb3", "global_run_rb3",
-    "heat1d_dst_modes", "heat1d_eigenvalues", "periodic2d_symbol", "periodic2d_fft_step",
+    "porous_phi", "barenblatt1d", "heat1d_dst_modes", "heat1d_eigenvalues", "periodic2d_symbol", "periodic2d_fft_step",
     "rel_l2",
 ]
 
@@ -271,23 +275,39 @@ def local_propagators(Xg: sp.csr_matrix, windows, mode: str = "phi", tiles=None)
     return out
 
 
-def residual(Xg: sp.csr_matrix, u: np.ndarray, dt: float = 0.0, reaction: bool = False):
-    """dt * F(u): X u (linear, g = 0) plus dt * (u - u^3) when the reaction is on."""
+def porous_phi(u: np.ndarray, m: float) -> np.ndarray:
+    """The porous-medium nonlinearity c^m of Eq. porous (Sec. 4.2), extended oddly,
+    |u|^(m-1) u, so that it stays defined where a step undershoots below zero."""
+    return np.abs(u) ** (m - 1.0) * u
+
+
+def residual(Xg: sp.csr_matrix, u: np.ndarray, dt: float = 0.0, reaction: bool = False,
+             porous_m: float = 0.0):
+    """dt * F(u): X u (linear, g = 0) plus dt * (u - u^3) when the reaction is on.
+    Porous medium (porous_m = m > 1): dt * F(u) = X phi(u) with phi(u) = |u|^(m-1) u, the
+    second-difference operator applied to c^m (Eq. porous)."""
+    if porous_m:
+        return Xg @ porous_phi(u, porous_m)
     r = Xg @ u
     if reaction:
         r = r + dt * (u - u ** 3)
     return r
 
 
-def jacobian(Xg: sp.csr_matrix, u: np.ndarray, dt: float, reaction: bool) -> sp.csr_matrix:
-    """dt * F'(u) = X + dt * diag(1 - 3 u^2) (just X for a linear problem)."""
+def jacobian(Xg: sp.csr_matrix, u: np.ndarray, dt: float, reaction: bool,
+             porous_m: float = 0.0) -> sp.csr_matrix:
+    """dt * F'(u) = X + dt * diag(1 - 3 u^2) (just X for a linear problem).
+    Porous medium: dt * F'(u) = X diag(phi'(u)), phi'(u) = m |u|^(m-1) (chain rule through
+    the operator: column j of X scaled by phi'(u_j))."""
+    if porous_m:
+        return (Xg @ sp.diags(porous_m * np.abs(u) ** (porous_m - 1.0))).tocsr()
     if not reaction:
         return Xg
     return (Xg + sp.diags(dt * (1.0 - 3.0 * u ** 2))).tocsr()
 
 
 def lem_step(Xg, u, windows, props, mode: str = "phi", dt: float = 0.0,
-             reaction: bool = False, tiles=None):
+             reaction: bool = False, tiles=None, porous_m: float = 0.0):
     """One LEM step u^n -> u^{n+1} (Sec. 3, steps 1-3; all windows read u^n).
 
     phi: u_D <- u_D + P_i (dt F(u^n))|_{M_i}   (Eq. lem, neighbours frozen at t^n)
@@ -299,7 +319,7 @@ def lem_step(Xg, u, windows, props, mode: str = "phi", dt: float = 0.0,
     out = u.copy()
     sel = range(len(windows)) if tiles is None else tiles
     if mode == "phi":
-        r = residual(Xg, u, dt, reaction)
+        r = residual(Xg, u, dt, reaction, porous_m)
         for i in sel:
             w = windows[i]
             out[w.D] = u[w.D] + props[i] @ r[w.M]
@@ -311,17 +331,19 @@ def lem_step(Xg, u, windows, props, mode: str = "phi", dt: float = 0.0,
 
 
 def lem_run(Xg, u0, windows, nsteps: int, mode: str = "phi", dt: float = 0.0,
-            reaction: bool = False, refresh: int = 0):
+            reaction: bool = False, refresh: int = 0, porous_m: float = 0.0):
     """nsteps LEM steps. Linear problems build the propagators once (Sec. 4: phi matrices
-    computed at the first step only). With the reaction, the Jacobian and its propagators
-    are rebuilt from the current state every ``refresh`` steps (0 = never after step 0):
-    the exponential Euler-Rosenbrock step with a frozen Jacobian (Sec. 4)."""
+    computed at the first step only). With the reaction (or the porous-medium nonlinearity),
+    the Jacobian and its propagators are rebuilt from the current state every ``refresh``
+    steps (0 = never after step 0): the exponential Euler-Rosenbrock step with a frozen
+    Jacobian (Sec. 4)."""
     u = _fp(u0).copy()
     props = None
+    nonlinear = reaction or porous_m
     for n in range(nsteps):
-        if props is None or (reaction and refresh > 0 and n % refresh == 0):
-            props = local_propagators(jacobian(Xg, u, dt, reaction), windows, mode)
-        u = lem_step(Xg, u, windows, props, mode, dt, reaction)
+        if props is None or (nonlinear and refresh > 0 and n % refresh == 0):
+            props = local_propagators(jacobian(Xg, u, dt, reaction, porous_m), windows, mode)
+        u = lem_step(Xg, u, windows, props, mode, dt, reaction, porous_m=porous_m)
     return u
 
 
@@ -362,18 +384,19 @@ def lem_run_rb3(Xg, u0, windows, nsteps: int, dt: float, refresh: int = 0):
 
 
 # --------------------------------------------------------------------------- global reference
-def global_step(Xg, u, dt: float = 0.0, reaction: bool = False, J=None):
+def global_step(Xg, u, dt: float = 0.0, reaction: bool = False, J=None, porous_m: float = 0.0):
     """Global exponential-Euler step u + phi_1(J) dt F(u) with dense phi_1 (small N only).
 
     For a linear problem with g = 0 this is exp(X) u exactly (Sec. 2 identity).
     """
-    Jm = jacobian(Xg, u, dt, reaction) if J is None else J
-    return u + phi1(Jm.toarray()) @ residual(Xg, u, dt, reaction)
+    Jm = jacobian(Xg, u, dt, reaction, porous_m) if J is None else J
+    return u + phi1(Jm.toarray()) @ residual(Xg, u, dt, reaction, porous_m)
 
 
-def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, refresh: int = 0):
+def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, refresh: int = 0,
+               porous_m: float = 0.0):
     u = _fp(u0).copy()
-    if not reaction:
+    if not reaction and not porous_m:
         E = expm_pade13(Xg.toarray())
         for _ in range(nsteps):
             u = E @ u
@@ -381,8 +404,8 @@ def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, ref
     J = None
     for n in range(nsteps):
         if J is None or (refresh > 0 and n % refresh == 0):
-            J = jacobian(Xg, u, dt, reaction)
-        u = global_step(Xg, u, dt, reaction, J=J)
+            J = jacobian(Xg, u, dt, reaction, porous_m)
+        u = global_step(Xg, u, dt, reaction, J=J, porous_m=porous_m)
     return u
 
 
@@ -436,6 +459,15 @@ def periodic2d_fft_step(u2d: np.ndarray, coef_dt: dict, nsteps: int = 1) -> np.n
     (X is circulant, so the 2D DFT diagonalises it)."""
     lam = periodic2d_symbol(u2d.shape, coef_dt)
     return np.real(np.fft.ifft2(np.fft.fft2(u2d) * np.exp(nsteps * lam)))
+
+
+def barenblatt1d(x: np.ndarray, t: float, m: float, A: float) -> np.ndarray:
+    """The closed-form solution of Eq. porous in 1D quoted in Sec. 4.2 (Barenblatt):
+    u(x, t) = t^-k (A^2 - k (m - 1) x^2 / (2 m t^(2k)))_+^(1/(m-1)) with k = 1/(m+1); the
+    paper's t + t0 is the argument t here."""
+    k = 1.0 / (m + 1.0)
+    core = A * A - k * (m - 1.0) * x * x / (2.0 * m * t ** (2.0 * k))
+    return t ** (-k) * np.maximum(core, 0.0) ** (1.0 / (m - 1.0))
 
 
 def rel_l2(a, b) -> float:

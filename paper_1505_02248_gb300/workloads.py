@@ -168,3 +168,23 @@ def schrodinger1d(n: int = 400, L: float = 10.0, kappa: float = 10.0, mu: float 
     u0 = np.exp(-(x - x0) ** 2 / (2 * sigma ** 2)).astype(np.complex128)
     return dict(name=f"schrodinger1d_{n}", shape=(n,), bc=("periodic",), coef=coef, dt=2 * mu * h * h,
                 tile=(tile,), overlap=(overlap,), u0=u0, reaction=False, x=x, h=h)
+
+
+def porous1d(n: int = 400, L: float = 10.0, m: float = 3.0, A: float = 1.0, t0: float = 1.0,
+             mu: float = 4.0, tile: int = 40, overlap: int = 12, refresh: int = 1) -> dict:
+    """1D porous-medium equation c_t = (c^m)_xx (Sec. 4.2, Eq. porous) on [-L/2, L/2] with
+    homogeneous Dirichlet walls and n interior nodes, h = L / (n + 1), x_j = -L/2 + (j + 1) h,
+    centred second differences applied to c^m (constant stencil C = -2/h^2, W = E = 1/h^2).
+    u0 = the Barenblatt profile at time t0 (k = 1/(m+1)):
+        t0^-k (A^2 - k (m-1) x^2 / (2 m t0^(2k)))_+^(1/(m-1)).
+    dt = mu h^2 / max(m u0^(m-1)): mu is the stability parameter of the Jacobian's largest
+    diffusivity at t0. The Jacobian is refreshed every ``refresh`` steps."""
+    h = L / (n + 1)
+    x = -L / 2 + h * (np.arange(n) + 1.0)
+    k = 1.0 / (m + 1.0)
+    u0 = t0 ** (-k) * np.maximum(A * A - k * (m - 1.0) * x * x / (2.0 * m * t0 ** (2.0 * k)), 0.0) ** (1.0 / (m - 1.0))
+    dmax = m * float(np.max(np.abs(u0))) ** (m - 1.0)
+    coef = {"C": -2.0 / h ** 2, "W": 1.0 / h ** 2, "E": 1.0 / h ** 2}
+    return dict(name=f"porous1d_{n}", shape=(n,), bc=("dirichlet",), coef=coef, dt=mu * h * h / dmax,
+                tile=(tile,), overlap=(overlap,), u0=u0, reaction=False, porous_m=m, refresh=refresh,
+                x=x, h=h, t0=t0, A=A)
