@@ -101,13 +101,18 @@ typedef struct {
   int64_t coef_stride;    /* 0: each coef[k] points at one value (constant coefficients);
                              1: each points at n[0]*n[1] values, row-major */
   int reaction;           /* 0: linear; 1: adds u - u^3 to A u (exponential Euler-
-                             Rosenbrock, Jacobian A + diag(1 - 3u^2), Sec. 4) */
+                             Rosenbrock, Jacobian A + diag(1 - 3u^2), Sec. 4); 2: the
+                             porous-medium equation of Sec. 4.2 (Eq. porous), F(u) = A phi(u)
+                             with phi(u) = |u|^(m-1) u and m = porous_m, Jacobian
+                             A diag(phi'(u)); real problems, LEM_SCHEME_EULER, stepped by
+                             lem_step (batches, the server and the allocation-free step refuse
+                             it) */
   double dt;              /* time step (> 0) */
   int tile[2];            /* owner-tile size per axis (>= 1) */
   int overlap[2];         /* buffer width H per side and axis (>= 0) */
   int mode;               /* lem_mode */
   int prec;               /* lem_prec */
-  int refresh;            /* reaction only: rebuild the Jacobian propagators every
+  int refresh;            /* reaction 1 or 2: rebuild the Jacobian propagators every
                              `refresh` steps (0: build once at the first step) */
   int scheme;             /* lem_scheme (0: the exponential Euler step of Eq. lem) */
   int complex_values;     /* 1: complex coefficients and states (e.g. the Schroedinger test of
@@ -117,6 +122,7 @@ typedef struct {
                              0; the apply runs on the batched GEMV with each class's propagator
                              stored as its real embedding [[Re P, -Im P], [Im P, Re P]]. */
   const double* coef_im[5];
+  double porous_m;        /* reaction 2: the exponent m (finite, > 1); ignored otherwise */
 } lem_problem_desc;
 
 typedef struct lem_ctx lem_ctx;

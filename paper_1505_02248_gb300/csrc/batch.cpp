@@ -127,6 +127,8 @@ lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n
     if (ctxs[i]->desc.reaction && ctxs[i]->desc.refresh > 0)
       return fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators and cannot be captured");
     if (ctxs[i]->cplx) return fail(LEM_EINVAL, "batches take real problems (step complex contexts with lem_step)");
+    if (ctxs[i]->desc.reaction == 2)
+      return fail(LEM_EINVAL, "batches do not take the porous-medium problem (step it with lem_step)");
   }
   lem::DeviceGuard guard(dev);
   lem_batch* b = new lem_batch();

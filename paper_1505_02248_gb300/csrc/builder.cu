@@ -5,7 +5,8 @@
 // denominator solve stays in FP64 either way.
 //
 // For each class the local matrix X = dt A_M (principal submatrix on the window, i.e.
-// Dirichlet data at the artificial boundary; plus dt diag(1 - 3u^2) with the reaction) is
+// Dirichlet data at the artificial boundary; plus dt diag(1 - 3u^2) with the reaction, or
+// times diag(phi'(u)) on the right for the porous-medium equation) is
 // assembled in a zero-padded n x n frame (padding is an exact block-diagonal embedding).
 //   EXP:  P = R_D exp(X)
 //   PHI:  P = R_D phi_1(X), the top-right block of exp(Z), Z = [[X, I], [0, 0]].
@@ -45,9 +46,12 @@ struct BatchClass {
 };
 
 // ---------------------------------------------------------------- assembly
+// nonlin 1: + dt diag(1 - 3u^2); nonlin 2 (porous medium): X diag(phi'(u)) with
+// phi'(u) = m |u|^(m-1), each entry scaled by phi' at its column's node.
 __global__ void assemble_local_kernel(double* X, int n, const BatchClass* bc, int nb,
                                       const double* coef, int64_t cstride, int64_t ny,
-                                      int64_t nx, int ndim, const double* u, double dt) {
+                                      int64_t nx, int ndim, const double* u, double dt,
+                                      int nonlin, double pm) {
   const int b = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb || k >= n) return;
@@ -64,19 +68,25 @@ __global__ void assemble_local_kernel(double* X, int n, const BatchClass* bc, in
   const int64_t p = gy * nx + gx;
   const int64_t npts = ny * nx;
   auto cf = [&](int which) { return coef[which * (cstride ? npts : 1) + (cstride ? p : 0)]; };
+  const bool porous = u && nonlin == 2;
+  // phi'(u) at global node q (1 unless porous)
+  auto dphi = [&](int64_t q) { return porous ? pm * pow(fabs(u[q]), pm - 1.0) : 1.0; };
+  // the four neighbours' global nodes (wrapped; a window never holds a node beyond a wall)
+  const int64_t qw = gy * nx + (gx + nx - 1) % nx, qe = gy * nx + (gx + 1) % nx;
+  const int64_t qs = ((gy + ny - 1) % ny) * nx + gx, qn = ((gy + 1) % ny) * nx + gx;
   double diag = cf(0);
-  if (u) diag += dt * (1.0 - 3.0 * u[p] * u[p]);
-  row[k] += diag;
+  if (u && nonlin == 1) diag += dt * (1.0 - 3.0 * u[p] * u[p]);
+  row[k] += diag * dphi(p);
   // W (x - 1) and E (x + 1): inside the window, or wrapped when it spans the periodic axis
-  if (bb >= 1) row[k - 1] += cf(1);
-  else if (c.whole[1]) row[k + wx - 1] += cf(1);
-  if (bb + 1 < wx) row[k + 1] += cf(2);
-  else if (c.whole[1]) row[k + 1 - wx] += cf(2);
+  if (bb >= 1) row[k - 1] += cf(1) * dphi(qw);
+  else if (c.whole[1]) row[k + wx - 1] += cf(1) * dphi(qw);
+  if (bb + 1 < wx) row[k + 1] += cf(2) * dphi(qe);
+  else if (c.whole[1]) row[k + 1 - wx] += cf(2) * dphi(qe);
   if (ndim == 2) {
-    if (a >= 1) row[k - wx] += cf(3);
-    else if (c.whole[0]) row[k + (wy - 1) * wx] += cf(3);
-    if (a + 1 < wy) row[k + wx] += cf(4);
-    else if (c.whole[0]) row[k - (wy - 1) * wx] += cf(4);
+    if (a >= 1) row[k - wx] += cf(3) * dphi(qs);
+    else if (c.whole[0]) row[k + (wy - 1) * wx] += cf(3) * dphi(qs);
+    if (a + 1 < wy) row[k + wx] += cf(4) * dphi(qn);
+    else if (c.whole[0]) row[k - (wy - 1) * wx] += cf(4) * dphi(qn);
   }
 }
 
@@ -458,7 +468,7 @@ static lem_status build_batch(lem_ctx* ctx, int c0, int nb, const double* d_stat
   else
     assemble_local_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(
         Xs, n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u,
-        ctx->desc.dt);
+        ctx->desc.dt, ctx->desc.reaction, ctx->desc.porous_m);
   LEM_CUDA_TRY(cudaGetLastError());
   // exact 1-norms -> s per class (host decides, same rule as theta_13 scaling)
   LEM_CUDA_TRY(cudaMemsetAsync(normbuf.p, 0, sizeof(double) * nb, st));
@@ -698,7 +708,8 @@ static lem_status build_batch_phi3(lem_ctx* ctx, int c0, int nb, const double* d
   // X = dt J_M, the 1-norms, s per class
   const double* u = ctx->desc.reaction ? d_state : nullptr;
   assemble_local_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(
-      Z.m[0], n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u, ctx->desc.dt);
+      Z.m[0], n, d_bc, nb, ctx->d_coef, ctx->desc.coef_stride, ctx->ny, ctx->nx, ctx->desc.ndim, u, ctx->desc.dt,
+      ctx->desc.reaction, ctx->desc.porous_m);
   LEM_CUDA_TRY(cudaMemsetAsync(normbuf.p, 0, sizeof(double) * nb, st));
   norm1_kernel<<<dim3((n + 127) / 128, nb), 128, 0, st>>>(Z.m[0], n,
                                                            reinterpret_cast<unsigned long long*>(normbuf.p));

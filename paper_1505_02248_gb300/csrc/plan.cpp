@@ -27,7 +27,11 @@ lem_status validate(const lem_problem_desc* d) {
   if (d->mode != LEM_MODE_PHI && d->mode != LEM_MODE_EXP) return fail(LEM_EINVAL, "bad mode");
   if (d->prec != LEM_PREC_FP64 && d->prec != LEM_PREC_SPLIT && d->prec != LEM_PREC_SPLIT_FAST)
     return fail(LEM_EINVAL, "bad prec");
-  if (d->reaction != 0 && d->reaction != 1) return fail(LEM_EINVAL, "reaction must be 0 or 1");
+  if (d->reaction < 0 || d->reaction > 2) return fail(LEM_EINVAL, "reaction must be 0, 1 or 2");
+  if (d->reaction == 2 && !(d->porous_m > 1.0 && std::isfinite(d->porous_m)))
+    return fail(LEM_EINVAL, "porous_m must be finite and > 1");
+  if (d->reaction == 2 && d->scheme != LEM_SCHEME_EULER)
+    return fail(LEM_EINVAL, "the porous-medium problem runs the exponential Euler scheme");
   if (d->reaction && d->mode != LEM_MODE_PHI) return fail(LEM_EINVAL, "the reaction needs LEM_MODE_PHI");
   if (d->refresh < 0) return fail(LEM_EINVAL, "refresh must be >= 0");
   if (d->scheme != LEM_SCHEME_EULER && d->scheme != LEM_SCHEME_RB3) return fail(LEM_EINVAL, "bad scheme");

@@ -493,6 +493,7 @@ lem_status lem_submit(lem_server* s, const lem_problem_desc* desc, double tol, d
   if (!(tol > 0.0)) return lem::fail(LEM_EINVAL, "tol must be > 0");
   LEM_TRY(lem::validate(desc));
   if (desc->complex_values) return lem::fail(LEM_EINVAL, "the server takes real problems");
+  if (desc->reaction == 2) return lem::fail(LEM_EINVAL, "the server does not take the porous-medium problem");
   if (s->stop.load()) return lem::fail(LEM_EBUSY, "server is stopping");
   auto r = std::make_shared<Request>();
   r->desc = *desc;

@@ -1,5 +1,6 @@
 // Plain FP64 LEM step (Sec. 3 steps 1-3, Eq. lem): the reference GPU path.
-//   PHI:  r = dt F(u^n) (stencil residual, Eq. spacedisc with g = 0, plus dt(u - u^3));
+//   PHI:  r = dt F(u^n) (stencil residual, Eq. spacedisc with g = 0, plus dt(u - u^3), or the
+//         stencil applied to |u|^(m-1) u for the porous-medium equation);
 //         U_i = r|_{M_i} (halo gather); Y_i = P_{c(i)} U_i; u_D += Y_i (owner scatter).
 //   EXP:  U_i = u^n|_{M_i}; Y_i = P_{c(i)} U_i; u_D = Y_i.
 // All windows read u^n: the gather completes before any owner node is written, and
@@ -12,29 +13,37 @@ namespace lem {
 namespace {
 
 // r[p] = sum of the dt-scaled stencil around p (+ dt (u - u^3)); walls drop neighbours.
+// NL (the reaction kind) 2, porous medium (Eq. porous): the stencil acts on
+// phi(u) = |u|^(m-1) u.
+template <int NL>
 __global__ void residual_fp64_kernel(double* __restrict__ r, const double* __restrict__ u,
                                      const double* __restrict__ coef, int64_t cstride,
                                      int64_t ny, int64_t nx, int ndim, int pery, int perx,
-                                     int reaction, double dt) {
+                                     double dt, double pm) {
   const int64_t npts = ny * nx;
   for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npts;
        p += int64_t(gridDim.x) * blockDim.x) {
     const int64_t y = p / nx, x = p % nx;
     // coefficient `w` (0..4 = C, W, E, S, N) at node p
     auto cf = [&](int w) { return cstride ? coef[int64_t(w) * npts + p] : coef[w]; };
+    auto val = [&](int64_t q) {
+      const double v = u[q];
+      if constexpr (NL == 2) return pow(fabs(v), pm - 1.0) * v;
+      return v;
+    };
     const double uc = u[p];
-    double acc = cf(0) * uc;
-    if (x > 0) acc = fma(cf(1), u[p - 1], acc);
-    else if (perx) acc = fma(cf(1), u[p + nx - 1], acc);
-    if (x + 1 < nx) acc = fma(cf(2), u[p + 1], acc);
-    else if (perx) acc = fma(cf(2), u[p + 1 - nx], acc);
+    double acc = cf(0) * val(p);
+    if (x > 0) acc = fma(cf(1), val(p - 1), acc);
+    else if (perx) acc = fma(cf(1), val(p + nx - 1), acc);
+    if (x + 1 < nx) acc = fma(cf(2), val(p + 1), acc);
+    else if (perx) acc = fma(cf(2), val(p + 1 - nx), acc);
     if (ndim == 2) {
-      if (y > 0) acc = fma(cf(3), u[p - nx], acc);
-      else if (pery) acc = fma(cf(3), u[p + (ny - 1) * nx], acc);
-      if (y + 1 < ny) acc = fma(cf(4), u[p + nx], acc);
-      else if (pery) acc = fma(cf(4), u[p - (ny - 1) * nx], acc);
+      if (y > 0) acc = fma(cf(3), val(p - nx), acc);
+      else if (pery) acc = fma(cf(3), val(p + (ny - 1) * nx), acc);
+      if (y + 1 < ny) acc = fma(cf(4), val(p + nx), acc);
+      else if (pery) acc = fma(cf(4), val(p - (ny - 1) * nx), acc);
     }
-    if (reaction) acc = fma(dt, uc - uc * uc * uc, acc);
+    if constexpr (NL == 1) acc = fma(dt, uc - uc * uc * uc, acc);
     r[p] = acc;
   }
 }
@@ -119,9 +128,16 @@ cudaError_t launch_residual_fp64(const lem_ctx* ctx, double* r, const double* u)
                                                              ctx->bcx == LEM_BC_PERIODIC);
     return cudaGetLastError();
   }
-  residual_fp64_kernel<<<blocks, 256, 0, ctx->stream>>>(
-      r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx, d.ndim, ctx->bcy == LEM_BC_PERIODIC,
-      ctx->bcx == LEM_BC_PERIODIC, d.reaction, d.dt);
+  const int py = ctx->bcy == LEM_BC_PERIODIC, px = ctx->bcx == LEM_BC_PERIODIC;
+  if (d.reaction == 2)
+    residual_fp64_kernel<2><<<blocks, 256, 0, ctx->stream>>>(r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx,
+                                                             d.ndim, py, px, d.dt, d.porous_m);
+  else if (d.reaction == 1)
+    residual_fp64_kernel<1><<<blocks, 256, 0, ctx->stream>>>(r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx,
+                                                             d.ndim, py, px, d.dt, d.porous_m);
+  else
+    residual_fp64_kernel<0><<<blocks, 256, 0, ctx->stream>>>(r, u, ctx->d_coef, d.coef_stride, ctx->ny, ctx->nx,
+                                                             d.ndim, py, px, d.dt, d.porous_m);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,8 @@ extern "C" lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int n
   if (!ctx->built) return lem::fail(LEM_ENOTREADY, "build the propagators (lem_build_propagators) before the allocation-free step");
   if (ctx->desc.reaction && ctx->desc.refresh > 0)
     return lem::fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators, which allocates; use refresh = 0");
+  if (ctx->desc.reaction == 2)
+    return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc does not take the porous-medium problem");
   // scratch layout: r | U | Y, each start 256-byte aligned
   const int64_t nt = int64_t(ctx->tiles.size());
   const int64_t n_r = round_up(ctx->npts, 32);

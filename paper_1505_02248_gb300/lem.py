@@ -45,6 +45,7 @@ class ProblemDesc(C.Structure):
         ("scheme", C.c_int),
         ("complex_values", C.c_int),
         ("coef_im", C.POINTER(C.c_double) * 5),
+        ("porous_m", C.c_double),
     ]
 
 
@@ -136,8 +137,9 @@ def check(status: int, what: str = "") -> None:
 
 
 def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec="fp64",
-              reaction=False, refresh=0, scheme="euler"):
-    """Build a ProblemDesc; returns (desc, keepalive) -- keep the second alive while used."""
+              reaction=False, refresh=0, scheme="euler", porous_m=0.0):
+    """Build a ProblemDesc; returns (desc, keepalive) -- keep the second alive while used.
+    porous_m > 0 selects the porous-medium nonlinearity (reaction 2) with that exponent."""
     shape = tuple(int(s) for s in shape)
     nd = len(shape)
     d = ProblemDesc()
@@ -165,7 +167,8 @@ def make_desc(shape, bc, coef: dict, dt: float, tile, overlap, mode="phi", prec=
             d.coef_im[k] = b.ctypes.data_as(C.POINTER(C.c_double))
     d.coef_stride = stride
     d.complex_values = 1 if cplx else 0
-    d.reaction = 1 if reaction else 0
+    d.reaction = 2 if porous_m else (1 if reaction else 0)
+    d.porous_m = float(porous_m)
     d.dt = float(dt)
     d.mode = MODE[mode]
     d.prec = PREC[prec]
@@ -189,10 +192,10 @@ class Lem:
     """One LEM context (lem_create ... lem_destroy) on a CUDA device."""
 
     def __init__(self, shape, bc, coef, dt, tile, overlap, mode="phi", prec="fp64",
-                 reaction=False, refresh=0, device=0, stream=None, scheme="euler"):
+                 reaction=False, refresh=0, device=0, stream=None, scheme="euler", porous_m=0.0):
         lib = load()
         self._lib = lib
-        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, prec, reaction, refresh, scheme)
+        d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, prec, reaction, refresh, scheme, porous_m)
         self.shape = tuple(int(s) for s in shape)
         self.npts = int(np.prod(self.shape))
         h = C.c_void_p()
@@ -205,7 +208,7 @@ class Lem:
     @classmethod
     def from_workload(cls, wl: dict, **kw):
         args = dict(mode="phi", prec="fp64", reaction=wl.get("reaction", False),
-                    refresh=wl.get("refresh", 0))
+                    refresh=wl.get("refresh", 0), porous_m=wl.get("porous_m", 0.0))
         args.update(kw)
         return cls(wl["shape"], wl["bc"], wl["coef"], wl["dt"], wl["tile"], wl["overlap"], **args)
 

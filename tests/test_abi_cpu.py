@@ -46,7 +46,8 @@ def test_status_strings(lib):
 
 
 @pytest.mark.parametrize("bad", ["ndim", "n", "tile", "overlap", "dt", "mode", "exp_reaction",
-                                 "coef", "refresh"])
+                                 "coef", "refresh", "reaction_kind", "porous_m", "porous_m_nan",
+                                 "porous_rb3", "porous_exp"])
 def test_invalid_descriptors_rejected(lib, bad):
     coef = W.stencil_advdiff_2d(1.0, 1.0, 0.5, 1.0)
     kw = dict(shape=(64, 64), bc=("periodic", "periodic"), coef=coef, dt=1.0, tile=(16, 16),
@@ -70,6 +71,16 @@ def test_invalid_descriptors_rejected(lib, bad):
         d.coef[3] = L.C.POINTER(L.C.c_double)()
     elif bad == "refresh":
         d.refresh = -2
+    elif bad == "reaction_kind":
+        d.reaction = 3
+    elif bad == "porous_m":
+        d.reaction, d.porous_m = 2, 1.0
+    elif bad == "porous_m_nan":
+        d.reaction, d.porous_m = 2, float("nan")
+    elif bad == "porous_rb3":
+        d.reaction, d.porous_m, d.scheme = 2, 3.0, 1
+    elif bad == "porous_exp":
+        d.reaction, d.porous_m, d.mode = 2, 3.0, 1
     st = lib.lem_plan_query(L.C.byref(d), None, None, None, None, None)
     assert st == L.LEM_EINVAL
     assert len(lib.lem_last_error()) > 0
@@ -125,3 +136,14 @@ def test_server_create_without_device_reports_cuda_error(lib):
     st = lib.lem_server_create(0, 0, L.C.byref(h))
     assert st in (L.LEM_ECUDA, L.LEM_EINVAL) and not h.value
 
+
+def test_porous_descriptor_accepted_with_per_tile_classes(lib):
+    """The porous-medium problem (reaction 2) validates on the host; its Jacobian depends on
+    the state, so every tile gets its own propagator class."""
+    wl = W.porous1d(n=400)
+    q = L.plan_query(wl["shape"], wl["bc"], wl["coef"], wl["dt"], wl["tile"], wl["overlap"],
+                     porous_m=wl["porous_m"])
+    assert q["ntiles"] == 10 and q["nclasses"] == 10
+    d, keep = L.make_desc(wl["shape"], wl["bc"], wl["coef"], wl["dt"], wl["tile"], wl["overlap"],
+                          porous_m=3.0)
+    assert d.reaction == 2 and d.porous_m == 3.0
