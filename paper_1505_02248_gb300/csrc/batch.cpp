@@ -43,6 +43,9 @@ void free_batch(lem_batch* b) {
   delete b;
 }
 
+// LEM_OK, or LEM_ECUDA with the call's error as the message.
+lem_status cuda_status(cudaError_t e, const char* what) { return e == cudaSuccess ? LEM_OK : lem::cuda_fail(e, what); }
+
 // Capture one launch of a schedule into an executable graph. lanes: each lane's problems in
 // sequence on the lane's stream, the lanes in parallel; fused: the multi-problem steps.
 lem_status capture(lem_batch* b, double* const* states, lem::SplitBatch* sb, cudaGraph_t* g_out,
@@ -54,8 +57,8 @@ lem_status capture(lem_batch* b, double* const* states, lem::SplitBatch* sb, cud
   std::vector<cudaEvent_t> ev(b->nlanes + 1, nullptr);
   lem_status st = LEM_OK;
   for (auto& e : ev)
-    if (st == LEM_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = LEM_ECUDA;
-  if (st == LEM_OK && cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LEM_ECUDA;
+    if (st == LEM_OK) st = cuda_status(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "capture event");
+  if (st == LEM_OK) st = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   if (st == LEM_OK) {
     if (sb) {
       st = lem::split_batch_step(sb, b->steps, cap);
@@ -148,9 +151,9 @@ lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n
       st = fail(LEM_ENOMEM, "batch scratch states");
       break;
     }
-    if (cudaMemcpyAsync(tmp[i], d_states[i], sizeof(double) * ctxs[i]->npts, cudaMemcpyDeviceToDevice,
-                        ctxs[i]->stream) != cudaSuccess)
-      st = LEM_ECUDA;
+    const cudaError_t e = cudaMemcpyAsync(tmp[i], d_states[i], sizeof(double) * ctxs[i]->npts,
+                                          cudaMemcpyDeviceToDevice, ctxs[i]->stream);
+    if (e != cudaSuccess) st = lem::cuda_fail(e, "batch scratch copy");
   }
   // warm up (builds, lazy buffers, packed propagators) and time each problem
   b->est_ms.assign(n, 0.0);
@@ -191,8 +194,11 @@ lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n
       b->lane[i] = l;
     }
     b->lane_streams.assign(b->nlanes, nullptr);
-    for (auto& s : b->lane_streams)
-      if (st == LEM_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = LEM_ECUDA;
+    for (auto& s : b->lane_streams) {
+      if (st != LEM_OK) break;
+      const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e != cudaSuccess) st = lem::cuda_fail(e, "lane stream");
+    }
   }
   // time both candidate schedules on the scratch states
   const bool can_fuse = lem::split_batch_eligible(const_cast<lem_ctx* const*>(ctxs), n);
@@ -284,11 +290,11 @@ lem_status lem_batch_profile(lem_batch* b, int nsteps, double* gemm_ms, double* 
   std::vector<cudaEvent_t> ev(2 * nsteps + 4, nullptr);
   lem_status st = LEM_OK;
   for (auto& e : ev)
-    if (st == LEM_OK && cudaEventCreate(&e) != cudaSuccess) st = LEM_ECUDA;
-  if (st == LEM_OK) st = cudaEventRecord(ev[2 * nsteps + 2], b->stream) == cudaSuccess ? LEM_OK : LEM_ECUDA;
+    if (st == LEM_OK) st = cuda_status(cudaEventCreate(&e), "profile event");
+  if (st == LEM_OK) st = cuda_status(cudaEventRecord(ev[2 * nsteps + 2], b->stream), "cudaEventRecord");
   if (st == LEM_OK) st = lem::split_batch_step(b->sb, nsteps, b->stream, ev.data());
-  if (st == LEM_OK) st = cudaEventRecord(ev[2 * nsteps + 3], b->stream) == cudaSuccess ? LEM_OK : LEM_ECUDA;
-  if (st == LEM_OK && cudaEventSynchronize(ev[2 * nsteps + 3]) != cudaSuccess) st = LEM_ECUDA;
+  if (st == LEM_OK) st = cuda_status(cudaEventRecord(ev[2 * nsteps + 3], b->stream), "cudaEventRecord");
+  if (st == LEM_OK) st = cuda_status(cudaEventSynchronize(ev[2 * nsteps + 3]), "cudaEventSynchronize");
   if (st == LEM_OK) {
     float t = 0.0f, total = 0.0f;
     cudaEventElapsedTime(&total, ev[2 * nsteps + 2], ev[2 * nsteps + 3]);
