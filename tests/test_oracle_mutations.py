@@ -1,0 +1,199 @@
+"""Planted mistakes in the oracle (on the CPU only): each plausible error below must make an
+independent check fail, and the unmutated oracle must pass the same check. The checks rest on
+closed forms, library routines or brute force, never on the oracle itself:
+
+  expm: eigendecomposition of a symmetric matrix (numpy eigh)
+  phi_1: the scalar closed form (e^z - 1) / z
+  operator: the action on a plane wave (its symbol, C + W e^-ikh + E e^ikh)
+  LEM: one window over the mesh equals exp(X) u (Sec. 2 identity)
+  reaction: the scalar exponential-Euler step of c' = c - c^3 for a uniform state
+  Jacobians: finite differences of the residual
+  windows: the dilated, clipped tile listed by hand on a tiny mesh (Sec. 3, Fig. 3)
+  porous medium: exact mass conservation of the global step (Sec. 4.2)
+  Schroedinger: the free equation against its Fourier closed form (Sec. 4.1)
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle.lem_oracle as OL
+from paper_1505_02248_gb300 import workloads as W
+
+
+def _heat(n=32, mu=10.0):
+    return OL.assemble_operator((n,), ("dirichlet",), W.stencil_heat_1d(1.0, 1.0), mu).toarray()
+
+
+def check_expm():
+    X = _heat()
+    lam, V = np.linalg.eigh(X)
+    ref = (V * np.exp(lam)) @ V.T
+    return np.abs(OL.expm_pade13(X) - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def check_phi1():
+    z = np.array([[-3.7]])
+    return abs(OL.phi1(z)[0, 0] - (np.exp(-3.7) - 1.0) / -3.7) <= 1e-14
+
+
+def check_operator_symbol():
+    n, h = 64, 1.0
+    coef = {"C": -3.0, "W": 2.0, "E": 0.5}
+    X = OL.assemble_operator((n,), ("periodic",), coef, 1.0)
+    k = 2 * np.pi * 5 / n
+    v = np.exp(1j * k * np.arange(n))
+    lam = coef["C"] + coef["W"] * np.exp(-1j * k * h) + coef["E"] * np.exp(1j * k * h)
+    return np.abs(X @ v - lam * v).max() <= 1e-12
+
+
+def check_one_window_is_global():
+    n = 40
+    coef = {"C": -2.5, "W": 2.0, "E": 0.5}  # not symmetric: a transposed propagator shows
+    X = OL.assemble_operator((n,), ("periodic",), coef, 0.8)
+    u0 = np.sin(2 * np.pi * np.arange(n) / n) + 0.3 * np.cos(6 * np.pi * np.arange(n) / n)
+    one = OL.decompose((n,), ("periodic",), (n,), (0,))
+    got = OL.lem_run(X, u0, one, 3, "phi")
+    lam, V = np.linalg.eig(X.toarray())
+    ref = np.real(V @ np.diag(np.exp(3 * lam)) @ np.linalg.solve(V, u0))
+    return OL.rel_l2(got, ref) <= 1e-12
+
+
+def check_reaction_uniform_state():
+    n, dt, c = 32, 0.3, 0.4
+    X = OL.assemble_operator((n,), ("periodic",), W.stencil_heat_1d(1.0, 1.0), dt)
+    got = OL.global_step(X, np.full(n, c), dt, True)
+    z = dt * (1.0 - 3.0 * c * c)
+    ref = c + (np.exp(z) - 1.0) / z * dt * (c - c ** 3)
+    return np.abs(got - ref).max() <= 1e-13
+
+
+def check_reaction_jacobian():
+    n, dt = 24, 0.2
+    X = OL.assemble_operator((n,), ("periodic",), W.stencil_heat_1d(1.0, 1.0), dt)
+    rng = np.random.default_rng(3)
+    u, v = rng.standard_normal(n), rng.standard_normal(n)
+    eps = 1e-6
+    fd = (OL.residual(X, u + eps * v, dt, True) - OL.residual(X, u - eps * v, dt, True)) / (2 * eps)
+    return OL.rel_l2(OL.jacobian(X, u, dt, True) @ v, fd) <= 1e-8
+
+
+def check_windows_by_hand():
+    wins = OL.decompose((20,), ("dirichlet",), (5,), (3,))
+    want = [list(range(0, 8)), list(range(2, 13)), list(range(7, 18)), list(range(12, 20))]
+    return [w.M.tolist() for w in wins] == want
+
+
+def check_porous_mass():
+    wl = W.porous1d(n=60)
+    X = OL.assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    g = OL.global_run(X, wl["u0"], 5, wl["dt"], refresh=1, porous_m=3.0)
+    return abs(g.sum() / wl["u0"].sum() - 1.0) <= 1e-12
+
+
+def check_free_schroedinger():
+    wl = W.schrodinger1d(n=64, kappa=0.0, mu=2.0)
+    X = OL.assemble_operator(wl["shape"], wl["bc"], wl["coef"], wl["dt"])
+    got = OL.global_run(X, wl["u0"], 3)
+    k = np.arange(64)
+    lam = 0.5j * (-4.0 * np.sin(np.pi * k / 64) ** 2 / wl["h"] ** 2) * wl["dt"]
+    ref = np.fft.ifft(np.fft.fft(wl["u0"]) * np.exp(3 * lam))
+    return OL.rel_l2(got, ref) <= 1e-12
+
+
+# ---------------------------------------------------------------- mutations
+def m_drop_pade_term(mp):
+    b = list(OL._B)
+    b[5] = 0.0
+    mp.setattr(OL, "_B", b)
+
+
+def m_theta_too_large(mp):
+    mp.setattr(OL, "THETA13", 60.0)
+
+
+def m_swap_west_east(mp):
+    orig = OL.assemble_operator
+
+    def bad(shape, bc, coef, dt):
+        c = dict(coef)
+        c["W"], c["E"] = coef["E"], coef["W"]
+        return orig(shape, bc, c, dt)
+    mp.setattr(OL, "assemble_operator", bad)
+
+
+def m_u_instead_of_r(mp):
+    mp.setattr(OL, "residual", lambda Xg, u, dt=0.0, reaction=False, porous_m=0.0: u)
+
+
+def m_transposed_propagator(mp):
+    orig = OL.local_propagators
+    mp.setattr(OL, "local_propagators", lambda *a, **k: [P.T.copy() if P is not None else None for P in orig(*a, **k)])
+
+
+def m_phi1_is_exp(mp):
+    mp.setattr(OL, "phi1", lambda X: OL.expm_pade13(X))
+
+
+def m_reaction_sign(mp):
+    orig = OL.residual
+
+    def bad(Xg, u, dt=0.0, reaction=False, porous_m=0.0):
+        return orig(Xg, u, dt, False, porous_m) + (dt * (u ** 3 - u) if reaction else 0.0)
+    mp.setattr(OL, "residual", bad)
+
+
+def m_reaction_jacobian(mp):
+    orig = OL.jacobian
+
+    def bad(Xg, u, dt, reaction, porous_m=0.0):
+        if reaction and not porous_m:
+            return (Xg + sp.diags(dt * (1.0 - u ** 2))).tocsr()
+        return orig(Xg, u, dt, reaction, porous_m)
+    mp.setattr(OL, "jacobian", bad)
+
+
+def m_window_short_by_one(mp):
+    orig = OL._axis_ranges
+
+    def bad(n, tile, H, periodic):
+        return [(d, w[1:] if len(w) > len(d) and w[0] != d[0] else w) for d, w in orig(n, tile, H, periodic)]
+    mp.setattr(OL, "_axis_ranges", bad)
+
+
+def m_porous_row_scaled(mp):
+    orig = OL.jacobian
+
+    def bad(Xg, u, dt, reaction, porous_m=0.0):
+        if porous_m:
+            return (sp.diags(porous_m * np.abs(u) ** (porous_m - 1.0)) @ Xg).tocsr()
+        return orig(Xg, u, dt, reaction, porous_m)
+    mp.setattr(OL, "jacobian", bad)
+
+
+def m_conjugate_stencil(mp):
+    orig = OL.assemble_operator
+    mp.setattr(OL, "assemble_operator",
+               lambda shape, bc, coef, dt: orig(shape, bc, {k: np.conj(v) for k, v in coef.items()}, dt))
+
+
+CASES = {
+    "dropped Pade term": (m_drop_pade_term, check_expm),
+    "theta_13 too large": (m_theta_too_large, check_expm),
+    "W and E swapped": (m_swap_west_east, check_operator_symbol),
+    "u instead of the residual": (m_u_instead_of_r, check_one_window_is_global),
+    "transposed propagator": (m_transposed_propagator, check_one_window_is_global),
+    "phi_1 returns exp": (m_phi1_is_exp, check_phi1),
+    "reaction sign flipped": (m_reaction_sign, check_reaction_uniform_state),
+    "reaction Jacobian 1 - u^2": (m_reaction_jacobian, check_reaction_jacobian),
+    "window short by one node": (m_window_short_by_one, check_windows_by_hand),
+    "porous Jacobian row-scaled": (m_porous_row_scaled, check_porous_mass),
+    "Schroedinger stencil conjugated": (m_conjugate_stencil, check_free_schroedinger),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_planted_mistake_is_caught(name, monkeypatch):
+    mutate, check = CASES[name]
+    assert check(), "the unmutated oracle must pass the check"
+    mutate(monkeypatch)
+    assert not check(), f"planted mistake '{name}' went unnoticed"
