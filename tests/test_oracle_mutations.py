@@ -11,10 +11,14 @@ closed forms, library routines or brute force, never on the oracle itself:
   windows: the dilated, clipped tile listed by hand on a tiny mesh (Sec. 3, Fig. 3)
   porous medium: exact mass conservation of the global step (Sec. 4.2)
   Schroedinger: the free equation against its Fourier closed form (Sec. 4.1)
+  phi_3: the scalar closed form (e^z - 1 - z - z^2/2) / z^3
+  exprb32: the local error against a library ODE solver (scipy DOP853) falls by about 2^4
+           per halving of dt (third order); a dropped factor 2 leaves about 2^3
 """
 import numpy as np
 import pytest
 import scipy.sparse as sp
+from scipy.integrate import solve_ivp
 
 import oracle.lem_oracle as OL
 from paper_1505_02248_gb300 import workloads as W
@@ -100,6 +104,26 @@ def check_free_schroedinger():
     return OL.rel_l2(got, ref) <= 1e-12
 
 
+def check_phi3():
+    z = -2.5
+    ref = (np.exp(z) - 1.0 - z - z * z / 2.0) / z ** 3
+    return abs(OL.phik(np.array([[z]]), 3)[0, 0] - ref) <= 1e-14
+
+
+def check_rb3_local_order():
+    n = 16
+    coef = W.stencil_heat_1d(4.0, 1.0)
+    A = OL.assemble_operator((n,), ("periodic",), coef, 1.0).toarray()
+    u0 = 0.6 * np.sin(2 * np.pi * np.arange(n) / n) + 0.2
+    errs = []
+    for dt in (0.1, 0.05):
+        X = OL.assemble_operator((n,), ("periodic",), coef, dt)
+        exact = solve_ivp(lambda t, u: A @ u + u - u ** 3, (0.0, dt), u0, method="DOP853",
+                          rtol=1e-13, atol=1e-14).y[:, -1]
+        errs.append(np.linalg.norm(OL.global_step_rb3(X, u0, dt, u0.copy()) - exact))
+    return errs[0] / errs[1] >= 10.0
+
+
 # ---------------------------------------------------------------- mutations
 def m_drop_pade_term(mp):
     b = list(OL._B)
@@ -176,6 +200,16 @@ def m_conjugate_stencil(mp):
                lambda shape, bc, coef, dt: orig(shape, bc, {k: np.conj(v) for k, v in coef.items()}, dt))
 
 
+def m_phik_off_by_one(mp):
+    orig = OL.phik
+    mp.setattr(OL, "phik", lambda X, k: orig(X, k - 1) if k == 3 else orig(X, k))
+
+
+def m_rb3_factor_one(mp):
+    orig = OL.rb3_defect
+    mp.setattr(OL, "rb3_defect", lambda u, U, um, dt: 0.5 * orig(u, U, um, dt))
+
+
 CASES = {
     "dropped Pade term": (m_drop_pade_term, check_expm),
     "theta_13 too large": (m_theta_too_large, check_expm),
@@ -188,6 +222,8 @@ CASES = {
     "window short by one node": (m_window_short_by_one, check_windows_by_hand),
     "porous Jacobian row-scaled": (m_porous_row_scaled, check_porous_mass),
     "Schroedinger stencil conjugated": (m_conjugate_stencil, check_free_schroedinger),
+    "phi_k one block off": (m_phik_off_by_one, check_phi3),
+    "exprb32 correction factor 1": (m_rb3_factor_one, check_rb3_local_order),
 }
 
 
