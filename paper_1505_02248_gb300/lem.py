@@ -188,6 +188,32 @@ def plan_query(shape, bc, coef, dt, tile, overlap, **kw):
     return dict(ntiles=nt.value, nclasses=nc.value, n_loc=nl.value, n_int=ni.value, tiles=info)
 
 
+def check_device_state(state, npts: int, complex_: bool = False, device=None):
+    """Raise unless `state` is a contiguous CUDA tensor of npts float64 (complex128 for a
+    complex problem) values, on `device` when given: the library dereferences its pointer on
+    the GPU, so a host or mis-sized buffer must never reach it."""
+    if not getattr(state, "is_cuda", False):
+        raise TypeError("the state must be a CUDA tensor")
+    if not state.is_contiguous():
+        raise ValueError("the state must be contiguous")
+    if state.dtype.itemsize != (16 if complex_ else 8) or state.is_complex() != complex_ or \
+            not (state.is_complex() or state.is_floating_point()):
+        raise TypeError("the state must be complex128" if complex_ else "the state must be float64")
+    if state.numel() != npts:
+        raise ValueError(f"the state has {state.numel()} values, the mesh {npts}")
+    if device is not None and state.device.index != int(device):
+        raise ValueError(f"the state is on {state.device}, the context on cuda:{int(device)}")
+
+
+def check_host_state(state, npts: int, complex_: bool = False):
+    """Raise unless `state` is a C-contiguous numpy array of npts float64 (complex128) values."""
+    want = np.complex128 if complex_ else np.float64
+    if not isinstance(state, np.ndarray) or state.dtype != want:
+        raise TypeError(f"the state must be a numpy {np.dtype(want).name} array")
+    if not state.flags.c_contiguous or state.size != npts:
+        raise ValueError(f"the state must be C-contiguous with {npts} values")
+
+
 class Lem:
     """One LEM context (lem_create ... lem_destroy) on a CUDA device."""
 
@@ -202,6 +228,7 @@ class Lem:
         st = C.c_void_p(stream) if stream is not None else None
         check(lib.lem_create(C.byref(d), int(device), st, C.byref(h)), "lem_create")
         self.complex = bool(d.complex_values)
+        self.device = int(device)
         del keep
         self._h = h
 
@@ -231,29 +258,27 @@ class Lem:
 
     # -- calls -------------------------------------------------------------------------
     def build(self, state=None):
+        if state is not None:
+            check_device_state(state, self.npts, self.complex, self.device)
         ptr = None if state is None else C.c_void_p(state.data_ptr())
         check(self._lib.lem_build_propagators(self._h, ptr), "lem_build_propagators")
 
     def step(self, state, nsteps: int):
         """Advance a CUDA tensor in place: float64 (npts values), or complex128 (npts values,
         interleaved re/im) for a complex problem."""
-        assert state.is_cuda and state.is_contiguous()
-        assert state.dtype.itemsize == (16 if self.complex else 8) and state.is_complex() == self.complex
-        assert state.numel() == self.npts
+        check_device_state(state, self.npts, self.complex, self.device)
         check(self._lib.lem_step(self._h, C.c_void_p(state.data_ptr()), int(nsteps)), "lem_step")
 
     def step_noalloc(self, state, nsteps: int):
         """lem_step_fp64_noalloc: the FP64 step with static scratch (no device allocation)."""
-        assert state.is_cuda and state.dtype.itemsize == 8 and state.is_contiguous()
-        assert state.numel() == self.npts
+        check_device_state(state, self.npts, False, self.device)
         check(self._lib.lem_step_fp64_noalloc(self._h, C.c_void_p(state.data_ptr()), int(nsteps)),
               "lem_step_fp64_noalloc")
 
     def step_host(self, state: np.ndarray, nsteps: int):
         """Advance a host float64 (complex128 for a complex problem) array in place (copies in
         and out inside the call)."""
-        assert state.dtype == (np.complex128 if self.complex else np.float64)
-        assert state.flags.c_contiguous and state.size == self.npts
+        check_host_state(state, self.npts, self.complex)
         check(self._lib.lem_step_host(self._h, state.ctypes.data_as(C.c_void_p), int(nsteps)),
               "lem_step_host")
 
@@ -318,7 +343,7 @@ class Server:
     def submit(self, shape, bc, coef, dt, tile, overlap, state: np.ndarray, nsteps: int, tol: float = 1e-6,
                mode="phi", reaction=False, refresh=0) -> int:
         """Queue `state` (float64, C-contiguous, updated in place when done); returns a ticket."""
-        assert state.dtype == np.float64 and state.flags.c_contiguous
+        check_host_state(state, int(np.prod([int(v) for v in shape])))
         d, keep = make_desc(shape, bc, coef, dt, tile, overlap, mode, "fp64", reaction, refresh)
         t = C.c_uint64()
         check(self._lib.lem_submit(self._h, C.byref(d), float(tol), state.ctypes.data_as(C.c_void_p), int(nsteps),
@@ -365,6 +390,10 @@ class Batch:
         lib = load()
         self._lib = lib
         n = len(ctxs)
+        if n != len(states):
+            raise ValueError("one state per context")
+        for c, s in zip(ctxs, states):
+            check_device_state(s, c.npts, c.complex, c.device)
         self._ctxs = list(ctxs)
         self._states = list(states)  # keep the captured tensors alive
         hc = (C.c_void_p * n)(*[c._h.value for c in ctxs])

@@ -147,3 +147,62 @@ def test_porous_descriptor_accepted_with_per_tile_classes(lib):
     d, keep = L.make_desc(wl["shape"], wl["bc"], wl["coef"], wl["dt"], wl["tile"], wl["overlap"],
                           porous_m=3.0)
     assert d.reaction == 2 and d.porous_m == 3.0
+
+
+class _FakeCudaTensor:
+    """Just the tensor attributes the binding's checks read (no CUDA device here)."""
+
+    def __init__(self, n, itemsize=8, complex_=False, floating=True, contiguous=True, index=0):
+        import torch
+        self.is_cuda = True
+        self._n, self._contig, self._cplx, self._float = n, contiguous, complex_, floating
+        self.dtype = type("D", (), {"itemsize": itemsize})()
+        self.device = torch.device("cuda", index)
+
+    def is_contiguous(self):
+        return self._contig
+
+    def is_complex(self):
+        return self._cplx
+
+    def is_floating_point(self):
+        return self._float
+
+    def numel(self):
+        return self._n
+
+
+def test_device_state_checks_raise_instead_of_passing_bad_pointers():
+    """The binding hands the library a raw device pointer: a host tensor, a wrong type or size,
+    or another device must raise (explicit checks, kept under python -O)."""
+    import torch
+    with pytest.raises(TypeError):
+        L.check_device_state(torch.zeros(16, dtype=torch.float64), 16)
+    L.check_device_state(_FakeCudaTensor(16), 16, device=0)
+    L.check_device_state(_FakeCudaTensor(16, itemsize=16, complex_=True), 16, complex_=True)
+    with pytest.raises(ValueError):
+        L.check_device_state(_FakeCudaTensor(15), 16)
+    with pytest.raises(ValueError):
+        L.check_device_state(_FakeCudaTensor(16, contiguous=False), 16)
+    with pytest.raises(TypeError):
+        L.check_device_state(_FakeCudaTensor(16, itemsize=4), 16)          # float32
+    with pytest.raises(TypeError):
+        L.check_device_state(_FakeCudaTensor(16, floating=False), 16)      # int64
+    with pytest.raises(TypeError):
+        L.check_device_state(_FakeCudaTensor(16), 16, complex_=True)       # real for complex
+    with pytest.raises(ValueError):
+        L.check_device_state(_FakeCudaTensor(16, index=1), 16, device=0)
+
+
+def test_host_state_checks():
+    L.check_host_state(np.zeros(12), 12)
+    L.check_host_state(np.zeros((3, 4)), 12)
+    L.check_host_state(np.zeros(12, dtype=np.complex128), 12, complex_=True)
+    with pytest.raises(TypeError):
+        L.check_host_state(np.zeros(12, dtype=np.float32), 12)
+    with pytest.raises(TypeError):
+        L.check_host_state([0.0] * 12, 12)
+    with pytest.raises(ValueError):
+        L.check_host_state(np.zeros(11), 12)
+    with pytest.raises(ValueError):
+        L.check_host_state(np.zeros((4, 6))[:, ::2], 12)
