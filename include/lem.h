@@ -155,14 +155,15 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
  * tiers: tensor-core slice products and a blocked elimination (see lem_prec).
  * LEM_SCHEME_RB3 builds phi_1 and phi_3 together; complex problems build the real embedding.
  * d_state (device, FP64, may be NULL for linear problems) is the state at which the
- * reaction Jacobian is taken. Synchronises the context stream before returning.
- * Errors: LEM_EINVAL (reaction without state), LEM_ENUMERIC (singular denominator),
+ * Jacobian of a nonlinear problem (reaction 1 or 2) is taken. Synchronises the context stream
+ * before returning.
+ * Errors: LEM_EINVAL (nonlinear problem without state), LEM_ENUMERIC (singular denominator),
  * LEM_ECUDA. */
 lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state);
 
 /* Advance the device state d_state (FP64, row-major, in/out; complex: interleaved pairs) by
  * nsteps LEM steps (Sec. 3 steps 1-3). Builds the propagators first if they do not exist;
- * with the reaction it rebuilds them every `refresh` steps. Small linear real problems on
+ * for a nonlinear problem (reaction 1 or 2) it rebuilds them every `refresh` steps. Small linear real problems on
  * the GEMV paths run all nsteps in one cooperative launch (identical results). Work is
  * enqueued on the context stream; the call returns after enqueueing (no synchronisation)
  * unless a rebuild is due.
@@ -170,7 +171,9 @@ lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state);
 lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps);
 
 /* Same as lem_step on a HOST state (pinned or pageable): copies it to the device,
- * advances nsteps, copies it back and synchronises. */
+ * advances nsteps, copies it back and synchronises. The first call allocates a device copy
+ * of the state, kept by the context. Errors: those of lem_step, LEM_ENOMEM, LEM_ETIMEOUT
+ * (a bounded wait in a tensor-core kernel expired), LEM_ECUDA. */
 lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
 
 /* Copy class `cls`'s propagator (n_int x n_loc, row-major, FP64, zero padded) into host
@@ -184,18 +187,19 @@ lem_status lem_get_propagator(lem_ctx* ctx, int64_t cls, double* h_out);
  * otherwise): R_D phi_3(dt J_M), the correction stage of the third-order Rosenbrock step. */
 lem_status lem_get_propagator_phi3(lem_ctx* ctx, int64_t cls, double* h_out);
 
-/* Class of tile `tile` (row-major over the tile grid) or -1 on a bad index. */
 /* Load every class's propagator from host memory (FP64, nclasses x n_int x n_loc, the layout
  * lem_get_propagator returns per class) instead of building them: with lem_get_propagator this
  * checkpoints and restores a context's propagators bit for bit. h_squarings (nclasses values,
  * or NULL) is only recorded. Marks the context built. Errors: LEM_EINVAL, LEM_ECUDA. */
 lem_status lem_set_propagators(lem_ctx* ctx, const double* h_P, const int* h_squarings);
 
+/* Class of tile `tile` (row-major over the tile grid) or -1 on a bad index. */
 int64_t lem_tile_class(const lem_ctx* ctx, int64_t tile);
 
 /* Squaring count s used for class `cls` (-1 before the build or on a bad index). */
 int lem_class_squarings(const lem_ctx* ctx, int64_t cls);
 
+/* Fill *out with the context's plan facts (lem_info). Errors: LEM_EINVAL (NULL argument). */
 lem_status lem_get_info(const lem_ctx* ctx, lem_info* out);
 
 /* Host-only planning query (no device is touched): validates `desc` and reports the
@@ -226,6 +230,8 @@ lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
  * until the process exits; no call allocates or frees memory.
  * - Needs built propagators (lem_build_propagators first: LEM_ENOTREADY otherwise) and
  *   no Jacobian refresh (reaction with refresh > 0: LEM_EINVAL), since building allocates.
+ * - Real problems with the exponential Euler scheme only; the porous-medium problem
+ *   (reaction 2) is refused (LEM_EINVAL).
  * - Problems whose scratch, npts + ntiles*(n_loc + n_int) doubles (each part rounded up to
  *   32), exceeds 8 MiB are rejected with LEM_EINVAL and a message giving both sizes.
  * - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
@@ -240,6 +246,9 @@ lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int nsteps);
 /* Synchronise the context stream and return any deferred device error. */
 lem_status lem_sync(lem_ctx* ctx);
 
+/* Synchronise the context stream and free everything the context holds (device memory,
+ * events, the split path's packed operands). NULL is a no-op. The caller's state buffers
+ * and stream are not touched. */
 void lem_destroy(lem_ctx* ctx);
 
 /* ------------------------------------------------------------------ batching
@@ -247,8 +256,9 @@ void lem_destroy(lem_ctx* ctx);
  * `steps_per_launch` LEM steps. At creation every context is built and warmed up on a copy
  * of its state and its step time is measured; the schedule (lem_batch_info) is then picked
  * by timing the candidates. The states d_states[i] (device, FP64) are captured: each launch
- * advances them in place. Contexts with a Jacobian refresh (reaction with refresh > 0) are rejected, because
- * rebuilding propagators cannot be captured. The contexts' streams are used only outside the
+ * advances them in place. Contexts with a Jacobian refresh (reaction with refresh > 0) are
+ * rejected, because rebuilding propagators cannot be captured; so are complex contexts and the
+ * porous-medium problem (step those with lem_step). The contexts' streams are used only outside the
  * graph; the graph runs on `stream`. The paper has no batching layer (its local problems are
  * independent, Sec. 3). Errors: LEM_EINVAL, LEM_ENOMEM, LEM_ECUDA. */
 typedef struct lem_batch lem_batch;
@@ -319,8 +329,10 @@ lem_status lem_server_create(size_t hbm_budget_bytes, int device, lem_server** o
 
 /* Queue a request to advance the host state h_state (FP64, row-major, in/out; it must stay
  * valid and untouched until the request is done) by nsteps LEM steps of the problem `desc`
- * (copied) within relative tolerance tier `tol`. Returns at once with a ticket.
- * Errors: LEM_EINVAL (descriptor, nsteps < 0, NULL pointers), LEM_EBUSY (server stopping). */
+ * (copied) within relative tolerance tier `tol`. Returns at once with a ticket. Real problems
+ * only, without the porous-medium nonlinearity (reaction 2).
+ * Errors: LEM_EINVAL (descriptor, complex or porous-medium problem, nsteps < 0, NULL pointers),
+ * LEM_EBUSY (server stopping). */
 lem_status lem_submit(lem_server* srv, const lem_problem_desc* desc, double tol, double* h_state,
                       int nsteps, uint64_t* ticket);
 
