@@ -73,7 +73,8 @@ def _fp(x) -> np.ndarray:
 
 def pade13_coefficients(m: int = PADE_DEGREE) -> list[float]:
     """Coefficients b_j of the numerator p_m(x) = sum_j b_j x^j of the [m/m] Pade
-    approximant to e^x; the denominator is p_m(-x).
+    approximant to e^x; the denominator is p_m(-x). (Sec. 1 and Sec. 4 name Pade
+    approximation with scaling and squaring; m = 13 follows Higham 2005.)
 
     b_j = (2m - j)! m! / ((2m)! j! (m - j)!), computed exactly as rationals then rounded.
     """
@@ -85,7 +86,8 @@ _B = pade13_coefficients()
 
 
 def squaring_count(norm1: float) -> int:
-    """Smallest s >= 0 with norm1 / 2^s <= theta_13 (exact 1-norm, no estimate)."""
+    """Smallest s >= 0 with norm1 / 2^s <= theta_13 (exact 1-norm, no estimate): the scaling
+    step of the scaling-and-squaring method named in Sec. 1 and Sec. 4 (Higham 2005's rule)."""
     s = 0
     while norm1 > THETA13 * (2.0 ** s):
         s += 1
@@ -93,7 +95,8 @@ def squaring_count(norm1: float) -> int:
 
 
 def expm_pade13(X: np.ndarray) -> np.ndarray:
-    """exp(X) by degree-13 Pade approximation with scaling and squaring.
+    """exp(X) by degree-13 Pade approximation with scaling and squaring (the method Sec. 1
+    and Sec. 4 name for the local matrix exponentials; Higham 2005's degree and theta).
 
     1. s from the exact 1-norm (``squaring_count``); 2. scale X by 2^-s;
     3. U (odd part) and V (even part) of p_13 from X^2, X^4, X^6;
@@ -119,7 +122,8 @@ def expm_pade13(X: np.ndarray) -> np.ndarray:
 
 
 def phi1(X: np.ndarray) -> np.ndarray:
-    """phi_1(X) = sum_k X^k / (k+1)!: the top-right block of exp([[X, I], [0, 0]])."""
+    """phi_1(X) = sum_k X^k / (k+1)! (Sec. 2, phi_k with k = 1; the matrix function of Eq. lem):
+    the top-right block of exp([[X, I], [0, 0]])."""
     X = _fp(X)
     n = X.shape[0]
     Z = np.zeros((2 * n, 2 * n), dtype=X.dtype)
@@ -144,6 +148,7 @@ def phik(X: np.ndarray, k: int) -> np.ndarray:
 
 # --------------------------------------------------------------------------- operator
 def _as_field(v, shape):
+    """A stencil coefficient of Eq. spacedisc as a field over the mesh (scalars broadcast)."""
     a = _fp(v)
     return np.broadcast_to(a, shape) if a.ndim == 0 else a.reshape(shape)
 
@@ -198,6 +203,8 @@ class Window:
 
 
 def _axis_ranges(n: int, tile: int, H: int, periodic: bool):
+    """Along one axis: each tile's owner nodes and its window, the tile dilated by H per side
+    (Sec. 3, Fig. 3), clipped at a wall or wrapped on a periodic axis."""
     out = []
     for t0 in range(0, n, tile):
         t1 = min(t0 + tile, n)  # the last tile may be ragged
@@ -296,7 +303,8 @@ def residual(Xg: sp.csr_matrix, u: np.ndarray, dt: float = 0.0, reaction: bool =
 
 def jacobian(Xg: sp.csr_matrix, u: np.ndarray, dt: float, reaction: bool,
              porous_m: float = 0.0) -> sp.csr_matrix:
-    """dt * F'(u) = X + dt * diag(1 - 3 u^2) (just X for a linear problem).
+    """dt * F'(u) = X + dt * diag(1 - 3 u^2) (just X for a linear problem): the Jacobian of the
+    exponential Euler-Rosenbrock step (Sec. 4).
     Porous medium: dt * F'(u) = X diag(phi'(u)), phi'(u) = m |u|^(m-1) (chain rule through
     the operator: column j of X scaled by phi'(u_j))."""
     if porous_m:
@@ -348,7 +356,7 @@ def lem_run(Xg, u0, windows, nsteps: int, mode: str = "phi", dt: float = 0.0,
 
 
 def rb3_defect(u, U, um, dt: float):
-    """dt (G(U) - G(u)) with G(v) = F(v) - J(u_m) v, the part of F(v) = A v + v - v^3 that the
+    """dt (G(U) - G(u)) with G(v) = F(v) - J(u_m) v (the exprb32 defect; Sec. 4.2), the part of F(v) = A v + v - v^3 that the
     frozen Jacobian J(u_m) = A + diag(1 - 3 u_m^2) leaves out. The linear parts cancel, so
     the defect is pointwise: dt [(U - U^3) - (u - u^3) - (1 - 3 u_m^2)(U - u)]."""
     return dt * ((U - U ** 3) - (u - u ** 3) - (1.0 - 3.0 * um ** 2) * (U - u))
@@ -369,8 +377,9 @@ def lem_step_rb3(Xg, u, windows, props1, props3, dt: float, um):
 
 
 def lem_run_rb3(Xg, u0, windows, nsteps: int, dt: float, refresh: int = 0):
-    """nsteps exprb32 LEM steps; the Jacobian (and both propagator sets) are rebuilt from
-    the current state every ``refresh`` steps (0 = only at the first step)."""
+    """nsteps exprb32 LEM steps (Sec. 4.2's third-order exponential Rosenbrock method in the
+    form of Eq. lem); the Jacobian (and both propagator sets) are rebuilt from the current
+    state every ``refresh`` steps (0 = only at the first step)."""
     u = _fp(u0).copy()
     props1 = props3 = um = None
     for n in range(nsteps):
@@ -395,6 +404,9 @@ def global_step(Xg, u, dt: float = 0.0, reaction: bool = False, J=None, porous_m
 
 def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, refresh: int = 0,
                porous_m: float = 0.0):
+    """nsteps global steps: exp(X)^nsteps u0 for a linear problem (Sec. 2 identity), else the
+    exponential Euler-Rosenbrock step with the Jacobian refreshed every ``refresh`` steps
+    (Sec. 4)."""
     u = _fp(u0).copy()
     if not reaction and not porous_m:
         E = expm_pade13(Xg.toarray())
@@ -410,13 +422,15 @@ def global_run(Xg, u0, nsteps: int, dt: float = 0.0, reaction: bool = False, ref
 
 
 def global_step_rb3(Xg, u, dt: float, um):
-    """exprb32 on the whole mesh with dense phi_1 and phi_3 of dt J(u_m) (small N only)."""
+    """exprb32 on the whole mesh with dense phi_1 and phi_3 of dt J(u_m) (small N only): the
+    global third-order exponential Rosenbrock step of Sec. 4.2 that the LEM form approximates."""
     Jd = jacobian(Xg, um, dt, True).toarray()
     U = u + phi1(Jd) @ residual(Xg, u, dt, True)
     return U + 2.0 * (phik(Jd, 3) @ rb3_defect(u, U, um, dt))
 
 
 def global_run_rb3(Xg, u0, nsteps: int, dt: float, refresh: int = 0):
+    """nsteps global exprb32 steps (Sec. 4.2), u_m refreshed every ``refresh`` steps."""
     u = _fp(u0).copy()
     um = None
     for n in range(nsteps):
@@ -428,14 +442,15 @@ def global_run_rb3(Xg, u0, nsteps: int, dt: float, refresh: int = 0):
 
 def heat1d_eigenvalues(n: int, mu: float) -> np.ndarray:
     """Eigenvalues lambda_k = -4 mu sin^2(pi k / (2(n+1))), k = 1..n, of
-    mu * tridiag(1, -2, 1) with homogeneous Dirichlet walls (eigenvectors sin(pi j k/(n+1)))."""
+    mu * tridiag(1, -2, 1) with homogeneous Dirichlet walls (eigenvectors sin(pi j k/(n+1))):
+    the closed form of the global step (Sec. 2) for the 1D heat equation."""
     k = np.arange(1, n + 1)
     return -4.0 * mu * np.sin(np.pi * k / (2.0 * (n + 1))) ** 2
 
 
 def heat1d_dst_modes(n: int, mu: float, amps: dict, nsteps: int) -> np.ndarray:
-    """Exact global solution after ``nsteps`` steps for u0 = sum_k a_k sin(pi k j/(n+1)),
-    j = 1..n: every sine mode decays by exp(lambda_k) per step."""
+    """Exact global solution after ``nsteps`` steps (Sec. 2 identity) for
+    u0 = sum_k a_k sin(pi k j/(n+1)), j = 1..n: every sine mode decays by exp(lambda_k) per step."""
     lam = heat1d_eigenvalues(n, mu)
     j = np.arange(1, n + 1)
     u = np.zeros(n)
@@ -445,7 +460,7 @@ def heat1d_dst_modes(n: int, mu: float, amps: dict, nsteps: int) -> np.ndarray:
 
 
 def periodic2d_symbol(shape, coef) -> np.ndarray:
-    """Fourier symbol of a constant dt-scaled 5-point stencil on a periodic mesh:
+    """Fourier symbol of a constant dt-scaled 5-point stencil (Eq. spacedisc) on a periodic mesh:
     lambda(tx, ty) = C + W e^{-i tx} + E e^{i tx} + S e^{-i ty} + N e^{i ty}."""
     ny, nx = shape
     tx = 2 * np.pi * np.fft.fftfreq(nx)[None, :]
@@ -455,8 +470,8 @@ def periodic2d_symbol(shape, coef) -> np.ndarray:
 
 
 def periodic2d_fft_step(u2d: np.ndarray, coef_dt: dict, nsteps: int = 1) -> np.ndarray:
-    """Exact global step(s) exp(nsteps X) u for a constant-coefficient periodic 2D stencil
-    (X is circulant, so the 2D DFT diagonalises it)."""
+    """Exact global step(s) exp(nsteps X) u (Sec. 2) for a constant-coefficient periodic 2D
+    stencil (X is circulant, so the 2D DFT diagonalises it)."""
     lam = periodic2d_symbol(u2d.shape, coef_dt)
     return np.real(np.fft.ifft2(np.fft.fft2(u2d) * np.exp(nsteps * lam)))
 
@@ -471,7 +486,7 @@ def barenblatt1d(x: np.ndarray, t: float, m: float, A: float) -> np.ndarray:
 
 
 def rel_l2(a, b) -> float:
-    """||a - b||_2 / ||b||_2."""
+    """||a - b||_2 / ||b||_2: the relative error the paper reports (Sec. 4), in the L2 norm."""
     a = _fp(a).ravel()
     b = _fp(b).ravel()
     nb = np.linalg.norm(b)
