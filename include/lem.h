@@ -30,6 +30,9 @@
  * - Errors: every call returns a lem_status; nothing is thrown across the ABI.
  *   lem_last_error() returns a thread-local message for the last failure.
  *   A context is not re-entrant: calls on one context must not overlap.
+ * - Entry points that implement a passage of the paper cite it. The rest have no counterpart
+ *   there and say what they serve: status and error strings, plan queries, propagator
+ *   checkpoints, timing, synchronisation, batching and serving.
  */
 #ifndef LEM_H
 #define LEM_H
