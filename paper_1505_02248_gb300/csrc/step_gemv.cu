@@ -191,38 +191,38 @@ __global__ void __launch_bounds__(256) gemv_tiles_kernel(const PT* __restrict__ 
         u[2 * p + 1] = accumulate ? u[2 * p + 1] + yi : yi;
       }
     }
-    return;
-  }
-  // every lane runs the same number of row iterations (the shuffles need the whole warp)
-  for (int i0 = ib + warp * 4; i0 < ie; i0 += nw * 4) {
-    const int i = i0 + grp;
-    const bool live = i < ie;
-    const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
-    Acc acc;
-    if (vec) {
-      const int nv = wl / V;
-      const int4* r4 = reinterpret_cast<const int4*>(row);
-      for (int j = gl; j < nv; j += 8 * U) {
-        int4 q[U];
-#pragma unroll
-        for (int k = 0; k < U; ++k) q[k] = (live && j + 8 * k < nv) ? __ldcs(r4 + j + 8 * k) : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int k = 0; k < U; ++k) {
-          if (j + 8 * k >= nv) break;
-          const PT* pq = reinterpret_cast<const PT*>(&q[k]);
-          const int4 wq = *reinterpret_cast<const int4*>(w + (j + 8 * k) * V);  // same 16 bytes of w
-          const PT* pw = reinterpret_cast<const PT*>(&wq);
-#pragma unroll
-          for (int h = 0; h < V; ++h) acc.add(pq[h], pw[h]);
+  } else {
+    // every lane runs the same number of row iterations (the shuffles need the whole warp)
+    for (int i0 = ib + warp * 4; i0 < ie; i0 += nw * 4) {
+      const int i = i0 + grp;
+      const bool live = i < ie;
+      const PT* row = Pt + int64_t(live ? i : 0) * n_loc;
+      Acc acc;
+      if (vec) {
+        const int nv = wl / V;
+        const int4* r4 = reinterpret_cast<const int4*>(row);
+        for (int j = gl; j < nv; j += 8 * U) {
+          int4 q[U];
+  #pragma unroll
+          for (int k = 0; k < U; ++k) q[k] = (live && j + 8 * k < nv) ? __ldcs(r4 + j + 8 * k) : make_int4(0, 0, 0, 0);
+  #pragma unroll
+          for (int k = 0; k < U; ++k) {
+            if (j + 8 * k >= nv) break;
+            const PT* pq = reinterpret_cast<const PT*>(&q[k]);
+            const int4 wq = *reinterpret_cast<const int4*>(w + (j + 8 * k) * V);  // same 16 bytes of w
+            const PT* pw = reinterpret_cast<const PT*>(&wq);
+  #pragma unroll
+            for (int h = 0; h < V; ++h) acc.add(pq[h], pw[h]);
+          }
         }
+      } else if (live) {
+        for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
       }
-    } else if (live) {
-      for (int k = gl; k < wl; k += 8) acc.add(row[k], w[k]);
-    }
-    const double y = group_reduce(acc);
-    if (live && gl == 0) {
-      const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
-      u[p] = accumulate ? u[p] + y : y;
+      const double y = group_reduce(acc);
+      if (live && gl == 0) {
+        const int64_t p = int64_t(td.t0[0] + i / td.iext[1]) * nx + td.t0[1] + i % td.iext[1];
+        u[p] = accumulate ? u[p] + y : y;
+      }
     }
   }
 }
