@@ -6,7 +6,14 @@ One bench step = one lem_step call advancing the state by --inner LEM time steps
 residual, the halo gather inside TMA, the propagator apply and the owner scatter for all
 4096 tiles, every LEM step). Prints ONE JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|split_fast|fp64]
+                  [--impl reference] [--workload advdiff2d|batch512|serve|heat1d|vardiff2d|
+                  schrodinger1d]
+
+--workload picks another configuration: batch512 (512 uneven problems under one CUDA graph),
+serve (a Poisson stream of requests through the server), heat1d (1D heat, persistent GEMV),
+vardiff2d (per-tile propagators with the u - u^3 reaction, batched GEMV; --scheme rb3 for the
+third-order scheme) and schrodinger1d (the complex Schroedinger test; --sn sets the mesh).
 
 Metric: LEM dof-steps/s = owner nodes x LEM steps / device time. L2 is flushed (256 MiB
 write) between timed calls; each call is bracketed by CUDA events on the context stream.
