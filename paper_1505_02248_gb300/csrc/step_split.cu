@@ -81,7 +81,6 @@ struct GemmGeom {
   int M;                // owner rows (Ty * Tx); M blocks past it are masked
   int nbx;              // window blocks per row of the tile grid
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
-  int bsplit_y;         // clustered: a window block's two halves split along y (else x)
   int drain_rows;       // three pieces: window rows per correction drain
   int unit0;            // multi-problem launch: this problem's first unit
   int fault;            // test hook (LEM_FAULT=timeout): CTA 0 arms its first stage but loads
@@ -427,31 +426,26 @@ __global__ void choose_rb_kernel(const double* __restrict__ S, int M, int* rb, i
   }
 }
 
-// Persistent GEMM. MC = false: each CTA walks output units u = blockIdx.x, + gridDim.x, ...
+// Persistent GEMM: each CTA walks output units u = blockIdx.x, + gridDim.x, ...
 // A unit is one (M block, window block) tile of one problem: of the single problem `one`
 // (M block u % nMB, window block u / nMB), or, when `many` is given, of the problem whose
 // unit range holds u (a multi-problem launch: every problem of a batch advances by one step
-// in one launch). MC = true (single problem only): clusters of 4 CTAs walk 2 x 2 groups of
-// tiles; the two CTAs on the same M block each load half of its P rows and multicast them to
-// both, and the two on the same window block each load half of the windows and multicast
-// them, so every CTA issues half the TMA rows. A stage is reused only after all three CTAs
-// that write into it (self, P partner, window partner) released it. Two TMEM accumulator sets
-// alternate between tiles, so the epilogue of one tile overlaps the MMAs of the next.
-template <bool MC, int BN, int NP, bool MULTI>
+// in one launch). Two TMEM accumulator sets alternate between tiles, so the epilogue of one
+// tile overlaps the MMAs of the next.
+template <int BN, int NP, bool MULTI>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ SplitProblem one, const SplitProblem* __restrict__ many, int nprob,
                       int nunits_many, int parity, int* err) {
-  static_assert(!(MC && MULTI), "clusters pair the tiles of one problem");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = Shape<BN, NP>::STAGES, STAGE_BYTES = Shape<BN, NP>::STAGE_BYTES;
   constexpr int B_BYTES = Shape<BN, NP>::B_BYTES, NBUF = Shape<BN, NP>::NBUF;
   constexpr int R_OFF = NP * A_BYTES;  // r pieces follow the P pieces in a stage
-  // [stage][P_int, P2, (P3) (A_BYTES each), r_int, r2, (r3) (B_BYTES each)], same offsets in every CTA
+  // [stage][P_int, P2, (P3) (A_BYTES each), r_int, r2, (r3) (B_BYTES each)]
   uint8_t* tiles = smem;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
   uint64_t* full = bars;                 // [STAGES] stage loaded
-  uint64_t* empty = bars + STAGES;       // [STAGES] stage released by every CTA writing into it
+  uint64_t* empty = bars + STAGES;       // [STAGES] stage released by the MMA issuer
   constexpr bool DRAIN = NP == 3;
   static_assert(!DRAIN || BN == 128, "drained correction: main[2] + corr[2] of 128 columns fill TMEM");
   uint64_t* accf = bars + 2 * STAGES;    // [2] accumulator set (main) ready (DRAIN: [0] only)
@@ -462,12 +456,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t rank = MC ? ptx::cluster_ctarank() : 0u;
-  const int mh = int(rank & 1u), nh = int(rank >> 1);  // MC: place in the 2 x 2 tile group
-  const int unit0 = MC ? int(ptx::cluster_id_x()) : int(blockIdx.x);
-  const int nunit_step = MC ? int(ptx::nclusters_x()) : int(gridDim.x);
-  const int nMBu = MC ? one.g.nMB / 2 : one.g.nMB;
-  const int nunits = MC ? nMBu * (one.g.nNB / 2) : (MULTI ? nunits_many : one.g.nMB * one.g.nNB);
+  const int unit0 = int(blockIdx.x);
+  const int nunit_step = int(gridDim.x);
+  const int nunits = MULTI ? nunits_many : one.g.nMB * one.g.nNB;
   // unit -> problem and its tile (one problem: the by-value parameter, addressed statically)
   auto locate = [&](int u, int& lu) -> const SplitProblem* {
     if constexpr (!MULTI) {
@@ -484,9 +475,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     return many + lo;
   };
   auto tile_of = [&](const GemmGeom& g, int lu, int& m0, int& tx0, int& ty0) {
-    const int nmb = MC ? nMBu : g.nMB;
-    const int mb = MC ? 2 * (lu % nmb) + nh : lu % nmb;
-    const int nb = MC ? 2 * (lu / nmb) + mh : lu / nmb;
+    const int mb = lu % g.nMB;
+    const int nb = lu / g.nMB;
     m0 = mb * BM;
     tx0 = (nb % g.nbx) * g.BNx;
     ty0 = (nb / g.nbx) * g.BNy;
@@ -501,15 +491,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     return true;
   };
   const int64_t cur0 = int64_t(unit0);
-  // MC multicast masks: P partner shares the M block (differs in mh), window partner the
-  // window block (differs in nh)
-  const uint16_t maskP = uint16_t((1u << rank) | (1u << (rank ^ 1u)));
-  const uint16_t maskR = uint16_t((1u << rank) | (1u << (rank ^ 2u)));
-  const uint16_t maskE = uint16_t(maskP | maskR);
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < STAGES; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], MC ? 3 : 1); }
+    for (int s = 0; s < STAGES; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(&accf[b], 1);
       ptx::mbar_init(&acce[b], EPI_WARPS);
@@ -535,8 +520,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
-  if (MC) ptx::cluster_sync();  // peers' barriers exist before any multicast reaches them
-  else __syncthreads();
+  __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -568,24 +552,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             issued = it + 1;
             continue;
           }
-          if (MC) {
-            // my half of the P rows (to me and the P partner), my half of the windows (to me
-            // and the window partner); the partners send the other halves
-            const int wx = g.bsplit_y ? tx0 : tx0 + nh * (g.BNx / 2);
-            const int wy = g.bsplit_y ? ty0 + nh * (g.BNy / 2) : ty0;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              ptx::tma_load_2d_mc(st + q * A_BYTES + mh * (A_BYTES / 2), &pr->tm[q], &full[s], kb * KB,
-                                  m0 + mh * (BM / 2), maskP);
-              ptx::tma_load_4d_mc(st + R_OFF + q * B_BYTES + nh * (B_BYTES / 2), &pr->tm[3 + q], &full[s], 0, wx,
-                                  kb, wy, maskR);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              ptx::tma_load_2d(st + q * A_BYTES, &pr->tm[q], &full[s], kb * KB, m0);
-              ptx::tma_load_4d(st + R_OFF + q * B_BYTES, &pr->tm[3 + q], &full[s], 0, tx0, kb, ty0);
-            }
+          for (int q = 0; q < NP; ++q) {
+            ptx::tma_load_2d(st + q * A_BYTES, &pr->tm[q], &full[s], kb * KB, m0);
+            ptx::tma_load_4d(st + R_OFF + q * B_BYTES, &pr->tm[3 + q], &full[s], 0, tx0, kb, ty0);
           }
           issued = it + 1;
         }
@@ -652,8 +622,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               ptx::mma_f16(corr, dP3 + adv, dRi + adv, idesc, 1u);
             }
           }
-          if (MC) ptx::mma_commit_mc(&empty[s], maskE);
-          else ptx::mma_commit(&empty[s]);
+          ptx::mma_commit(&empty[s]);
           if (group_last) {
             ptx::mma_commit(&cf[kc % 3]);
             ++kc;
@@ -664,11 +633,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       if (!ok) {
         atomicExch(err, ERR_TIMEOUT_MMA);
         s_abort = 1;
-      }
-      if (MC) {
-        // the partners' releases of my last stages have arrived before the cluster may exit
-        for (int k = (it > STAGES ? it - STAGES : 0); k < it; ++k)
-          ptx::mbar_wait(&empty[k % STAGES], (k / STAGES) & 1, WAIT_NS);
       }
     }
   } else {
@@ -812,34 +776,31 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, TMEM_COLS);
   }
-  if (MC) ptx::cluster_sync();  // no CTA leaves while a partner may still signal it
 }
 
 using GemmKernel = void (*)(SplitProblem, const SplitProblem*, int, int, int, int*);
 
 int gemm_threads(int) { return GEMM_THREADS; }
 
-// The instantiated (cluster, tile width, pieces) combinations: BN 256 with two pieces for
-// large tile grids, BN 128 otherwise.
-GemmKernel gemm_kernel_for(bool mc, int bn, int np, bool multi = false) {
+// The instantiated (tile width, pieces) combinations: BN 256 with two pieces for large tile
+// grids, BN 128 otherwise.
+GemmKernel gemm_kernel_for(int bn, int np, bool multi = false) {
   if (multi) {
-    if (np == 3) return split_gemm_kernel<false, 128, 3, true>;
-    return bn == 256 ? split_gemm_kernel<false, 256, 2, true> : split_gemm_kernel<false, 128, 2, true>;
+    if (np == 3) return split_gemm_kernel<128, 3, true>;
+    return bn == 256 ? split_gemm_kernel<256, 2, true> : split_gemm_kernel<128, 2, true>;
   }
-  if (np == 3) return mc ? split_gemm_kernel<true, 128, 3, false> : split_gemm_kernel<false, 128, 3, false>;
-  if (bn == 256) return mc ? split_gemm_kernel<true, 256, 2, false> : split_gemm_kernel<false, 256, 2, false>;
-  return mc ? split_gemm_kernel<true, 128, 2, false> : split_gemm_kernel<false, 128, 2, false>;
+  if (np == 3) return split_gemm_kernel<128, 3, false>;
+  return bn == 256 ? split_gemm_kernel<256, 2, false> : split_gemm_kernel<128, 2, false>;
 }
 
 }  // namespace
 
 struct SplitPlan {
   int Ty = 0, Tx = 0, Hy = 0, Hx = 0, Wy = 0, Wx = 0, nty = 0, ntx = 0, M = 0, BNx = 0, BNy = 0;
-  int pitch = 0, prow = 0, nsm = 0, bsplit_y = 0;
+  int pitch = 0, prow = 0, nsm = 0;
   int np = 2;        // FP16 pieces per operand: 2 (four products) or 3 (six products)
   int bn = 128;      // windows per CTA tile (256 for large tile grids with two pieces)
   int nbx = 0, nby = 0;  // window blocks per grid row / column (the last ones may overhang)
-  int clusters = 0;  // > 0: the multicast (2 x 2 cluster) kernel runs with this many clusters
   ResParams rp{};
   float* d_uh = nullptr;
   float* d_ul = nullptr;
@@ -855,8 +816,7 @@ struct SplitPlan {
   int* d_escale = nullptr;
   int* d_err = nullptr;
   int* d_rb = nullptr;
-  SplitProblem prob{};       // tensor maps (half boxes when clustered) and GEMM geometry
-  SplitProblem prob_flat{};  // the same with whole boxes, for launches without clusters
+  SplitProblem prob{};  // tensor maps and GEMM geometry
   int packed_gen = -1;
 };
 
@@ -990,57 +950,23 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_R2, 0, rbytes));
   LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
-  // Clustered (multicast) kernel when the tile grid splits into 2 x 2 groups and the device
-  // can co-schedule clusters of 4 one-CTA-per-SM blocks.
-  const int nMB = (sp->M + BM - 1) / BM, nNB = sp->nbx * sp->nby;
-  const bool bsplit_y = sp->BNy % 2 == 0;
-  // (two pieces only: with three, the per-row correction drain dominates and clusters measured
-  // about 3 % slower on 2048^2: 138 us against 134 us per launch)
-  const bool mc_ok = sp->np == 2 && nMB % 2 == 0 && nNB % 2 == 0 &&
-                     (bsplit_y || (sp->BNy == 1 && sp->BNx % 2 == 0)) && std::getenv("LEM_SPLIT_NO_CLUSTER") == nullptr;
-  sp->bsplit_y = bsplit_y ? 1 : 0;
-  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(false, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES));
-  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(true, sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    SMEM_BYTES));
-  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(false, sp->bn, sp->np, true),
+  LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(sp->bn, sp->np, true),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  sp->clusters = 0;
-  if (mc_ok) {
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 4; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(4 * ((nMB / 2) * (nNB / 2)));
-    cfg.blockDim = dim3(gemm_threads(sp->np));
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclus = 0;
-    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclus, gemm_kernel_for(true, sp->bn, sp->np), &cfg);
-    if (e == cudaSuccess && nclus > 0) sp->clusters = std::min(nclus, (nMB / 2) * (nNB / 2));
-    cudaGetLastError();
-  }
   // tensor maps: P slices [M][Wy*64] fp16 (2D, box 64 x rows); residual slices through a 4D
   // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx]
-  for (int variant = 0; variant < 2; ++variant) {
-    // variant 0: the maps the single-problem launch uses (half boxes when clustered);
-    // variant 1: whole boxes, for multi-problem launches (never clustered)
-    const bool mc = variant == 0 && sp->clusters > 0;
-    SplitProblem& pr = variant == 0 ? sp->prob : sp->prob_flat;
+  {
+    SplitProblem& pr = sp->prob;
     // with two pieces the third maps alias the second (never loaded)
     __half* pbase[3] = {sp->d_Pint, sp->d_P2, sp->np == 3 ? sp->d_P3 : sp->d_P2};
     __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
     cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(Mpad)};
     cuuint64_t ps[1] = {cuuint64_t(sp->Wy) * KB * 2};
-    cuuint32_t pbox[2] = {KB, cuuint32_t(mc ? BM / 2 : BM)};
+    cuuint32_t pbox[2] = {KB, cuuint32_t(BM)};
     cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
     cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
     cuuint32_t rbox[4] = {KB, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
-    if (mc) {
-      if (bsplit_y) rbox[3] /= 2;
-      else rbox[1] /= 2;
-    }
     for (int k = 0; k < 3; ++k) {
       LEM_TRY(encode_f16_map(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
       LEM_TRY(encode_f16_map(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
@@ -1049,7 +975,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   GemmGeom& g = sp->prob.g;
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx; g.nty = sp->nty; g.M = sp->M;
-  g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bsplit_y = sp->bsplit_y;
+  g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby;
   // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
   // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
   g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
@@ -1060,9 +986,8 @@ lem_status split_prepare(lem_ctx* ctx) {
     g.fault = f && std::strcmp(f, "timeout") == 0;
   }
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
-  sp->prob_flat.g = g;
   cudaFuncAttributes fa{};
-  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(false, sp->bn, sp->np)));
+  LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(sp->bn, sp->np)));
   if (fa.maxThreadsPerBlock < gemm_threads(sp->np))
     return fail(LEM_ECUDA, "split GEMM kernel cannot launch " + std::to_string(gemm_threads(sp->np)) + " threads (" +
                                std::to_string(fa.numRegs) + " registers per thread)");
@@ -1098,26 +1023,17 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
   LEM_CUDA_TRY(cudaGetLastError());
   const GemmGeom& g = sp->prob.g;
   cudaLaunchConfig_t cfg{};
-  cudaLaunchAttribute attr[1];
   cfg.blockDim = dim3(gemm_threads(sp->np));
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
-  if (sp->clusters > 0) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 4; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(4 * sp->clusters);
-  } else {
-    cfg.gridDim = dim3(std::min(g.nMB * g.nNB, sp->nsm));
-  }
+  cfg.gridDim = dim3(std::min(g.nMB * g.nNB, sp->nsm));
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
     residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
                                                  sp->d_rmax, sp->d_escale, parity, 0);
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->clusters > 0, sp->bn, sp->np), sp->prob,
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->bn, sp->np), sp->prob,
                                     static_cast<const SplitProblem*>(nullptr), 1, 0, parity, sp->d_err));
     ctx->timing_end(stop);
   }
@@ -1181,7 +1097,7 @@ lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, in
   for (int k = 0; k < n; ++k) {
     const lem_ctx* c = ctxs[order[k]];
     const SplitPlan* sp = c->split;
-    probs[k] = sp->prob_flat;
+    probs[k] = sp->prob;
     probs[k].g.unit0 = b->nunits;
     b->nunits += sp->prob.g.nMB * sp->prob.g.nNB;
     ResProblem& r = res[k];
@@ -1237,7 +1153,7 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
     const int parity = k & 1;
     residual_multi_kernel<<<b->res_blocks, 256, 0, st>>>(b->d_res, b->d_res_first, b->n, parity, 0);
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[1 + 2 * k], st));
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(false, b->bn, b->np, true), b->first,
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(b->bn, b->np, true), b->first,
                                     static_cast<const SplitProblem*>(b->d_probs), b->n, b->nunits, parity, b->d_err));
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[2 + 2 * k], st));
   }
