@@ -226,20 +226,25 @@ lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
 
 /* Allocation-free FP64 step (the paper has no counterpart; this is a service to callers).
  * Same result as lem_step on an LEM_PREC_FP64 context, for callers that must not allocate
- * device memory while they step: code running under CUDA stream capture, runtimes that
- * own all device memory through their own pool, and loops that cannot take cudaMalloc's
- * implicit synchronisation. Its per-step scratch (residual, gathered windows and local
- * results) comes from one static 8 MiB device array that every GPU loading liblem.so holds
- * until the process exits; no call allocates or frees memory.
+ * device memory while they step: runtimes that own all device memory through their own
+ * pool and forbid later driver allocations, and loops that cannot take cudaMalloc's
+ * implicit synchronisation. Its per-step scratch comes from one static 8 MiB device array
+ * that every GPU loading liblem.so holds until the process exits; no call allocates or frees
+ * memory. The scratch is the residual, plus the gathered windows and local results on the
+ * GEMM apply path (apply_path LEM_APPLY_FP64_GEMM); contexts on the batched GEMV
+ * (LEM_APPLY_FP64_GEMV, many propagator classes) need the residual alone and run the same
+ * GEMV kernel as lem_step.
  * - Needs built propagators (lem_build_propagators first: LEM_ENOTREADY otherwise) and
  *   no Jacobian refresh (reaction with refresh > 0: LEM_EINVAL), since building allocates.
  * - Real problems with the exponential Euler scheme only; the porous-medium problem
  *   (reaction 2) is refused (LEM_EINVAL).
- * - Problems whose scratch, npts + ntiles*(n_loc + n_int) doubles (each part rounded up to
- *   32), exceeds 8 MiB are rejected with LEM_EINVAL and a message giving both sizes.
+ * - Problems whose scratch, npts (+ ntiles*(n_loc + n_int) on the GEMM path) doubles (each
+ *   part rounded up to 32), exceeds 8 MiB are rejected with LEM_EINVAL and a message giving
+ *   both sizes.
  * - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *   which may load the library's device code on that device); make that first call before
- *   any stream capture.
+ *   which may load the library's device code on that device) and keeps it for the life of
+ *   the process; make that first call before any stream capture. A device reset
+ *   (cudaDeviceReset) invalidates the kept address: do not call this entry point after one.
  * - Every call on a device shares the one array, which keeps the last call's contents
  *   (each step rewrites every element it reads, so nothing needs clearing). Calls whose
  *   work overlaps on the GPU (other streams, other contexts, other threads) race on it.

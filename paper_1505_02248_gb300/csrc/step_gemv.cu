@@ -433,6 +433,24 @@ lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool
   return LEM_OK;
 }
 
+// Threads per GEMV block: 128 for the complex FP32 kernel (short rows, little work per block,
+// more blocks resident per SM), 256 otherwise.
+static int gemv_threads(const lem_ctx* ctx, bool f32) { return (ctx->cplx && f32) ? 128 : 256; }
+
+// Blocks per tile: about four waves of blocks (6 to 8 resident per SM), at least 32 owner rows
+// per block, each block's share a whole number of passes (a pass: 4 rows per warp), so that no
+// pass runs part empty (512^2 variable diffusion: 4 blocks of 64 rows per tile, not 5 of 52).
+static int gemv_row_split(const lem_ctx* ctx, int threads) {
+  const int64_t nt = int64_t(ctx->tiles.size());
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm < 1) nsm = 152;
+  const int rmax = std::max<int>(1, int(ctx->n_int / 32));
+  int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
+  const int owners = int(ctx->cplx ? ctx->n_int / 2 : ctx->n_int), pass = threads / 8;
+  const int rows = ((owners + rsplit - 1) / rsplit + pass - 1) / pass * pass;
+  return std::max(1, (owners + rows - 1) / rows);
+}
+
 // One LEM step by the batched GEMV: PHI reads the residual, EXP a copy of u^n.
 lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   cudaStream_t st = ctx->stream;
@@ -452,19 +470,8 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
   if (f32 && ctx->p32_gen != ctx->build_gen) LEM_TRY(gemv_prepare_f32(ctx));
   const size_t smem = sizeof(double) * size_t(ctx->n_loc);
   const unsigned nt = unsigned(ctx->tiles.size());
-  // about four waves of blocks (6 to 8 resident per SM), at least 32 owner rows per block, each
-  // block's share a whole number of passes (a pass: 4 rows per warp), so that no pass runs
-  // part empty (512^2 variable diffusion: 4 blocks of 64 rows per tile, not 5 of 52)
-  int nsm = 0;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm < 1) nsm = 152;
-  const int rmax = std::max<int>(1, int(ctx->n_int / 32));
-  int rsplit = std::max(1, std::min<int>(rmax, int((4LL * 8 * nsm + nt - 1) / nt)));
-  const int threads = (ctx->cplx && f32) ? 128 : 256;
-  {
-    const int owners = int(ctx->cplx ? ctx->n_int / 2 : ctx->n_int), pass = threads / 8;
-    const int rows = ((owners + rsplit - 1) / rsplit + pass - 1) / pass * pass;
-    rsplit = std::max(1, (owners + rows - 1) / rows);
-  }
+  const int threads = gemv_threads(ctx, f32);
+  const int rsplit = gemv_row_split(ctx, threads);
   cudaEvent_t stop;
   LEM_CUDA_TRY(ctx->timing_begin(&stop));
   auto gemv = [&](const double* P64, const float* P32, const double* x) {
@@ -490,6 +497,27 @@ lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32) {
     gemv(ctx->d_P3, ctx->d_P3_32, ctx->d_r);
   }
   ctx->timing_end(stop);
+  LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
+// One FP64 GEMV step of a real exponential-Euler problem with caller-provided scratch r (npts
+// doubles): the kernels and launch shape of step_gemv, so the result is the same bit for bit.
+// Used by the allocation-free entry point.
+lem_status step_gemv_scratch(lem_ctx* ctx, double* d_u, double* r) {
+  cudaStream_t st = ctx->stream;
+  if (ctx->desc.mode == LEM_MODE_PHI) {
+    LEM_CUDA_TRY(launch_residual_fp64(ctx, r, d_u));
+  } else {
+    LEM_CUDA_TRY(cudaMemcpyAsync(r, d_u, sizeof(double) * ctx->npts, cudaMemcpyDeviceToDevice, st));
+  }
+  const size_t smem = sizeof(double) * size_t(ctx->n_loc);
+  const unsigned nt = unsigned(ctx->tiles.size());
+  const int threads = gemv_threads(ctx, false);
+  const int rsplit = gemv_row_split(ctx, threads);
+  const int acc = ctx->desc.mode == LEM_MODE_PHI ? 1 : 0;
+  gemv_tiles_kernel<double, false><<<nt * rsplit, threads, smem, st>>>(ctx->d_P, ctx->n_int, ctx->n_loc, ctx->d_tiles,
+                                                                       r, d_u, ctx->ny, ctx->nx, acc, rsplit);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
 }

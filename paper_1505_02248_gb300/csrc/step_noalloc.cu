@@ -1,11 +1,10 @@
 // Allocation-free FP64 LEM step (lem_step_fp64_noalloc).
 //
-// Some callers cannot call cudaMalloc while they advance a state: code that runs while a
-// CUDA stream is being captured into a graph (allocation is not a capturable operation),
-// runtimes that hand all device memory to their own pool at start-up and forbid later
-// driver allocations, and latency-critical loops that cannot afford cudaMalloc's implicit
-// device synchronisation. For them this entry point takes its per-step scratch (residual,
-// gathered windows, local results) from a fixed array in the library's static device
+// Some callers cannot call cudaMalloc while they advance a state: runtimes that hand all
+// device memory to their own pool at start-up and forbid later driver allocations, and
+// latency-critical loops that cannot afford cudaMalloc's implicit device synchronisation.
+// For them this entry point takes its per-step scratch (the residual, and on the GEMM path
+// the gathered windows and local results) from a fixed array in the library's static device
 // memory instead of allocating it. The array exists on every GPU that loads the library,
 // until the process exits.
 #include <cuda_runtime.h>
@@ -17,6 +16,7 @@
 
 namespace lem {
 lem_status step_fp64_scratch(lem_ctx* ctx, double* d_u, double* r, double* U, double* Y);
+lem_status step_gemv_scratch(lem_ctx* ctx, double* d_u, double* r);
 }
 
 namespace {
@@ -31,7 +31,9 @@ double* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (set up once per device).
 // In host code g_noalloc_scratch names a host-side shadow, not device memory, so the
-// kernels get the address that cudaGetSymbolAddress returns for the current device.
+// kernels get the address that cudaGetSymbolAddress returns for the current device. The
+// address is kept for the life of the process: a device reset (cudaDeviceReset) unloads the
+// module and makes it stale, so this entry point must not be used after one.
 lem_status scratch_address(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return lem::fail(LEM_EINVAL, "device index out of range");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -61,11 +63,13 @@ extern "C" lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int n
     return lem::fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators, which allocates; use refresh = 0");
   if (ctx->desc.reaction == 2)
     return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc does not take the porous-medium problem");
-  // scratch layout: r | U | Y, each start 256-byte aligned
+  // scratch layout: r | U | Y, each start 256-byte aligned. The batched GEMV (contexts with
+  // many propagator classes) reads the windows straight from r and needs r alone.
+  const bool gemv = ctx->apply_path == LEM_APPLY_FP64_GEMV;
   const int64_t nt = int64_t(ctx->tiles.size());
   const int64_t n_r = round_up(ctx->npts, 32);
-  const int64_t n_U = round_up(nt * ctx->n_loc, 32);
-  const int64_t n_Y = round_up(nt * ctx->n_int, 32);
+  const int64_t n_U = gemv ? 0 : round_up(nt * ctx->n_loc, 32);
+  const int64_t n_Y = gemv ? 0 : round_up(nt * ctx->n_int, 32);
   const int64_t need = n_r + n_U + n_Y;
   if (need > int64_t(kScratchDoubles))
     return lem::fail(LEM_EINVAL, "problem needs " + std::to_string(need * 8) + " bytes of step scratch; " +
@@ -81,7 +85,8 @@ extern "C" lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int n
   double* base = nullptr;
   lem_status s = scratch_address(ctx->device, &base);
   for (int k = 0; s == LEM_OK && k < nsteps; ++k)
-    s = lem::step_fp64_scratch(ctx, d_state, base, base + n_r, base + n_r + n_U);
+    s = gemv ? lem::step_gemv_scratch(ctx, d_state, base)
+             : lem::step_fp64_scratch(ctx, d_state, base, base + n_r, base + n_r + n_U);
   if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
   return s;
 }
