@@ -260,7 +260,9 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   c->build_tc = builder_uses_tc(desc->prec);
   const bool split_tier = desc->prec == LEM_PREC_SPLIT || desc->prec == LEM_PREC_SPLIT_FAST;
   if (desc->scheme == LEM_SCHEME_RB3 || c->cplx) {  // two propagator sets / complex: the batched GEMV
-    c->apply_path = desc->prec == LEM_PREC_SPLIT_FAST ? LEM_APPLY_F32_GEMV : LEM_APPLY_FP64_GEMV;
+    // (FP32 propagators in PHI mode only: in EXP mode they would round the whole state every step)
+    c->apply_path = desc->prec == LEM_PREC_SPLIT_FAST && desc->mode == LEM_MODE_PHI ? LEM_APPLY_F32_GEMV
+                                                                                   : LEM_APPLY_FP64_GEMV;
   } else if (split_tier && split_eligible(c)) {
     c->apply_path = LEM_APPLY_TC_SPLIT;
     s = split_prepare(c);
