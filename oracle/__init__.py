@@ -13,7 +13,8 @@ Modules
                  (Eq. lem, Sec. 3 steps 1-3), a third-order exponential Rosenbrock LEM step
                  (Sec. 4.2) and the global steps they approximate; real or complex inputs
                  (the Schroedinger test of Sec. 4.1); the porous-medium nonlinearity and its
-                 Barenblatt solution (Sec. 4.2).
+                 Barenblatt solution (Sec. 4.2); truncated propagators (the off-band decay
+                 of Sec. 2, Theorem 1).
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms, invariants,
 an independent library (scipy), arbitrary precision (mpmath) or brute force.

@@ -32,6 +32,16 @@ What is here, in the paper's order and notation (dt-scaled throughout, X = dt*A)
   2009): a phi_1 stage and a phi_3 correction, both applied window by window.
   ``global_step_rb3`` / ``global_run_rb3`` are the same scheme on the whole mesh.
 
+* ``window_offsets`` / ``truncation_extents`` / ``truncate_propagator`` -- truncated
+  propagators. Sec. 2 (Theorem 1, after Iserles) states that the entries of the exponential
+  of a banded matrix decay faster than exponentially away from the band; that decay is why
+  the local problems work at all. A truncated propagator keeps, for every owner row, only
+  the window nodes inside a box around the owner node (offsets -ly..hy along y, -lx..hx
+  along x in window coordinates) and zeroes the rest. Each side's extent is the smallest
+  whose dropped mass, max over rows of sum |P| beyond it, is at most tol/4 of the largest
+  row mass max_d sum_m |P_dm|; the four sides together then drop at most tol of it. The
+  tolerance rule is a reading: the paper gives no truncation rule.
+
 * ``porous_m`` (``residual``, ``jacobian``, the step and run functions) -- the porous-medium
   equation c_t = (c^m)_xx of Sec. 4.2 (Eq. porous): dt F(u) = X phi(u), dt F'(u) =
   X diag(phi'(u)) with phi(u) = |u|^(m-1) u; ``barenblatt1d`` its closed-form solution.
@@ -55,6 +65,7 @@ __all__ = [
     "jacobian", "lem_step", "lem_run", "global_step", "global_run",
     "rb3_defect", "lem_step_rb3", "lem_run_rb3", "global_step_rb3", "global_run_rb3",
     "porous_phi", "barenblatt1d", "heat1d_dst_modes", "heat1d_eigenvalues", "periodic2d_symbol", "periodic2d_fft_step",
+    "window_offsets", "truncation_extents", "truncate_propagator",
     "rel_l2",
 ]
 
@@ -280,6 +291,48 @@ def local_propagators(Xg: sp.csr_matrix, windows, mode: str = "phi", tiles=None)
             cache[key] = F[w.d_pos, :]
         out[i] = cache[key]
     return out
+
+
+# --------------------------------------------------------------------------- truncation
+def window_offsets(window: Window, shape):
+    """(oy, ox): for every owner row d and window node m, the offset of m from the owner node
+    d in window coordinates (window rows and columns, row-major order of M), each an
+    n_int x n_loc integer array. 1D problems have oy = 0."""
+    shape = tuple(int(s) for s in shape)
+    nloc = len(window.M)
+    if len(shape) == 1:
+        wx = nloc
+    else:
+        wx = len(np.unique(window.M % shape[1]))
+    k = np.arange(nloc)
+    cy, cx = k // wx, k % wx
+    dy, dx = cy[window.d_pos], cx[window.d_pos]
+    return cy[None, :] - dy[:, None], cx[None, :] - dx[:, None]
+
+
+def truncation_extents(P: np.ndarray, window: Window, shape, tol: float):
+    """(ly, hy, lx, hx): the box a truncated propagator keeps (Sec. 2, Theorem 1: off-band
+    decay). For each side, e.g. x below the owner, the smallest extent e >= 0 such that
+    max_d sum_{m : ox_dm < -e} |P_dm| <= (tol / 4) * max_d sum_m |P_dm|."""
+    oy, ox = window_offsets(window, shape)
+    A = np.abs(_fp(P))
+    bar = 0.25 * tol * A.sum(axis=1).max()
+    ext = []
+    for off, sign in ((oy, -1), (oy, 1), (ox, -1), (ox, 1)):
+        side = sign * off  # distance beyond the owner on this side (negative: the other side)
+        e = 0
+        while (A * (side > e)).sum(axis=1).max() > bar:
+            e += 1
+        ext.append(e)
+    return tuple(ext)
+
+
+def truncate_propagator(P: np.ndarray, window: Window, shape, ext) -> np.ndarray:
+    """P with every entry outside the owner's box -ly <= oy <= hy, -lx <= ox <= hx zeroed."""
+    ly, hy, lx, hx = ext
+    oy, ox = window_offsets(window, shape)
+    keep = (oy >= -ly) & (oy <= hy) & (ox >= -lx) & (ox <= hx)
+    return np.where(keep, _fp(P), 0.0)
 
 
 def porous_phi(u: np.ndarray, m: float) -> np.ndarray:
