@@ -8,12 +8,14 @@ residual, the halo gather inside TMA, the propagator apply and the owner scatter
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|split_fast|fp64]
                   [--impl reference] [--workload advdiff2d|batch512|serve|heat1d|vardiff2d|
-                  schrodinger1d]
+                  vardiff1d|schrodinger1d] [--trunc TOL]
 
 --workload picks another configuration: batch512 (512 uneven problems under one CUDA graph),
 serve (a Poisson stream of requests through the server), heat1d (1D heat, persistent GEMV),
 vardiff2d (per-tile propagators with the u - u^3 reaction, batched GEMV; --scheme rb3 for the
-third-order scheme) and schrodinger1d (the complex Schroedinger test; --sn sets the mesh).
+third-order scheme), vardiff1d (2^20-node 1D variable-coefficient diffusion, a propagator per
+tile; --trunc TOL applies truncated propagators) and schrodinger1d (the complex Schroedinger
+test; --sn sets the mesh).
 
 Metric: LEM dof-steps/s = owner nodes x LEM steps / device time. L2 is flushed (256 MiB
 write) between timed calls; each call is bracketed by CUDA events on the context stream.
@@ -51,7 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=2048)
     ap.add_argument("--workload", default="advdiff2d",
-                    choices=["advdiff2d", "batch512", "serve", "heat1d", "vardiff2d", "schrodinger1d"],
+                    choices=["advdiff2d", "batch512", "serve", "heat1d", "vardiff2d", "vardiff1d", "schrodinger1d"],
                     help="advdiff2d: one 2048^2 problem (default); batch512: 512 uneven problems under one "
                          "CUDA graph; serve: a Poisson stream of advance requests through the server")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
@@ -59,6 +61,9 @@ def parse():
     ap.add_argument("--drain", type=float, default=120.0, help="serve: seconds to wait for completions")
     ap.add_argument("--nprob", type=int, default=512, help="batch512: number of problems")
     ap.add_argument("--vside", type=int, default=1024, help="vardiff2d: mesh side")
+    ap.add_argument("--vn", type=int, default=1 << 20, help="vardiff1d: mesh nodes")
+    ap.add_argument("--trunc", type=float, default=None,
+                    help="heat1d / vardiff1d / vardiff2d: truncated propagators with this tolerance")
     ap.add_argument("--sn", type=int, default=400, help="schrodinger1d: mesh points (the paper's test: 400)")
     ap.add_argument("--scheme", default="euler", choices=["euler", "rb3"],
                     help="vardiff2d: exponential Euler-Rosenbrock (phi_1) or the third-order exprb32 (phi_1 + phi_3)")
@@ -286,6 +291,9 @@ def small_workload(a):
         return W.heat1d(), "fp64", "heat1d_N1024_dirichlet_tile64_H16_fp64"
     if a.workload == "schrodinger1d":
         return W.schrodinger1d(n=a.sn), a.prec, f"schrodinger1d_{a.sn}_periodic_kappa10_mu2_tile80_H20"
+    if a.workload == "vardiff1d":
+        name = f"vardiff1d_{a.vn}_dirichlet_tile64_H16_mu2" + (f"_trunc{a.trunc:g}" if a.trunc is not None else "")
+        return W.vardiff1d(n=a.vn), a.prec, name
     name = f"vardiff2d_{a.vside}_dirichlet_tile16_H6_reaction" + ("_rb3" if a.scheme == "rb3" else "")
     return W.vardiff2d(side=a.vside), a.prec, name
 
@@ -325,7 +333,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if a.workload in ("heat1d", "vardiff2d", "schrodinger1d"):
+    if a.workload in ("heat1d", "vardiff2d", "vardiff1d", "schrodinger1d"):
         _, _, name = small_workload(a)
         if a.scheme == "rb3" and a.workload == "vardiff2d":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle's third-order Rosenbrock step "
@@ -659,11 +667,16 @@ def run_small(a):
     npts = wl["u0"].size
     ctx = L.Lem.from_workload(wl, prec=prec, stream=stream.cuda_stream,
                               scheme=a.scheme if a.workload == "vardiff2d" else "euler")
+    if a.trunc is not None:
+        ctx.set_truncation(a.trunc)
     u = torch.tensor(wl["u0"], device=dev)
     t0 = time.perf_counter()
     ctx.build(u)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    band_values = None
+    if a.trunc is not None:
+        band_values = ctx.band_total()  # values of all packed boxes (extents from this build)
     info = ctx.info()
     path = L.APPLY_PATHS[info["apply_path"]]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -705,12 +718,26 @@ def run_small(a):
                        "propagator_classes": info["nclasses"], "n_loc": info["n_loc"], "n_int": info["n_int"],
                        "build_s": round(build_s, 2), "l2": "256 MiB write between timed steps"},
             "gpu_launches": a.steps if persistent else
-                            a.steps * a.inner * ((2 if "gemv" in path else 4) + (3 if a.scheme == "rb3" else 0)),
+                            a.steps * a.inner * ((2 if ("gemv" in path or "band" in path) else 4) +
+                                                 (3 if a.scheme == "rb3" else 0)),
             "e2e": {"value": npts * a.inner / (statistics.median(e2e) * 1e-3), "unit": METRIC,
                     "h2d_bytes_per_step": (16 if ctx.complex else 8) * npts,
                     "d2h_bytes_per_step": (16 if ctx.complex else 8) * npts},
             "clocks": clk.summary()}
-    if k_n and "gemv" in path:
+    if band_values is not None:
+        dense_values = info["nclasses"] * info["n_int"] * info["n_loc"]
+        line["config"]["truncation"] = {"tol": a.trunc, "kept_values": band_values, "dense_values": dense_values,
+                                        "kept_frac": band_values / dense_values}
+    if k_n and "band" in path:
+        pbytes = (4 if path == "f32_band" else 8) * band_values
+        ach = pbytes / (k_ms / k_n * 1e-3) / 1e9
+        line["roofline"] = {"kernel": f"gemv_band_kernel ({path})", "bound": "hbm", "achieved": ach,
+                            "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                            "avg_launch_us": k_ms / k_n * 1e3, "launches": k_n,
+                            "algorithmic_bytes": "truncated propagator boxes streamed once per step (the packed "
+                                                 "values of every tile's owner rows)",
+                            "peak_source": f"{peak_src} HBM copy"}
+    elif k_n and "gemv" in path:
         pbytes = (4 if path == "f32_gemv" else 8) * info["nclasses"] * info["n_int"] * info["n_loc"]
         if ctx.complex:
             pbytes //= 2  # the Re and Im rows of each owner, left halves of the stored embedding
@@ -736,7 +763,7 @@ def run_small(a):
 
 def main():
     a = parse()
-    if a.workload in ("heat1d", "vardiff2d", "schrodinger1d") and a.impl == "ours":
+    if a.workload in ("heat1d", "vardiff2d", "vardiff1d", "schrodinger1d") and a.impl == "ours":
         run_small(a)
         return
     if a.workload == "serve" and a.impl == "ours":

@@ -93,7 +93,9 @@ typedef enum {
   LEM_APPLY_FP64_GEMV = 1,   /* FP64, one batched GEMV over all tiles (many classes) */
   LEM_APPLY_F32_GEMV = 2,    /* FP32 propagators, float-float accumulation (complex: of FP32
                                 FMA sums over 16-byte chunks of a row) */
-  LEM_APPLY_TC_SPLIT = 3     /* shared propagator on the tcgen05 tensor cores */
+  LEM_APPLY_TC_SPLIT = 3,    /* shared propagator on the tcgen05 tensor cores */
+  LEM_APPLY_FP64_BAND = 4,   /* truncated FP64 propagators (lem_set_truncation), batched GEMV */
+  LEM_APPLY_F32_BAND = 5     /* truncated FP32 propagators, float-float accumulation */
 } lem_apply_path;
 
 typedef struct {
@@ -250,6 +252,35 @@ lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
  *   work overlaps on the GPU (other streams, other contexts, other threads) race on it.
  * Errors: LEM_EINVAL, LEM_ENOTREADY, LEM_ECUDA. */
 lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int nsteps);
+
+/* Truncated propagators (Sec. 2, Theorem 1: the entries of the exponential of a banded
+ * matrix decay faster than exponentially away from the band, which is what makes the local
+ * problems accurate at all). With tol >= 0, each owner row of every class's propagator keeps
+ * only the window nodes inside a box around its owner node, offsets -ly..hy along y and
+ * -lx..hx along x in window coordinates, and later lem_step calls apply the kept entries only
+ * (apply_path LEM_APPLY_F32_BAND for LEM_PREC_SPLIT_FAST in PHI mode, LEM_APPLY_FP64_BAND
+ * otherwise, whatever path lem_create chose). Each side's extent, per class, is the smallest
+ * e >= 0 with
+ *     max_d sum_{m beyond e on that side} |P_dm| <= (tol / 4) * max_d sum_m |P_dm|,
+ * so one step's increment at any owner node moves by at most tol * max_d sum_m |P_dm| *
+ * max|r| (r the residual in PHI mode, the state in EXP mode). tol = 0 keeps every nonzero
+ * entry; tol < 0 turns truncation off and restores the path lem_create chose. Extents are
+ * recomputed from the propagators after every build (refreshes included); the first step
+ * after a build synchronises the context stream once to read them. A stored box row holds
+ * min(ly + hy + 1, wy) x min(lx + hx + 1, wx) values (columns padded to a multiple of 4).
+ * Real problems with LEM_SCHEME_EULER only (complex or third-order contexts: LEM_EINVAL);
+ * windows of at most 1024 nodes per axis. The batch's fused schedule, the server and the
+ * allocation-free step do not take truncated contexts (a batch runs them in lanes).
+ * Errors: LEM_EINVAL. */
+lem_status lem_set_truncation(lem_ctx* ctx, double tol);
+
+/* The box kept for class cls: ext = {ly, hy, lx, hx}; *row_values (may be NULL) = values
+ * stored per owner row. cls = -1: ext is zeroed and *row_values is the number of values stored
+ * for all classes together (what one step streams). Computes the extents if the propagators
+ * changed since the last step.
+ * Errors: LEM_EINVAL (no truncation set, class out of range), LEM_ENOTREADY (not built),
+ * LEM_ECUDA. */
+lem_status lem_get_band(lem_ctx* ctx, int64_t cls, int32_t* ext, int64_t* row_values);
 
 /* Synchronise the context stream and return any deferred device error. */
 lem_status lem_sync(lem_ctx* ctx);

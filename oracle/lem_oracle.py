@@ -392,18 +392,23 @@ def lem_step(Xg, u, windows, props, mode: str = "phi", dt: float = 0.0,
 
 
 def lem_run(Xg, u0, windows, nsteps: int, mode: str = "phi", dt: float = 0.0,
-            reaction: bool = False, refresh: int = 0, porous_m: float = 0.0):
+            reaction: bool = False, refresh: int = 0, porous_m: float = 0.0,
+            trunc_tol=None, shape=None):
     """nsteps LEM steps. Linear problems build the propagators once (Sec. 4: phi matrices
     computed at the first step only). With the reaction (or the porous-medium nonlinearity),
     the Jacobian and its propagators are rebuilt from the current state every ``refresh``
     steps (0 = never after step 0): the exponential Euler-Rosenbrock step with a frozen
-    Jacobian (Sec. 4)."""
+    Jacobian (Sec. 4). With ``trunc_tol`` (and the mesh ``shape``) every propagator is
+    truncated to its box (``truncation_extents``) right after each build."""
     u = _fp(u0).copy()
     props = None
     nonlinear = reaction or porous_m
     for n in range(nsteps):
         if props is None or (nonlinear and refresh > 0 and n % refresh == 0):
             props = local_propagators(jacobian(Xg, u, dt, reaction, porous_m), windows, mode)
+            if trunc_tol is not None:
+                props = [truncate_propagator(P, w, shape, truncation_extents(P, w, shape, trunc_tol))
+                         for P, w in zip(props, windows)]
         u = lem_step(Xg, u, windows, props, mode, dt, reaction, porous_m=porous_m)
     return u
 

@@ -93,6 +93,7 @@ namespace {
 void free_ctx(lem_ctx* c) {
   if (!c) return;
   split_destroy(c);
+  band_destroy(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   cudaFree(c->d_coef);
   cudaFree(c->d_tiles);
@@ -276,6 +277,7 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
     s = gemv_set_smem(c);
     if (s != LEM_OK) { free_ctx(c); return s; }
   }
+  c->apply_path_dense = c->apply_path;
   *out = c;
   return LEM_OK;
 }
@@ -295,6 +297,15 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
   DeviceGuard g(ctx->device);
   NvtxRange range("lem_step");
   if (!ctx->built) LEM_TRY(build_propagators(ctx, d_state));
+  if (ctx->band_tol >= 0.0) {  // truncated propagators
+    for (int k = 0; k < nsteps; ++k) {
+      if (ctx->desc.reaction && ctx->desc.refresh > 0 && ctx->steps_since_build >= ctx->desc.refresh)
+        LEM_TRY(build_propagators(ctx, d_state));
+      LEM_TRY(band_step(ctx, d_state));
+      ctx->steps_since_build++;
+    }
+    return LEM_OK;
+  }
   if (ctx->split) return split_step(ctx, d_state, nsteps);
   if (ctx->apply_path == LEM_APPLY_FP64_GEMV || ctx->apply_path == LEM_APPLY_F32_GEMV) {
     bool done = false;  // small linear problems: every step in one persistent launch
@@ -388,6 +399,33 @@ lem_status lem_get_info(const lem_ctx* ctx, lem_info* out) {
   out->device_bytes = ctx->device_bytes;
   out->apply_path = ctx->apply_path;
   return LEM_OK;
+}
+
+lem_status lem_set_truncation(lem_ctx* ctx, double tol) {
+  if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  if (tol != tol) return fail(LEM_EINVAL, "tol is NaN");
+  if (tol < 0.0) {
+    ctx->band_tol = -1.0;
+    ctx->apply_path = ctx->apply_path_dense;
+    return LEM_OK;
+  }
+  if (ctx->cplx) return fail(LEM_EINVAL, "truncated propagators take real problems only");
+  if (ctx->desc.scheme != LEM_SCHEME_EULER)
+    return fail(LEM_EINVAL, "truncated propagators take the exponential Euler scheme only");
+  ctx->band_tol = tol;
+  ctx->band_gen = -1;  // extents follow the new tolerance at the next step
+  const bool f32 = ctx->desc.prec == LEM_PREC_SPLIT_FAST && ctx->desc.mode == LEM_MODE_PHI;
+  ctx->apply_path = f32 ? LEM_APPLY_F32_BAND : LEM_APPLY_FP64_BAND;
+  return LEM_OK;
+}
+
+lem_status lem_get_band(lem_ctx* ctx, int64_t cls, int32_t* ext, int64_t* row_values) {
+  if (!ctx || !ext) return fail(LEM_EINVAL, "NULL argument");
+  if (ctx->band_tol < 0.0) return fail(LEM_EINVAL, "no truncation set (lem_set_truncation)");
+  if (cls < -1 || cls >= int64_t(ctx->classes.size())) return fail(LEM_EINVAL, "class out of range");
+  if (!ctx->built) return fail(LEM_ENOTREADY, "propagators not built");
+  DeviceGuard g(ctx->device);
+  return band_get(ctx, cls, ext, row_values);
 }
 
 lem_status lem_set_timing(lem_ctx* ctx, int enable) {

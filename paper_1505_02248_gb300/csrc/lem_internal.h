@@ -70,6 +70,7 @@ struct Stencil {
 };
 
 struct SplitPlan;  // tcgen05 split-precision state (step_split.cu)
+struct BandPlan;   // truncated propagators (step_band.cu)
 
 }  // namespace lem
 
@@ -112,6 +113,11 @@ struct lem_ctx {
   int* d_status = nullptr;             // device error word
   int64_t device_bytes = 0;
   lem::SplitPlan* split = nullptr;
+  // truncated propagators (lem_set_truncation): off while band_tol < 0
+  double band_tol = -1.0;
+  int band_gen = -1;                   // build_gen the packed boxes were made from
+  int apply_path_dense = 0;            // the apply path lem_create chose, restored when off
+  lem::BandPlan* band = nullptr;
   // optional event timing of the apply kernel
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop)
@@ -129,8 +135,18 @@ lem_status make_plan(lem_ctx* ctx);
 lem_status build_propagators(lem_ctx* ctx, const double* d_state);
 // step_fp64.cu
 lem_status step_fp64(lem_ctx* ctx, double* d_u);
+// step_fp64.cu: dt F(u) (or its complex / porous variants) into r on the context stream
+cudaError_t launch_residual_fp64(const lem_ctx* ctx, double* r, const double* u);
 // step_gemv.cu
 lem_status step_gemv(lem_ctx* ctx, double* d_u, bool f32);
+// blocks per tile of a batched GEMV launch with `threads` threads per block
+int gemv_row_split(const lem_ctx* ctx, int threads);
+// step_band.cu: truncated propagators (extents from ctx->band_tol, packed boxes, apply)
+lem_status band_prepare(lem_ctx* ctx);
+lem_status band_step(lem_ctx* ctx, double* d_u);
+lem_status band_get(lem_ctx* ctx, int64_t cls, int32_t* ext, int64_t* row_values);
+int64_t band_values(const lem_ctx* ctx);
+void band_destroy(lem_ctx* ctx);
 // nsteps of a small linear problem in one cooperative launch; *done false: not eligible
 lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool* done);
 lem_status gemv_set_smem(lem_ctx* ctx);

@@ -246,7 +246,6 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restric
 
 }  // namespace
 
-cudaError_t launch_residual_fp64(const lem_ctx* ctx, double* r, const double* u);
 
 // FP32 copy of the propagators for the reduced-precision GEMV (refreshed after each build).
 lem_status gemv_prepare_f32(lem_ctx* ctx) {
@@ -440,7 +439,7 @@ static int gemv_threads(const lem_ctx* ctx, bool f32) { return (ctx->cplx && f32
 // Blocks per tile: about four waves of blocks (6 to 8 resident per SM), at least 32 owner rows
 // per block, each block's share a whole number of passes (a pass: 4 rows per warp), so that no
 // pass runs part empty (512^2 variable diffusion: 4 blocks of 64 rows per tile, not 5 of 52).
-static int gemv_row_split(const lem_ctx* ctx, int threads) {
+int gemv_row_split(const lem_ctx* ctx, int threads) {
   const int64_t nt = int64_t(ctx->tiles.size());
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || nsm < 1) nsm = 152;

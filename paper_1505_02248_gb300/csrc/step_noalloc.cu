@@ -63,6 +63,8 @@ extern "C" lem_status lem_step_fp64_noalloc(lem_ctx* ctx, double* d_state, int n
     return lem::fail(LEM_EINVAL, "Jacobian refreshes rebuild propagators, which allocates; use refresh = 0");
   if (ctx->desc.reaction == 2)
     return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc does not take the porous-medium problem");
+  if (ctx->band_tol >= 0.0)
+    return lem::fail(LEM_EINVAL, "lem_step_fp64_noalloc does not take truncated propagators (use lem_step)");
   // scratch layout: r | U | Y, each start 256-byte aligned. The batched GEMV (contexts with
   // many propagator classes) reads the windows straight from r and needs r alone.
   const bool gemv = ctx->apply_path == LEM_APPLY_FP64_GEMV;

@@ -1062,6 +1062,7 @@ bool split_batch_eligible(lem_ctx* const* ctxs, int n) {
   for (int i = 0; i < n; ++i) {
     const SplitPlan* sp = ctxs[i]->split;
     if (!sp || sp->np != ctxs[0]->split->np || sp->bn != ctxs[0]->split->bn) return false;
+    if (ctxs[i]->apply_path != LEM_APPLY_TC_SPLIT) return false;  // e.g. truncated propagators
     if (ctxs[i]->device != ctxs[0]->device) return false;
   }
   return true;

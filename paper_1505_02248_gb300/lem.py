@@ -57,7 +57,7 @@ class Info(C.Structure):
     ]
 
 
-APPLY_PATHS = {0: "fp64_gemm", 1: "fp64_gemv", 2: "f32_gemv", 3: "tc_split"}
+APPLY_PATHS = {0: "fp64_gemm", 1: "fp64_gemv", 2: "f32_gemv", 3: "tc_split", 4: "fp64_band", 5: "f32_band"}
 
 
 class ServerStats(C.Structure):
@@ -88,6 +88,8 @@ SIGNATURES = [
     ("lem_plan_query", C.c_int, [C.POINTER(ProblemDesc), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]),
     ("lem_step_fp64_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("lem_set_truncation", C.c_int, [C.c_void_p, C.c_double]),
+    ("lem_get_band", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int64)]),
     ("lem_set_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("lem_get_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     ("lem_sync", C.c_int, [C.c_void_p]),
@@ -315,6 +317,25 @@ class Lem:
         i = Info()
         check(self._lib.lem_get_info(self._h, C.byref(i)), "lem_get_info")
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def set_truncation(self, tol: float):
+        """lem_set_truncation: keep each owner row's box of window nodes (tol >= 0), or turn
+        truncation off (tol < 0)."""
+        check(self._lib.lem_set_truncation(self._h, float(tol)), "lem_set_truncation")
+
+    def band(self, cls: int):
+        """lem_get_band: ((ly, hy, lx, hx), values stored per owner row) of class cls."""
+        ext = (C.c_int32 * 4)()
+        nv = C.c_int64()
+        check(self._lib.lem_get_band(self._h, int(cls), ext, C.byref(nv)), "lem_get_band")
+        return tuple(int(e) for e in ext), int(nv.value)
+
+    def band_total(self) -> int:
+        """Values stored for all classes' boxes together (lem_get_band with cls = -1)."""
+        ext = (C.c_int32 * 4)()
+        nv = C.c_int64()
+        check(self._lib.lem_get_band(self._h, -1, ext, C.byref(nv)), "lem_get_band")
+        return int(nv.value)
 
     def set_timing(self, on: bool):
         check(self._lib.lem_set_timing(self._h, 1 if on else 0), "lem_set_timing")

@@ -12,6 +12,8 @@ coefficients, Sec. 4) at the sizes the GPU path is built for:
                   Laplacian, tiles 32^2 + H = 8, u0 = Gaussian random field (length 16 h).
 * ``vardiff2d``   2D Dirichlet diffusion-reaction div(k grad u) + u - u^3, 1024^2,
                   k = exp(GRF(32 h)) (lognormal, sigma = 1), tiles 16^2 + H = 6.
+* ``vardiff1d``   1D Dirichlet diffusion (k u_x)_x, 2^20 nodes, lognormal k, median
+                  diffusion number 2, tiles of 64 + H = 16 (a propagator per tile).
 
 Stencil coefficients follow the C-ABI convention: entries of A (not dt-scaled) in the
 order C, W, E, S, N, where W/E are the x - 1 / x + 1 neighbours and S/N the y - 1 / y + 1
@@ -85,6 +87,15 @@ def stencil_advdiff_2d(nu: float, ax: float, ay: float, h: float) -> dict:
     return {"C": -4 * d - cx - cy, "W": d + cx, "E": d, "S": d + cy, "N": d}
 
 
+def stencil_vardiff_1d(k: np.ndarray, h: float) -> dict:
+    """(k u_x)_x with face coefficients k_{i+1/2} = (k_i + k_{i+1}) / 2; a face on a Dirichlet
+    wall takes the value of its interior node. Returns per-node arrays."""
+    kp = np.pad(k, (1, 1), mode="edge")
+    W = 0.5 * (kp[1:-1] + kp[:-2]) / h ** 2
+    E = 0.5 * (kp[1:-1] + kp[2:]) / h ** 2
+    return {"C": -(W + E), "W": W, "E": E}
+
+
 def stencil_vardiff_2d(k: np.ndarray, h: float) -> dict:
     """div(k grad u) with face coefficients k_{i+1/2} = (k_i + k_{i+1}) / 2; a face on a
     Dirichlet wall takes the value of its interior node. Returns per-node arrays."""
@@ -120,6 +131,19 @@ def advdiff2d(side: int = 2048, tile=32, overlap=8, nu: float = 5.0,
     overlap = (overlap, overlap) if np.isscalar(overlap) else tuple(overlap)
     return dict(name=f"advdiff2d_{side}", shape=(side, side), bc=("periodic", "periodic"),
                 coef=coef, dt=dt, tile=tile, overlap=overlap, u0=u0, reaction=False)
+
+
+def vardiff1d(n: int = 1 << 20, tile: int = 64, overlap: int = 16, mu_med: float = 2.0, ell_k: float = 32.0,
+              sigma: float = 1.0, ell_u: float = 16.0, seed: int = 6) -> dict:
+    """1D variable-coefficient diffusion (k u_x)_x, Dirichlet, k = exp(sigma GRF(ell_k h))
+    (lognormal), dt from median(k) dt / h^2 = mu_med; u0 = GRF(ell_u h). Every window has its
+    own local operator, so every tile has its own propagator (streamed from HBM each step)."""
+    h = 1.0 / (n + 1)
+    k = np.exp(sigma * grf_1d(n, ell_k, seed))
+    dt = mu_med * h ** 2 / float(np.median(k))
+    u0 = grf_1d(n, ell_u, seed + 100)
+    return dict(name=f"vardiff1d_{n}", shape=(n,), bc=("dirichlet",), coef=stencil_vardiff_1d(k, h), dt=dt,
+                tile=(tile,), overlap=(overlap,), u0=u0, reaction=False)
 
 
 def vardiff2d(side: int = 1024, tile: int = 16, overlap: int = 6, ell_k: float = 32.0,
