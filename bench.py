@@ -468,10 +468,12 @@ def run_batch(a):
     # dominant kernel (the split GEMM), algorithmic FLOPs = products x 2 x owner rows x window
     # nodes x windows. Fused schedule: the multi-problem GEMM launches of a.inner steps timed
     # with events outside the graph; lanes: each problem's launches timed on a copy of its state.
-    gemm_ms, gemm_n, flops, prof = 0.0, 0, 0.0, None
+    gemm_ms, gemm_n, flops, prof, exec_flops = 0.0, 0, 0.0, None, None
+    cands = batch.candidates()
     if sched["fused"]:
         prof = batch.profile(a.inner)
         gemm_ms, gemm_n, flops = prof["gemm_ms"], a.inner, prof["gemm_flops"]
+        exec_flops = batch.gemm_work()[1] * a.inner
     else:
         nprod = {"split": 6, "split_fast": 4}.get(a.prec, 1)
         for p, c, s in zip(probs, ctxs, states):
@@ -506,6 +508,9 @@ def run_batch(a):
                    "schedule_s": round(schedule_s, 1),
                    "schedule": "fused" if sched["fused"] else "lanes",
                    "candidate_ms_per_launch": {"lanes": sched["lanes_ms"], "fused": sched["fused_ms"]},
+                   "autotuner": [{"schedule": "fused" if c["fused"] else "lanes",
+                                  ("block_cap" if c["fused"] else "lanes"): c["n_cap"] if c["fused"] else c["lanes"],
+                                  "ms": round(c["ms"], 4), "chosen": bool(c["chosen"])} for c in cands],
                    "lane_load_ms": {"max": float(loads.max()), "mean": float(loads.mean())}},
         # per problem and launch: FP64->float-float, max|r| pass, (residual + GEMM) per LEM
         # step, float-float->FP64 (split); residual, gather, GEMM, scatter per step (FP64)
@@ -522,6 +527,9 @@ def run_batch(a):
                             "achieved": ach, "peak": tflops_peak, "unit": "TFLOP/s", "frac": ach / tflops_peak,
                             "traffic": None, "avg_launch_us": gemm_ms / gemm_n * 1e3, "launches": gemm_n,
                             "peak_source": f"{peak_src} bf16 dense (fp16 same rate)"}
+        if exec_flops:
+            line["roofline"]["executed_over_algorithmic"] = exec_flops / flops
+            line["roofline"]["executed_frac"] = exec_flops / (gemm_ms * 1e-3) / 1e12 / tflops_peak
     line["e2e"] = {"value": total * a.inner / (e2e_ms_med * 1e-3), "unit": METRIC,
                    "h2d_bytes_per_step": 8 * total, "d2h_bytes_per_step": 8 * total, "ms_per_step": e2e_ms_med}
     line["clocks"] = clk.summary()

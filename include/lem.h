@@ -293,8 +293,12 @@ void lem_destroy(lem_ctx* ctx);
 /* ------------------------------------------------------------------ batching
  * Advance many independent problems (contexts) together with one CUDA graph launch per
  * `steps_per_launch` LEM steps. At creation every context is built and warmed up on a copy
- * of its state and its step time is measured; the schedule (lem_batch_info) is then picked
- * by timing the candidates. The states d_states[i] (device, FP64) are captured: each launch
+ * of its state and its step time is measured; an autotuner then captures and times candidate
+ * schedules (lem_batch_candidates) and keeps the fastest (lem_batch_info): lanes with
+ * lanes/2, lanes and 2 lanes (within 1..n), and, when every context is on the same
+ * tensor-core split tier, the fused schedule with window-block width caps 0 (each context's
+ * own block), 128, 64 and 32 (each problem takes the power of two in [16, cap] whose blocks
+ * load the fewest operand bytes). The states d_states[i] (device, FP64) are captured: each launch
  * advances them in place. Contexts with a Jacobian refresh (reaction with refresh > 0) are
  * rejected, because rebuilding propagators cannot be captured; so are complex contexts and the
  * porous-medium problem (step those with lem_step). The contexts' streams are used only outside the
@@ -311,16 +315,38 @@ lem_status lem_batch_run(lem_batch* b, int launches);
 /* Measured single-launch time of each problem (ms, host array of n) and its lane. */
 lem_status lem_batch_schedule(const lem_batch* b, double* est_ms, int* lane);
 
-/* Which schedule the graph runs. Both candidates are captured and timed on scratch copies of
- * the states at creation, and the faster is kept: lanes (every context's own launches on
+/* Which schedule the graph runs. The candidates are captured and timed on scratch copies of
+ * the states at creation, and the fastest is kept: lanes (every context's own launches on
  * concurrent graph branches, problems assigned longest-first) or fused (all contexts on the
  * same tensor-core split tier: one residual and one persistent GEMM launch per LEM step for
- * the whole batch). fused_ms = -1 when the contexts cannot be fused. The environment variable
- * LEM_BATCH_SCHEDULE=lanes|fused, read at creation, overrides the timed choice. */
+ * the whole batch). lanes_ms and fused_ms are the best timed candidate of each kind;
+ * fused_ms = -1 when the contexts cannot be fused. The environment variable
+ * LEM_BATCH_SCHEDULE=lanes|fused|fused:<cap>, read at creation, restricts the choice to one
+ * kind (or one fused width cap). */
 lem_status lem_batch_info(const lem_batch* b, int* fused, double* lanes_ms, double* fused_ms);
 
 /* Wait for the batch stream; LEM_ETIMEOUT if a tensor-core kernel gave up waiting. */
 lem_status lem_batch_sync(lem_batch* b);
+
+/* One autotuner candidate: fused (1) or lanes (0), its lane count (lanes) or window-block
+ * width cap (fused), the best of three timed graph launches (ms), and whether it was chosen. */
+typedef struct {
+  int fused;
+  int lanes;
+  int n_cap;
+  double ms;
+  int chosen;
+} lem_batch_candidate;
+
+/* The autotuner's candidates in the order they were timed: *count = how many; up to `max`
+ * are copied to out. Errors: LEM_EINVAL. */
+lem_status lem_batch_candidates(const lem_batch* b, int max, lem_batch_candidate* out, int* count);
+
+/* Work of one fused GEMM launch (one LEM step of every problem): the algorithmic FLOPs
+ * (products x 2 x owner rows x window nodes over all windows) and the FLOPs the MMAs execute
+ * (128-row M blocks, whole window blocks, window rows padded to 16-node K steps). Errors:
+ * LEM_EINVAL (NULL arguments, or the batch runs the lanes schedule). */
+lem_status lem_batch_gemm_work(const lem_batch* b, double* algorithmic_flops, double* executed_flops);
 
 /* Fused schedule only: run `nsteps` LEM steps of every problem outside the graph (advancing the
  * captured states like a launch does) with CUDA events around each kernel, and report the

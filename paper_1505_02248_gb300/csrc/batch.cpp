@@ -1,10 +1,15 @@
 // Batched advance of independent problems under one CUDA graph (lem_batch_*, include/lem.h).
 //
-// Two schedules are built and timed, and the faster one is kept:
-//  * lanes: every context's own step launches, spread over concurrent lanes (graph branches)
-//    by longest-processing-time-first from each problem's measured step time;
-//  * fused (all contexts on the same tensor-core split tier): one residual launch and one
-//    persistent GEMM launch per LEM step for all problems together.
+// An autotuner captures and times candidate schedules on scratch copies of the states, and
+// the fastest one is kept (lem_batch_candidates lists them with their times):
+//  * lanes, for several lane counts: every context's own step launches, spread over
+//    concurrent lanes (graph branches) by longest-processing-time-first from each problem's
+//    measured step time;
+//  * fused (all contexts on the same tensor-core split tier), for several window-block
+//    widths: one residual launch and one persistent GEMM launch per LEM step for all problems
+//    together. Width cap 0 keeps every context's own block of 128 (or 256) windows; a cap c
+//    gives each problem the power of two in [16, c] whose blocks load the fewest operand
+//    bytes, so small tile grids take narrow MMAs instead of mostly empty blocks.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -16,8 +21,10 @@
 struct lem_batch {
   int n = 0, steps = 0, nlanes = 0, device = 0;
   int fused = 0;              // the graph runs the fused schedule
-  double lanes_ms = -1.0;     // measured time of one launch of each candidate (-1: not built)
-  double fused_ms = -1.0;
+  int fused_cap = 0;          // its window-block width cap
+  double lanes_ms = -1.0;     // measured time of one launch of the best candidate of each kind
+  double fused_ms = -1.0;     // (-1: none built)
+  std::vector<lem_batch_candidate> cands;
   cudaStream_t stream = nullptr;
   std::vector<cudaStream_t> lane_streams;
   std::vector<lem_ctx*> ctxs;
@@ -95,19 +102,43 @@ lem_status capture(lem_batch* b, double* const* states, lem::SplitBatch* sb, cud
   return st;
 }
 
-// One warm launch, then the time of one launch.
+// Lanes for nl lanes: longest problems first, each to the lane with the least work so far.
+void assign_lanes(lem_batch* b, int nl) {
+  const int n = b->n;
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->est_ms[a] > b->est_ms[c]; });
+  std::vector<double> load(nl, 0.0);
+  b->nlanes = nl;
+  b->lane_items.assign(nl, {});
+  b->lane.assign(n, 0);
+  for (int i : order) {
+    const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
+    load[l] += b->est_ms[i];
+    b->lane_items[l].push_back(i);
+    b->lane[i] = l;
+  }
+}
+
+// One warm launch, then the best of three timed launches.
 lem_status time_graph(cudaGraphExec_t exec, cudaStream_t s, double* ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LEM_CUDA_TRY(cudaEventCreate(&e0));
   LEM_CUDA_TRY(cudaEventCreate(&e1));
   lem_status st = LEM_OK;
-  if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
-      cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
-      cudaEventSynchronize(e1) != cudaSuccess)
-    st = lem::cuda_fail(cudaGetLastError(), "timing a batch graph");
-  float f = 0.0f;
-  if (st == LEM_OK) cudaEventElapsedTime(&f, e0, e1);
-  *ms = f;
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) st = lem::cuda_fail(cudaGetLastError(), "timing a batch graph");
+  float best = -1.0f;
+  for (int r = 0; r < 3 && st == LEM_OK; ++r) {
+    if (cudaEventRecord(e0, s) != cudaSuccess || cudaGraphLaunch(exec, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = lem::cuda_fail(cudaGetLastError(), "timing a batch graph");
+      break;
+    }
+    float f = 0.0f;
+    cudaEventElapsedTime(&f, e0, e1);
+    if (best < 0.0f || f < best) best = f;
+  }
+  *ms = best;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
@@ -179,62 +210,87 @@ lem_status lem_batch_create(lem_ctx* const* ctxs, double* const* d_states, int n
     cudaEventDestroy(e1);
     if (st == LEM_OK && cudaDeviceSynchronize() != cudaSuccess) st = lem::cuda_fail(cudaGetLastError(), "warm-up");
   }
-  // lanes: longest problems first, each to the lane with the least work so far
+  // candidate lane counts (lanes/2, lanes, 2 lanes, within 1..n) and their streams
+  std::vector<int> lane_counts;
+  for (int nl : {lanes / 2, lanes, 2 * lanes}) {
+    nl = std::max(1, std::min(nl, n));
+    if (std::find(lane_counts.begin(), lane_counts.end(), nl) == lane_counts.end()) lane_counts.push_back(nl);
+  }
   if (st == LEM_OK) {
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->est_ms[a] > b->est_ms[c]; });
-    std::vector<double> load(b->nlanes, 0.0);
-    b->lane_items.assign(b->nlanes, {});
-    b->lane.assign(n, 0);
-    for (int i : order) {
-      const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
-      load[l] += b->est_ms[i];
-      b->lane_items[l].push_back(i);
-      b->lane[i] = l;
-    }
-    b->lane_streams.assign(b->nlanes, nullptr);
-    for (auto& s : b->lane_streams) {
+    b->lane_streams.assign(*std::max_element(lane_counts.begin(), lane_counts.end()), nullptr);
+    for (auto& s2 : b->lane_streams) {
       if (st != LEM_OK) break;
-      const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      const cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
       if (e != cudaSuccess) st = lem::cuda_fail(e, "lane stream");
     }
   }
-  // time both candidate schedules on the scratch states
-  const bool can_fuse = lem::split_batch_eligible(const_cast<lem_ctx* const*>(ctxs), n);
-  if (st == LEM_OK) {
+  // time every candidate on the scratch states
+  for (int nl : lane_counts) {
+    if (st != LEM_OK) break;
+    assign_lanes(b, nl);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t e = nullptr;
+    double ms = -1.0;
     st = capture(b, tmp.data(), nullptr, &g, &e);
-    if (st == LEM_OK) st = time_graph(e, b->stream, &b->lanes_ms);
+    if (st == LEM_OK) st = time_graph(e, b->stream, &ms);
     if (e) cudaGraphExecDestroy(e);
     if (g) cudaGraphDestroy(g);
+    if (st == LEM_OK) b->cands.push_back(lem_batch_candidate{0, nl, 0, ms, 0});
   }
-  if (st == LEM_OK && can_fuse) {
-    lem::SplitBatch* sb = nullptr;
-    st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), tmp.data(), n, &sb);
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t e = nullptr;
-    if (st == LEM_OK) st = capture(b, tmp.data(), sb, &g, &e);
-    if (st == LEM_OK) st = time_graph(e, b->stream, &b->fused_ms);
-    if (st == LEM_OK) st = lem::split_batch_check_error(sb);
-    if (e) cudaGraphExecDestroy(e);
-    if (g) cudaGraphDestroy(g);
-    lem::split_batch_destroy(sb);
+  const bool can_fuse = lem::split_batch_eligible(const_cast<lem_ctx* const*>(ctxs), n);
+  if (can_fuse) {
+    for (int cap : {0, 128, 64, 32}) {
+      if (st != LEM_OK) break;
+      lem::SplitBatch* sb = nullptr;
+      st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), tmp.data(), n, cap, &sb);
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t e = nullptr;
+      double ms = -1.0;
+      if (st == LEM_OK) st = capture(b, tmp.data(), sb, &g, &e);
+      if (st == LEM_OK) st = time_graph(e, b->stream, &ms);
+      if (st == LEM_OK) st = lem::split_batch_check_error(sb);
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+      lem::split_batch_destroy(sb);
+      if (st == LEM_OK) b->cands.push_back(lem_batch_candidate{1, 0, cap, ms, 0});
+    }
   }
   for (double* p : tmp)
     if (p) cudaFree(p);
-  // the chosen schedule on the caller's states
+  // the fastest candidate (LEM_BATCH_SCHEDULE=lanes|fused restricts the choice to one kind,
+  // fused:<cap> to one width cap; a fused request on contexts that cannot be fused keeps lanes)
   if (st == LEM_OK) {
-    b->fused = can_fuse && b->fused_ms >= 0.0 && b->fused_ms < b->lanes_ms;
-    // LEM_BATCH_SCHEDULE=lanes|fused overrides the timing (a fused request on contexts that
-    // cannot be fused keeps lanes)
+    int want = -1, want_cap = -1;
     if (const char* f = std::getenv("LEM_BATCH_SCHEDULE")) {
-      if (std::strcmp(f, "lanes") == 0) b->fused = 0;
-      if (std::strcmp(f, "fused") == 0) b->fused = can_fuse && b->fused_ms >= 0.0;
+      if (std::strcmp(f, "lanes") == 0) want = 0;
+      if (std::strncmp(f, "fused", 5) == 0 && can_fuse) {
+        want = 1;
+        if (f[5] == ':') want_cap = std::atoi(f + 6);
+      }
     }
-    if (b->fused) st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), const_cast<double* const*>(d_states), n, &b->sb);
-    if (st == LEM_OK) st = capture(b, const_cast<double* const*>(d_states), b->sb, &b->graph, &b->exec);
+    int best = -1;
+    for (int k = 0; k < int(b->cands.size()); ++k) {
+      const lem_batch_candidate& c = b->cands[k];
+      double& kind_best = c.fused ? b->fused_ms : b->lanes_ms;
+      if (kind_best < 0.0 || c.ms < kind_best) kind_best = c.ms;
+      if (want >= 0 && c.fused != want) continue;
+      if (want_cap >= 0 && c.n_cap != want_cap) continue;
+      if (best < 0 || c.ms < b->cands[best].ms) best = k;
+    }
+    if (best < 0) st = fail(LEM_ECUDA, "no batch schedule could be timed");
+    if (st == LEM_OK) {
+      b->cands[best].chosen = 1;
+      const lem_batch_candidate& c = b->cands[best];
+      b->fused = c.fused;
+      b->fused_cap = c.n_cap;
+      if (b->fused) {
+        st = lem::split_batch_prepare(const_cast<lem_ctx* const*>(ctxs), const_cast<double* const*>(d_states), n,
+                                      c.n_cap, &b->sb);
+      } else {
+        assign_lanes(b, c.lanes);
+      }
+      if (st == LEM_OK) st = capture(b, const_cast<double* const*>(d_states), b->sb, &b->graph, &b->exec);
+    }
   }
   if (st != LEM_OK) {
     free_batch(b);
@@ -277,6 +333,21 @@ lem_status lem_batch_info(const lem_batch* b, int* fused, double* lanes_ms, doub
   if (fused) *fused = b->fused;
   if (lanes_ms) *lanes_ms = b->lanes_ms;
   if (fused_ms) *fused_ms = b->fused_ms;
+  return LEM_OK;
+}
+
+lem_status lem_batch_candidates(const lem_batch* b, int max, lem_batch_candidate* out, int* count) {
+  if (!b || !count || (max > 0 && !out)) return fail(LEM_EINVAL, "bad batch candidates arguments");
+  *count = int(b->cands.size());
+  for (int k = 0; k < max && k < int(b->cands.size()); ++k) out[k] = b->cands[k];
+  return LEM_OK;
+}
+
+lem_status lem_batch_gemm_work(const lem_batch* b, double* algorithmic_flops, double* executed_flops) {
+  if (!b || !algorithmic_flops || !executed_flops) return fail(LEM_EINVAL, "NULL argument");
+  if (!b->fused) return fail(LEM_EINVAL, "the batch runs the lanes schedule (no fused GEMM)");
+  *algorithmic_flops = lem::split_batch_gemm_flops(b->sb, b->ctxs.data());
+  *executed_flops = lem::split_batch_executed_flops(b->sb);
   return LEM_OK;
 }
 

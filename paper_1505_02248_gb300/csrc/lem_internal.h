@@ -161,7 +161,10 @@ lem_status encode_f16_map(CUtensorMap* m, void* base, int rank, const cuuint64_t
 // multi-problem split steps (one residual and one GEMM launch per step for a whole batch)
 struct SplitBatch;
 bool split_batch_eligible(lem_ctx* const* ctxs, int n);
-lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, SplitBatch** out);
+// cap: widest window block per problem (0: each context's own width; else the cheapest power of
+// two in [16, cap] per problem)
+lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, int cap, SplitBatch** out);
+double split_batch_executed_flops(const SplitBatch* b);
 lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEvent_t* ev = nullptr);
 double split_batch_gemm_flops(const SplitBatch* b, lem_ctx* const* ctxs);
 lem_status split_batch_check_error(SplitBatch* b);

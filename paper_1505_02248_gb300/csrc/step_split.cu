@@ -80,6 +80,7 @@ struct GemmGeom {
   int Wy, Wx, Ty, Tx, nx, BNx, BNy, ntx, nty;
   int M;                // owner rows (Ty * Tx); M blocks past it are masked
   int nbx;              // window blocks per row of the tile grid
+  int bnp;              // windows per block (BNx * BNy <= BN, a multiple of 16): the MMA's N
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int drain_rows;       // three pieces: window rows per correction drain
   int unit0;            // multi-problem launch: this problem's first unit
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
           if (s_abort) break;
           uint8_t* st = tiles + s * STAGE_BYTES;
-          ptx::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          // the stage's bytes: NP P pieces and NP residual pieces of bnp window rows each
+          ptx::mbar_arrive_expect_tx(&full[s], uint32_t(NP) * uint32_t(A_BYTES + g.bnp * KB * 2));
           if (g.fault && blockIdx.x == 0 && it == 0) {  // test hook: the bytes never arrive
             issued = it + 1;
             continue;
@@ -571,7 +573,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // each collecting drain_rows window rows before the epilogue takes it. The epilogue folds a
     // tile's main sum into its last correction buffer and frees main at once.
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_f16_f32(BM, BN);
       bool ok = true;
       int it = 0, lt = 0, kc = 0;
       int64_t cur = cur0;
@@ -581,6 +582,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const GemmGeom& g = locate(u, lu)->g;
         if (kb1 < 0) kb1 = g.Wy;
         const int ksteps = (g.Wx + 15) / 16, dr = DRAIN ? g.drain_rows : 1;
+        const uint32_t idesc = ptx::idesc_f16_f32(BM, g.bnp);  // N = this problem's window block
         const int nbuf = DRAIN ? 1 : NBUF;
         const int b = lt % nbuf;
         if (lt >= nbuf) {
@@ -662,6 +664,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint32_t tc = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + j) * BN);
 #pragma unroll
           for (int h = 0; h < BN / 64; ++h) {  // 64 columns per load round trip
+            if (h * 64 >= g.bnp) break;       // (columns past bnp hold nothing of this unit)
             uint32_t r[64];
             ptx::tmem_ld_32x32b_x64(tc + h * 64, r);
 #pragma unroll
@@ -735,6 +738,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const uint32_t t_fold = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + fold) * BN);
 #pragma unroll
         for (int q = 0; q < BN / 16; ++q) {  // unrolled: cs is indexed statically
+          if (q * 16 >= g.bnp) break;
           float vm[16];
           ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
 #pragma unroll
@@ -747,7 +751,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) ptx::mbar_arrive(&acce[b]);
         const float zero[16] = {};
 #pragma unroll 1
-        for (int q = 0; q < BN / 16; ++q) {
+        for (int q = 0; q < g.bnp / 16; ++q) {
           float vm[16];
           ptx::tmem_ld_32x32b_x16(t_fold + q * 16, vm);
           batch(q * 16, vm, zero);
@@ -758,7 +762,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         continue;
       } else {
 #pragma unroll 1
-        for (int q = 0; q < BN / 16; ++q) {
+        for (int q = 0; q < g.bnp / 16; ++q) {
           float vm[16], vc[16];
           ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
           ptx::tmem_ld_32x32b_x16(t_lane + BN + q * 16, vc);
@@ -975,7 +979,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   GemmGeom& g = sp->prob.g;
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx; g.nty = sp->nty; g.M = sp->M;
-  g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby;
+  g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bnp = sp->bn;
   // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
   // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
   g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
@@ -1048,6 +1052,7 @@ lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
 // GEMM launch (units of all problems, the heaviest problems' units first).
 struct SplitBatch {
   int n = 0, np = 2, bn = 128, nunits = 0, res_blocks = 0, conv_blocks = 0, grid = 0;
+  double executed_flops = 0.0;  // MMA work of one fused GEMM launch, padding included
   SplitProblem first{};  // by-value kernel argument (unused when the array is given)
   SplitProblem* d_probs = nullptr;
   ResProblem* d_res = nullptr;
@@ -1075,7 +1080,29 @@ void split_batch_destroy(SplitBatch* b) {
   delete b;
 }
 
-lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, SplitBatch** out) {
+// Windows per block of one problem in a multi-problem launch: the power of two in [16, cap]
+// (cap 0: the context's own width) whose blocks cost the fewest operand bytes, NP P pieces
+// plus NP residual pieces of bnp window rows per stage and block (ties: the wider). Small
+// tile grids then take narrow N blocks instead of mostly empty 128-window ones.
+static int batch_block_width(const SplitPlan* sp, int cap) {
+  if (cap <= 0) return sp->bn;
+  cap = std::min(cap, sp->bn);
+  int best = sp->bn;
+  int64_t best_cost = -1;
+  for (int w = 16; w <= cap; w *= 2) {
+    int bx = 0, by = 0;
+    group_tiles(sp->ntx, sp->nty, w, &bx, &by);
+    const int64_t blocks = int64_t((sp->ntx + bx - 1) / bx) * ((sp->nty + by - 1) / by);
+    const int64_t cost = blocks * int64_t(sp->np) * (A_BYTES + int64_t(w) * KB * 2);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best = w;
+    }
+  }
+  return best;
+}
+
+lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, int n, int cap, SplitBatch** out) {
   *out = nullptr;
   if (!split_batch_eligible(ctxs, n)) return fail(LEM_EINVAL, "batch is not one tensor-core split tier");
   for (int i = 0; i < n; ++i)
@@ -1099,8 +1126,30 @@ lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, in
     const lem_ctx* c = ctxs[order[k]];
     const SplitPlan* sp = c->split;
     probs[k] = sp->prob;
-    probs[k].g.unit0 = b->nunits;
-    b->nunits += sp->prob.g.nMB * sp->prob.g.nNB;
+    GemmGeom& g = probs[k].g;
+    const int w = batch_block_width(sp, cap);
+    if (w != sp->bn) {  // narrower window blocks: their own residual tensor maps
+      int bx = 0, by = 0;
+      group_tiles(sp->ntx, sp->nty, w, &bx, &by);
+      g.BNx = bx; g.BNy = by; g.bnp = w;
+      g.nbx = (sp->ntx + bx - 1) / bx;
+      g.nNB = g.nbx * ((sp->nty + by - 1) / by);
+      __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
+      cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
+      cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
+      cuuint32_t rbox[4] = {KB, cuuint32_t(bx), 1, cuuint32_t(by)};
+      for (int q = 0; q < 3; ++q) {
+        const lem_status e = encode_f16_map(&probs[k].tm[3 + q], rbase[q], 4, rd, rs, rbox, "residual slice");
+        if (e != LEM_OK) {
+          delete b;
+          return e;
+        }
+      }
+    }
+    g.unit0 = b->nunits;
+    b->nunits += g.nMB * g.nNB;
+    b->executed_flops += 2.0 * sp->np * 2.0 * double(g.nMB) * BM * double(sp->Wy) * ((sp->Wx + 15) / 16 * 16) *
+                         double(g.nNB) * g.bnp;
     ResProblem& r = res[k];
     r.p = sp->rp;
     r.uh = sp->d_uh; r.ul = sp->d_ul; r.Rint = sp->d_Rint; r.R2 = sp->d_R2; r.R3 = sp->d_R3;
@@ -1162,6 +1211,8 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
 }
+
+double split_batch_executed_flops(const SplitBatch* b) { return b->executed_flops; }
 
 // Algorithmic FLOPs of one fused GEMM launch: products x 2 x owner rows x window nodes, summed
 // over every window of every problem.

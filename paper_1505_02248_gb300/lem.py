@@ -60,6 +60,10 @@ class Info(C.Structure):
 APPLY_PATHS = {0: "fp64_gemm", 1: "fp64_gemv", 2: "f32_gemv", 3: "tc_split", 4: "fp64_band", 5: "f32_band"}
 
 
+class BatchCandidate(C.Structure):
+    _fields_ = [("fused", C.c_int), ("lanes", C.c_int), ("n_cap", C.c_int), ("ms", C.c_double), ("chosen", C.c_int)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [
         ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
@@ -101,6 +105,8 @@ SIGNATURES = [
     ("lem_batch_destroy", None, [C.c_void_p]),
     ("lem_batch_info", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lem_batch_sync", C.c_int, [C.c_void_p]),
+    ("lem_batch_candidates", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
+    ("lem_batch_gemm_work", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lem_batch_profile", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("lem_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
@@ -442,6 +448,20 @@ class Batch:
 
     def sync(self):
         check(self._lib.lem_batch_sync(self._h), "lem_batch_sync")
+
+    def candidates(self):
+        """The autotuner's timed candidates: list of dicts (fused, lanes, n_cap, ms, chosen)."""
+        n = C.c_int()
+        check(self._lib.lem_batch_candidates(self._h, 0, None, C.byref(n)), "lem_batch_candidates")
+        arr = (BatchCandidate * max(1, n.value))()
+        check(self._lib.lem_batch_candidates(self._h, n.value, arr, C.byref(n)), "lem_batch_candidates")
+        return [{f: getattr(arr[k], f) for f, _ in BatchCandidate._fields_} for k in range(n.value)]
+
+    def gemm_work(self):
+        """(algorithmic, executed) FLOPs of one fused GEMM launch (fused schedule only)."""
+        a, e = C.c_double(), C.c_double()
+        check(self._lib.lem_batch_gemm_work(self._h, C.byref(a), C.byref(e)), "lem_batch_gemm_work")
+        return a.value, e.value
 
     def profile(self, nsteps: int = 1):
         g, r, o, f = C.c_double(), C.c_double(), C.c_double(), C.c_double()

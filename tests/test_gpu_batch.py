@@ -66,10 +66,18 @@ def test_batch_equals_per_problem_steps(steps_per_launch, launches, lanes):
     for i, (s, r) in enumerate(zip(states, ref)):
         assert np.array_equal(s.cpu().numpy(), r), probs[i]["name"]
     est, lane = b.schedule()
-    assert np.all(est > 0) and lane.min() >= 0 and lane.max() < min(lanes, len(probs))
-    # longest-processing-time bound on the busiest lane
-    loads = np.bincount(lane, weights=est, minlength=min(lanes, len(probs)))
-    assert loads.max() <= est.sum() / min(lanes, len(probs)) + est.max() + 1e-9
+    cands = b.candidates()
+    chosen = [c for c in cands if c["chosen"]]
+    assert len(chosen) == 1 and all(c["ms"] > 0 for c in cands)
+    # the autotuner tried lanes/2, lanes and 2 lanes (within 1..n)
+    want = sorted({max(1, min(k, len(probs))) for k in (lanes // 2, lanes, 2 * lanes)})
+    assert sorted(c["lanes"] for c in cands if not c["fused"]) == want
+    if not chosen[0]["fused"]:
+        nl = chosen[0]["lanes"]
+        assert np.all(est > 0) and lane.min() >= 0 and lane.max() < nl
+        # longest-processing-time bound on the busiest lane
+        loads = np.bincount(lane, weights=est, minlength=nl)
+        assert loads.max() <= est.sum() / nl + est.max() + 1e-9
     b.close()
 
 
@@ -105,10 +113,11 @@ def test_batch_rejects_bad_arguments():
         L.Batch([cr], [sr])
 
 
-@pytest.mark.parametrize("schedule", ["fused", "lanes"])
+@pytest.mark.parametrize("schedule", ["fused:0", "fused:128", "fused:64", "fused:32", "lanes"])
 def test_split_batch_schedules_equal_per_problem_steps(schedule, monkeypatch):
     """All-split batches can run fused (one residual and one persistent GEMM launch per step
-    for every problem) or on lanes; both give each problem exactly its own lem_step result."""
+    for every problem; every window-block width cap the autotuner tries) or on lanes; each
+    gives each problem exactly its own lem_step result."""
     monkeypatch.setenv("LEM_BATCH_SCHEDULE", schedule)
     probs = W.batch_problems(n=24, seed=7, side_max=160)
     ref = []
@@ -125,7 +134,12 @@ def test_split_batch_schedules_equal_per_problem_steps(schedule, monkeypatch):
     b = L.Batch(ctxs, states, steps_per_launch=3, lanes=4)
     info = b.info()
     assert info["fused_ms"] > 0 and info["lanes_ms"] > 0
-    assert info["fused"] == (schedule == "fused")
+    assert info["fused"] == schedule.startswith("fused")
+    chosen = [c for c in b.candidates() if c["chosen"]][0]
+    if info["fused"]:
+        assert chosen["n_cap"] == int(schedule.split(":")[1])
+        alg, exe = b.gemm_work()
+        assert exe >= alg > 0
     b.run(2)
     b.sync()
     for i, (s, r) in enumerate(zip(states, ref)):
