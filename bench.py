@@ -644,6 +644,10 @@ def run_serve(a):
                    "warmup": f"{len(warm)} one-step requests (one per operator and tier) in {warm_s:.1f} s, "
                              "then the counters restart"},
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"]},
+        "tiers": {name: {"completed": st["tier_completed"][k], "dof_steps": st["tier_dof_steps"][k],
+                         "p50_ms": st["tier_p50_ms"][k], "p99_ms": st["tier_p99_ms"][k],
+                         "dof_steps_per_s": st["tier_dof_steps"][k] / span if span > 0 else None}
+                  for k, name in enumerate(("1e-6 (split where eligible)", "1e-10 (FP64)"))},
         "requests": {k: st[k] for k in ("submitted", "admitted", "completed", "failed", "queued", "active")},
         "contexts": {"hits": st["ctx_hits"], "misses": st["ctx_misses"], "adopted_propagators": st["ctx_adopted"]},
         "worker_s": {"admit": st["worker_admit_s"], "issue": st["worker_issue_s"], "build": st["worker_build_s"],

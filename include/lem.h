@@ -386,10 +386,21 @@ typedef struct {
   double worker_build_s;        /* of worker_admit_s: building the first propagator of each operator */
   int64_t ctx_built;            /* contexts that built at admission (first of their operator) */
   int64_t adopt_failed;         /* contexts whose operator had a donor that did not match */
+  /* per tier: [0] tol >= 1e-6 (the split tier where the problem allows it), [1] tol < 1e-6 */
+  int64_t tier_completed[2], tier_dof_steps[2];
+  double tier_p50_ms[2], tier_p99_ms[2];
 } lem_server_stats;
 
 /* Create a server on `device` with a device-memory budget in bytes (states, scratch and cached
- * propagators; 0 = 80 GiB). Starts one worker thread. Errors: LEM_EINVAL, LEM_ECUDA. */
+ * propagators; 0 = 80 GiB). Starts one worker thread. Requests with tol >= 1e-6 run on the
+ * tensor-core split tier where their problem allows it (2D periodic, one shared propagator)
+ * and keep their state in float-float on the device until they complete, so each result is
+ * the same bit for bit as one lem_step call of all its steps; the others run the FP64 path.
+ * The tiers queue separately, each in arrival order: the split tier is admitted first, the
+ * FP64 tier while fewer than 8 of its requests run and within three quarters of the budget.
+ * Split-tier contexts get the device's highest stream priority, FP64-tier ones its lowest, and
+ * FP64-tier steps are issued only while no split-tier request has work on the GPU or waits
+ * for admission (else one FP64-tier chunk every 50 ms). Errors: LEM_EINVAL, LEM_ECUDA. */
 lem_status lem_server_create(size_t hbm_budget_bytes, int device, lem_server** out);
 
 /* Queue a request to advance the host state h_state (FP64, row-major, in/out; it must stay

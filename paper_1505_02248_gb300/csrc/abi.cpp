@@ -35,7 +35,9 @@ lem_status dev_alloc(lem_ctx* ctx, void** p, size_t bytes) {
   *p = nullptr;
   if (fault_alloc()) return fail(LEM_ENOMEM, "device allocation refused (LEM_FAULT=alloc)");
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  // stream-ordered: a context made or freed while other streams run (the server) must not
+  // wait for the whole device, as cudaMalloc / cudaFree may
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -95,20 +97,20 @@ void free_ctx(lem_ctx* c) {
   split_destroy(c);
   band_destroy(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  cudaFree(c->d_coef);
-  cudaFree(c->d_tiles);
-  cudaFree(c->d_class_order);
-  cudaFree(c->d_P);
-  cudaFree(c->d_P32);
-  cudaFree(c->d_P3);
-  cudaFree(c->d_P3_32);
-  cudaFree(c->d_um);
-  cudaFree(c->d_u0);
-  cudaFree(c->d_r);
-  cudaFree(c->d_U);
-  cudaFree(c->d_Y);
-  cudaFree(c->d_state_tmp);
-  cudaFree(c->d_status);
+  cudaFreeAsync(c->d_coef, c->stream);
+  cudaFreeAsync(c->d_tiles, c->stream);
+  cudaFreeAsync(c->d_class_order, c->stream);
+  cudaFreeAsync(c->d_P, c->stream);
+  cudaFreeAsync(c->d_P32, c->stream);
+  cudaFreeAsync(c->d_P3, c->stream);
+  cudaFreeAsync(c->d_P3_32, c->stream);
+  cudaFreeAsync(c->d_um, c->stream);
+  cudaFreeAsync(c->d_u0, c->stream);
+  cudaFreeAsync(c->d_r, c->stream);
+  cudaFreeAsync(c->d_U, c->stream);
+  cudaFreeAsync(c->d_Y, c->stream);
+  cudaFreeAsync(c->d_state_tmp, c->stream);
+  cudaFreeAsync(c->d_status, c->stream);
   delete c;
 }
 
@@ -250,10 +252,13 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
   if (s == LEM_OK) s = dev_alloc(c, reinterpret_cast<void**>(&c->d_status), sizeof(int));
   if (s != LEM_OK) { free_ctx(c); return s; }
   if (!desc->coef_stride) c->h_coef = hc;
-  e = cudaMemcpy(c->d_coef, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * nt, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->d_class_order, c->class_order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  e = cudaMemcpyAsync(c->d_coef, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_class_order, c->class_order.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "lem_create upload"); }
   // apply path: tensor-core split for a shared propagator, else a batched GEMV when tiles
   // have (mostly) their own propagators or FP32 propagators are asked for, else grouped GEMMs
@@ -278,6 +283,10 @@ lem_status lem_create(const lem_problem_desc* desc, int device, void* cuda_strea
     if (s != LEM_OK) { free_ctx(c); return s; }
   }
   c->apply_path_dense = c->apply_path;
+  // the context's memory is ready for use from any stream once its stream has run the
+  // allocations, uploads and clears above
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "lem_create"); }
   *out = c;
   return LEM_OK;
 }

@@ -366,9 +366,12 @@ __global__ void copy_cols_kernel(double* dst, int64_t ldd, int dcol0, const doub
   dst[int64_t(b) * n * ldd + int64_t(i) * ldd + dcol0 + j] = src[int64_t(b) * n * lds + int64_t(i) * lds + scol0 + j];
 }
 
+// Builder scratch from cudaMallocAsync. It is freed after the build has synchronised its
+// stream, on the legacy stream: that waits for no non-blocking stream, where cudaFree would
+// wait for the whole device.
 struct Buf {
   double* p = nullptr;
-  ~Buf() { if (p) cudaFree(p); }
+  ~Buf() { if (p) cudaFreeAsync(p, 0); }
 };
 
 inline dim3 grid1(int64_t total, int by) { return dim3(unsigned((total + 255) / 256), by); }

@@ -153,6 +153,12 @@ lem_status gemv_set_smem(lem_ctx* ctx);
 // step_split.cu
 lem_status split_prepare(lem_ctx* ctx);
 lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
+// the steps of split_step on a resident float-float state, with the residual scale carried
+// across calls through d_carry (one unsigned on the device; carry_in: it holds the previous
+// step's max|r|), and the conversions split_step does around them
+lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in);
+lem_status split_to_ff(lem_ctx* ctx, const double* d_u, float* uh, float* ul);
+lem_status split_from_ff(lem_ctx* ctx, const float* uh, const float* ul, double* d_u);
 void split_destroy(lem_ctx* ctx);
 lem_status split_check_error(lem_ctx* ctx);
 bool split_eligible(const lem_ctx* ctx);

@@ -2,13 +2,24 @@
 // (lem_server_create / lem_submit / lem_poll / lem_wait / lem_server_get_stats /
 // lem_server_destroy, declared in include/lem.h).
 //
-// One worker thread owns the device work. Each iteration it admits queued requests in
-// arrival order while their device memory fits the budget, then gives every admitted
-// request that is not waiting on the GPU its next chunk of LEM steps (a lem_step call on the
-// stream of the request's context) and checks finished chunks with events. A request whose
-// steps are done gets its state copied back and completes. New requests therefore join the
-// running set between chunks, and requests on different contexts run on different streams,
-// so their kernels overlap on the device.
+// One worker thread owns the device work. Each iteration it admits queued requests while
+// their device memory fits the budget, then gives every admitted request that is not waiting
+// on the GPU its next chunk of LEM steps (on the stream of the request's context) and checks
+// finished chunks with events. A request whose steps are done gets its state copied back and
+// completes. New requests therefore join the running set between chunks, and requests on
+// different contexts run on different streams, so their kernels overlap on the device.
+//
+// Tiers. Requests with tol >= 1e-6 run on the tensor-core split tier where their problem
+// allows it, the others on the FP64 path. The two tiers queue separately, each in arrival
+// order: split-tier requests are admitted first; FP64-tier requests only while fewer than
+// kMaxFp64Active of them run and the budget keeps a quarter free for the split tier. Streams
+// of split-tier contexts have the device's highest priority and FP64-tier ones its lowest,
+// and FP64-tier chunks are issued only while the split tier has nothing on the GPU (or one
+// every kFp64GapMs), so long FP64 kernels do not hold back the quick tier.
+//
+// A split-tier request keeps its state in float-float on the device from admission to
+// completion, with the residual scale carried from chunk to chunk, so its result is the same
+// bit for bit as one lem_step call of all its steps, whatever else runs.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -30,6 +41,9 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kChunk = 4;                       // LEM steps per scheduling quantum
 constexpr size_t kDefaultBudget = size_t(80) << 30;
+constexpr int kMaxFp64Active = 8;               // FP64-tier requests running at once
+constexpr double kFp64GapMs = 50.0;             // FP64-tier chunk spacing while the split tier is busy
+constexpr double kAdmitMs = 2.0;                // admission work per worker iteration
 
 enum class RS { Queued, Running, CopyBack, Done, Failed };
 
@@ -54,7 +68,16 @@ struct Request {
   RS state = RS::Queued;
   lem_status status = LEM_OK;
   double* d_state = nullptr;
-  double* h_stage = nullptr;  // pinned staging copy of the state (asynchronous transfers)
+  // split tier: the float-float state (npts + npts floats) and the carried residual scale
+  // (one unsigned after them), resident from admission to completion
+  float* d_ff = nullptr;
+  bool fp64_tier = false;     // tol < 1e-6
+  bool counted_fp64 = false;  // counts against kMaxFp64Active
+  int64_t acc_bytes = 0;      // bytes counted against the budget while admitted
+  // pinned staging copy of the state for the asynchronous transfers: held from admission until
+  // the copy in has completed, and again from the copy back until completion, so that the
+  // pinned memory in use follows the transfers in flight, not the requests admitted
+  double* h_stage = nullptr;
   size_t stage_bytes = 0;
   CachedCtx* cc = nullptr;
   cudaEvent_t ev = nullptr;
@@ -96,7 +119,10 @@ struct lem_server {
   int64_t budget = 0;
   std::mutex mu;
   std::map<uint64_t, std::shared_ptr<Request>> all;
-  std::deque<std::shared_ptr<Request>> queue;
+  std::deque<std::shared_ptr<Request>> queue;    // split tier (tol >= 1e-6)
+  std::deque<std::shared_ptr<Request>> queue64;  // FP64 tier
+  int fp64_active = 0;                           // worker-owned
+  Clock::time_point last_fp64_issue{};           // worker-owned
   std::vector<std::shared_ptr<Request>> active;  // worker-owned
   std::map<std::string, std::unique_ptr<CachedCtx>> cache;
   // pinned host buffers by size class (powers of two), reused across requests: transfers from
@@ -116,6 +142,8 @@ struct lem_server {
   double build_s = 0.0;                  // of admit_s: building donor propagators
   int64_t ctx_built = 0, adopt_failed = 0;
   std::vector<double> lat_ms;
+  std::vector<double> lat_tier[2];
+  int64_t tier_completed[2] = {0, 0}, tier_dof[2] = {0, 0};
   bool any_admitted = false;
   Clock::time_point t_first_admit, t_last_done;
 };
@@ -123,6 +151,28 @@ struct lem_server {
 namespace {
 
 constexpr int64_t kStagePoolMax = int64_t(16) << 30;  // pinned bytes kept for reuse
+
+// Host copy between a caller's state and a pinned staging buffer: large states are split over
+// several threads (a single core copies about 10 GB/s, and the worker does one copy per
+// request in each direction).
+void pmemcpy(void* dst, const void* src, size_t bytes) {
+  constexpr size_t kPart = size_t(4) << 20;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t parts = std::min<size_t>(std::min<size_t>(8, hw), (bytes + kPart - 1) / kPart);
+  if (parts <= 1) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  const size_t chunk = (bytes + parts - 1) / parts;
+  std::vector<std::thread> th;
+  for (size_t k = 1; k < parts; ++k) {
+    const size_t o = k * chunk;
+    if (o >= bytes) break;
+    th.emplace_back([=] { std::memcpy(static_cast<char*>(dst) + o, static_cast<const char*>(src) + o, std::min(chunk, bytes - o)); });
+  }
+  std::memcpy(dst, src, std::min(chunk, bytes));
+  for (auto& t : th) t.join();
+}
 
 void* stage_get(lem_server* s, size_t bytes, size_t* cls) {
   size_t c = 4096;
@@ -160,15 +210,23 @@ void finish(lem_server* s, const std::shared_ptr<Request>& r, lem_status st) {
     cudaFreeAsync(r->d_state, r->cc ? r->cc->stream : nullptr);
     r->d_state = nullptr;
   }
+  if (r->d_ff) {
+    cudaFreeAsync(r->d_ff, r->cc ? r->cc->stream : nullptr);
+    r->d_ff = nullptr;
+  }
   if (r->h_stage) {
-    if (st == LEM_OK) std::memcpy(r->h_state, r->h_stage, sizeof(double) * size_t(r->npts));
+    if (st == LEM_OK) pmemcpy(r->h_state, r->h_stage, sizeof(double) * size_t(r->npts));
     stage_put(s, r->h_stage, r->stage_bytes);  // worker thread only
     r->h_stage = nullptr;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (r->accounted) {
-    s->used -= int64_t(sizeof(double)) * r->npts;
+    s->used -= r->acc_bytes;
     r->accounted = false;
+  }
+  if (r->counted_fp64) {
+    s->fp64_active--;
+    r->counted_fp64 = false;
   }
   if (r->cc) {
     r->cc->users--;
@@ -182,6 +240,10 @@ void finish(lem_server* s, const std::shared_ptr<Request>& r, lem_status st) {
     s->completed++;
     s->dof_steps += r->npts * r->nsteps;
     s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    const int tier = r->fp64_tier ? 1 : 0;
+    s->lat_tier[tier].push_back(s->lat_ms.back());
+    s->tier_completed[tier]++;
+    s->tier_dof[tier] += r->npts * r->nsteps;
     s->t_last_done = r->t_done;
   } else {
     r->state = RS::Failed;
@@ -205,10 +267,49 @@ int64_t ctx_bytes_estimate(const lem_problem_desc& d, int64_t* scratch) {
   return b;
 }
 
-// Admit r if its state (and a new context, when it needs one) fits the budget. Returns
-// false if r must keep waiting; fails r (and returns true) when it can never run.
-bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
-  const int64_t sbytes = int64_t(sizeof(double)) * r->npts;
+// Evict idle contexts (no request on them), least recently used first and contexts that lend
+// their propagators to later ones last, until `bytes` more fit within `cap` or nothing idle is
+// left; `spare` is never evicted. Call with s->mu held.
+void make_room(lem_server* s, int64_t bytes, int64_t cap, const CachedCtx* spare) {
+  auto is_donor = [&](const lem_ctx* c) {
+    for (auto& kv : s->donors)
+      if (kv.second.first == c) return true;
+    return false;
+  };
+  while (s->used + bytes > cap) {
+    auto victim = s->cache.end();
+    bool victim_donor = true;
+    for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
+      if (it->second->users != 0 || it->second.get() == spare) continue;
+      const bool dn = is_donor(it->second->ctx);
+      if (victim == s->cache.end() || (victim_donor && !dn) ||
+          (victim_donor == dn && it->second->last_use < victim->second->last_use)) {
+        victim = it;
+        victim_donor = dn;
+      }
+    }
+    if (victim == s->cache.end()) break;
+    for (auto d = s->donors.begin(); d != s->donors.end();) {
+      if (d->second.first == victim->second->ctx) {
+        cudaEventDestroy(d->second.second);
+        d = s->donors.erase(d);
+      } else {
+        ++d;
+      }
+    }
+    lem_destroy(victim->second->ctx);
+    cudaStreamDestroy(victim->second->stream);
+    s->used -= victim->second->bytes;
+    s->cache.erase(victim);
+  }
+}
+
+// Admit r if its state (and a new context, when it needs one) fits within `cap` bytes of the
+// budget. Returns false if r must keep waiting; fails r (and returns true) when it can never
+// run. A split-tier request also holds a float-float copy of its state (8 more bytes a node).
+bool try_admit(lem_server* s, const std::shared_ptr<Request>& r, int64_t cap) {
+  const bool want_split = r->tol >= 1e-6;
+  const int64_t sbytes = int64_t(sizeof(double)) * r->npts * (want_split ? 2 : 1) + (want_split ? 256 : 0);
   {
     // host-side fault injection for tests: LEM_FAULT=admit refuses every admission
     const char* f = std::getenv("LEM_FAULT");
@@ -220,7 +321,6 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
   }
   lem_problem_desc d = r->desc;
   for (int k = 0; k < 5; ++k) d.coef[k] = r->coef[k].empty() ? nullptr : r->coef[k].data();
-  const bool want_split = r->tol >= 1e-6;
   CachedCtx* cc = nullptr;
   for (int attempt = want_split ? 0 : 1; attempt < 2 && !cc; ++attempt) {
     d.prec = attempt == 0 ? LEM_PREC_SPLIT : LEM_PREC_FP64;
@@ -229,7 +329,8 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
       std::lock_guard<std::mutex> lk(s->mu);
       auto it = s->cache.find(key);
       if (it != s->cache.end()) {
-        if (s->used + sbytes > s->budget) return false;
+        make_room(s, sbytes, cap, it->second.get());  // idle contexts make way for this state
+        if (s->used + sbytes > cap) return false;
         cc = it->second.get();
         s->ctx_hits++;
         break;
@@ -259,43 +360,16 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      // evict idle contexts, least recently used first (contexts that lend their propagators
-      // to later ones last), until the new one fits
-      auto is_donor = [&](const lem_ctx* c) {
-        for (auto& kv : s->donors)
-          if (kv.second.first == c) return true;
-        return false;
-      };
-      while (s->used + need + sbytes > s->budget) {
-        auto victim = s->cache.end();
-        bool victim_donor = true;
-        for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
-          if (it->second->users != 0) continue;
-          const bool dn = is_donor(it->second->ctx);
-          if (victim == s->cache.end() || (victim_donor && !dn) ||
-              (victim_donor == dn && it->second->last_use < victim->second->last_use)) {
-            victim = it;
-            victim_donor = dn;
-          }
-        }
-        if (victim == s->cache.end()) break;
-        for (auto d = s->donors.begin(); d != s->donors.end();) {
-          if (d->second.first == victim->second->ctx) {
-            cudaEventDestroy(d->second.second);
-            d = s->donors.erase(d);
-          } else {
-            ++d;
-          }
-        }
-        lem_destroy(victim->second->ctx);
-        cudaStreamDestroy(victim->second->stream);
-        s->used -= victim->second->bytes;
-        s->cache.erase(victim);
-      }
-      if (s->used + need + sbytes > s->budget) return false;  // wait for running requests
+      make_room(s, need + sbytes, cap, nullptr);
+      if (s->used + need + sbytes > cap) return false;  // wait for running requests
     }
     auto c = std::make_unique<CachedCtx>();
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+      cudaGetLastError();
+      least = greatest = 0;
+    }
+    if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, want_split ? greatest : least) != cudaSuccess) {
       cudaGetLastError();
       finish(s, r, LEM_ECUDA);
       return true;
@@ -360,21 +434,41 @@ bool try_admit(lem_server* s, const std::shared_ptr<Request>& r) {
     finish(s, r, LEM_ECUDA);
     return true;
   }
-  r->h_stage = static_cast<double*>(stage_get(s, size_t(sbytes), &r->stage_bytes));
+  r->h_stage = static_cast<double*>(stage_get(s, sizeof(double) * size_t(r->npts), &r->stage_bytes));
   if (!r->h_stage) {
     finish(s, r, LEM_ENOMEM);
     return true;
   }
-  std::memcpy(r->h_stage, r->h_state, size_t(sbytes));
-  cudaMemcpyAsync(r->d_state, r->h_stage, size_t(sbytes), cudaMemcpyHostToDevice, cc->stream);
+  const size_t fbytes = sizeof(double) * size_t(r->npts);
+  pmemcpy(r->h_stage, r->h_state, fbytes);
+  cudaMemcpyAsync(r->d_state, r->h_stage, fbytes, cudaMemcpyHostToDevice, cc->stream);
+  if (cc->ctx->apply_path == LEM_APPLY_TC_SPLIT) {
+    // resident float-float state + carried scale for the split tier
+    if (cudaMallocAsync(reinterpret_cast<void**>(&r->d_ff), fbytes + 256, cc->stream) != cudaSuccess) {
+      cudaGetLastError();
+      r->d_ff = nullptr;
+      finish(s, r, LEM_ENOMEM);
+      return true;
+    }
+    const lem_status cs = lem::split_to_ff(cc->ctx, r->d_state, r->d_ff, r->d_ff + r->npts);
+    if (cs != LEM_OK) {
+      finish(s, r, cs);
+      return true;
+    }
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   s->used += sbytes;
+  r->acc_bytes = sbytes;
   r->accounted = true;
   cc->users++;
   cc->last_use = ++s->tick;
   r->cc = cc;
   r->state = RS::Running;
   r->remaining = r->nsteps;
+  if (r->fp64_tier) {
+    r->counted_fp64 = true;
+    s->fp64_active++;
+  }
   s->admitted++;
   if (!s->any_admitted) {
     s->any_admitted = true;
@@ -387,37 +481,81 @@ void worker_loop(lem_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
     bool progress = false;
-    // admission in arrival order
-    for (;;) {
-      std::shared_ptr<Request> r;
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (s->queue.empty()) break;
-        r = s->queue.front();
+    // admission: the split tier first, then the FP64 tier (each in arrival order; FP64-tier
+    // requests only while fewer than kMaxFp64Active run, within three quarters of the budget)
+    // (at most kAdmitMs of admission work per iteration, so that a burst of arrivals does not
+    // keep the worker from issuing the running requests' next steps)
+    const auto t_adm = Clock::now();
+    for (int tier = 0; tier < 2; ++tier) {
+      for (;;) {
+        if (tier == 1 && s->fp64_active >= kMaxFp64Active) break;
+        if (std::chrono::duration<double, std::milli>(Clock::now() - t_adm).count() > kAdmitMs) break;
+        std::shared_ptr<Request> r;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          std::deque<std::shared_ptr<Request>>& q = tier == 0 ? s->queue : s->queue64;
+          if (q.empty()) break;
+          r = q.front();
+        }
+        const auto ta = Clock::now();
+        const bool admitted = try_admit(s, r, tier == 0 ? s->budget : s->budget - s->budget / 4);
+        s->admit_s += std::chrono::duration<double>(Clock::now() - ta).count();
+        if (!admitted) break;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          (tier == 0 ? s->queue : s->queue64).pop_front();
+        }
+        if (r->state == RS::Running) s->active.push_back(r);
+        progress = true;
       }
-      const auto ta = Clock::now();
-      const bool admitted = try_admit(s, r);
-      s->admit_s += std::chrono::duration<double>(Clock::now() - ta).count();
-      if (!admitted) break;
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->queue.pop_front();
-      }
-      if (r->state == RS::Running) s->active.push_back(r);
-      progress = true;
     }
-    // issue and retire chunks
+    // issue and retire chunks. FP64-tier steps are issued only while no split-tier request
+    // has work on the GPU or waits for admission (a long FP64 kernel holds SMs that the
+    // tensor-core kernels need whole), or at most every kFp64GapMs when the split tier never
+    // pauses, so that the FP64 tier still advances.
+    bool quick_busy = false;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      quick_busy = !s->queue.empty();
+    }
+    for (auto& r : s->active)
+      if (!r->fp64_tier && (r->in_flight || r->state == RS::Running)) quick_busy = true;
+    const auto now = Clock::now();
+    bool fp64_ok = !quick_busy ||
+                   std::chrono::duration<double, std::milli>(now - s->last_fp64_issue).count() >= kFp64GapMs;
     for (auto& r : s->active) {
       if (r->state != RS::Running && r->state != RS::CopyBack) continue;
       if (!r->in_flight) {
+        if (r->fp64_tier && r->state == RS::Running && r->remaining > 0) {
+          if (!fp64_ok) continue;
+          if (quick_busy) fp64_ok = false;  // one FP64 chunk per gap
+          s->last_fp64_issue = now;
+        }
         if (r->state == RS::Running && r->remaining == 0) {
+          if (r->d_ff) {
+            const lem_status cs = lem::split_from_ff(r->cc->ctx, r->d_ff, r->d_ff + r->npts, r->d_state);
+            if (cs != LEM_OK) { finish(s, r, cs); progress = true; continue; }
+          }
+          if (!r->h_stage) r->h_stage = static_cast<double*>(stage_get(s, sizeof(double) * size_t(r->npts), &r->stage_bytes));
+          if (!r->h_stage) { finish(s, r, LEM_ENOMEM); progress = true; continue; }
           cudaMemcpyAsync(r->h_stage, r->d_state, sizeof(double) * size_t(r->npts), cudaMemcpyDeviceToHost,
                           r->cc->stream);
           r->state = RS::CopyBack;
         } else {
-          const int chunk = std::min(r->remaining, kChunk);
+          // FP64-tier requests advance one step per chunk: their steps are long, and shorter
+          // chunks interleave better with the split tier
+          const int chunk = std::min(r->remaining, r->fp64_tier ? 1 : kChunk);
           const auto ti = Clock::now();
-          lem_status st = lem_step(r->cc->ctx, r->d_state, chunk);
+          lem_status st = LEM_OK;
+          if (r->d_ff) {  // resident float-float state; the scale carries over from the last chunk
+            lem_ctx* c = r->cc->ctx;
+            if (!c->built) st = lem_build_propagators(c, nullptr);
+            if (st == LEM_OK)
+              st = lem::split_run(c, r->d_ff, r->d_ff + r->npts, chunk, reinterpret_cast<unsigned*>(r->d_ff + 2 * r->npts),
+                                  r->remaining < r->nsteps);
+          } else {
+            st = lem_step(r->cc->ctx, r->d_state, chunk);
+          }
           s->issue_s += std::chrono::duration<double>(Clock::now() - ti).count();
           if (st != LEM_OK) { finish(s, r, st); progress = true; continue; }
           r->pending = chunk;
@@ -437,6 +575,10 @@ void worker_loop(lem_server* s) {
       } else {
         r->remaining -= r->pending;
         r->pending = 0;
+        if (r->h_stage) {  // the copy in ran before this chunk: its staging buffer is free again
+          stage_put(s, r->h_stage, r->stage_bytes);
+          r->h_stage = nullptr;
+        }
       }
     }
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(),
@@ -447,8 +589,10 @@ void worker_loop(lem_server* s) {
     if (s->stop.load()) {
       std::lock_guard<std::mutex> lk(s->mu);
       if (s->active.empty()) {
-        for (auto& r : s->queue) { r->state = RS::Failed; r->status = LEM_EBUSY; s->failed++; }
-        s->queue.clear();
+        for (auto* q : {&s->queue, &s->queue64}) {
+          for (auto& r : *q) { r->state = RS::Failed; r->status = LEM_EBUSY; s->failed++; }
+          q->clear();
+        }
         break;
       }
     }
@@ -505,6 +649,7 @@ lem_status lem_submit(lem_server* s, const lem_problem_desc* desc, double tol, d
   r->key = make_key(r->desc, r->coef);
   r->op_key = make_key(r->desc, r->coef, false);
   r->tol = tol;
+  r->fp64_tier = !(tol >= 1e-6);
   r->h_state = h_state;
   r->npts = npts;
   r->nsteps = nsteps;
@@ -512,7 +657,7 @@ lem_status lem_submit(lem_server* s, const lem_problem_desc* desc, double tol, d
   std::lock_guard<std::mutex> lk(s->mu);
   r->id = s->next_id++;
   s->all[r->id] = r;
-  s->queue.push_back(r);
+  (r->fp64_tier ? s->queue64 : s->queue).push_back(r);
   s->submitted++;
   *ticket = r->id;
   return LEM_OK;
@@ -548,6 +693,10 @@ lem_status lem_server_reset_stats(lem_server* s) {
   s->ctx_hits = s->ctx_misses = s->ctx_adopted = s->ctx_built = s->adopt_failed = 0;
   s->admit_s = s->issue_s = s->build_s = 0.0;
   s->lat_ms.clear();
+  for (int t = 0; t < 2; ++t) {
+    s->lat_tier[t].clear();
+    s->tier_completed[t] = s->tier_dof[t] = 0;
+  }
   s->any_admitted = false;
   return LEM_OK;
 }
@@ -559,21 +708,26 @@ lem_status lem_server_get_stats(lem_server* s, lem_server_stats* o) {
   o->admitted = s->admitted;
   o->completed = s->completed;
   o->failed = s->failed;
-  o->queued = int64_t(s->queue.size());
+  o->queued = int64_t(s->queue.size() + s->queue64.size());
   int64_t act = 0;
   for (auto& kv : s->all)
     if (kv.second->state == RS::Running || kv.second->state == RS::CopyBack) ++act;
   o->active = act;
   o->dof_steps = s->dof_steps;
-  std::vector<double> l = s->lat_ms;
-  std::sort(l.begin(), l.end());
-  auto pct = [&](double p) {
+  auto pct = [](std::vector<double> l, double p) {
     if (l.empty()) return 0.0;
+    std::sort(l.begin(), l.end());
     const size_t i = std::min(l.size() - 1, size_t(std::ceil(p * double(l.size()))) - (p > 0 ? 1 : 0));
     return l[i];
   };
-  o->p50_ms = pct(0.50);
-  o->p99_ms = pct(0.99);
+  o->p50_ms = pct(s->lat_ms, 0.50);
+  o->p99_ms = pct(s->lat_ms, 0.99);
+  for (int t = 0; t < 2; ++t) {
+    o->tier_completed[t] = s->tier_completed[t];
+    o->tier_dof_steps[t] = s->tier_dof[t];
+    o->tier_p50_ms[t] = pct(s->lat_tier[t], 0.50);
+    o->tier_p99_ms[t] = pct(s->lat_tier[t], 0.99);
+  }
   o->first_admit_to_last_done_s =
       s->any_admitted && s->completed ? std::chrono::duration<double>(s->t_last_done - s->t_first_admit).count() : 0.0;
   o->device_bytes = s->used;

@@ -459,10 +459,9 @@ struct BandPlan {
 void band_destroy(lem_ctx* ctx) {
   BandPlan* b = ctx->band;
   if (!b) return;
-  cudaFree(b->d_cls);
-  cudaFree(b->d_ext);
-  cudaFree(b->d_Pb);
-  cudaFree(b->d_Pb32);
+  for (void* p : {static_cast<void*>(b->d_cls), static_cast<void*>(b->d_ext), static_cast<void*>(b->d_Pb),
+                  static_cast<void*>(b->d_Pb32)})
+    if (p) cudaFreeAsync(p, ctx->stream);
   delete b;
   ctx->band = nullptr;
 }
@@ -516,8 +515,8 @@ lem_status band_prepare(lem_ctx* ctx) {
   }
   const bool f32 = ctx->apply_path == LEM_APPLY_F32_BAND;
   if (total > b->cap) {
-    cudaFree(b->d_Pb);
-    cudaFree(b->d_Pb32);
+    if (b->d_Pb) cudaFreeAsync(b->d_Pb, st);
+    if (b->d_Pb32) cudaFreeAsync(b->d_Pb32, st);
     b->d_Pb = nullptr;
     b->d_Pb32 = nullptr;
     b->cap = 0;

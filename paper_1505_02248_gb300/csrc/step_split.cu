@@ -939,8 +939,8 @@ lem_status split_prepare(lem_ctx* ctx) {
   if (sp->np == 3) {
     LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R3), rbytes));
     LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P3), pbytes));
-    LEM_CUDA_TRY(cudaMemset(sp->d_R3, 0, rbytes));
-    LEM_CUDA_TRY(cudaMemset(sp->d_P3, 0, pbytes));
+    LEM_CUDA_TRY(cudaMemsetAsync(sp->d_R3, 0, rbytes, ctx->stream));
+    LEM_CUDA_TRY(cudaMemsetAsync(sp->d_P3, 0, pbytes, ctx->stream));
   }
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_eP), sizeof(int) * sp->M));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_S), sizeof(double) * sp->M));
@@ -949,11 +949,11 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_err), sizeof(int)));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_rb), sizeof(int)));
   sp->rp.rb = sp->d_rb;
-  LEM_CUDA_TRY(cudaMemset(sp->d_Pint, 0, pbytes));
-  LEM_CUDA_TRY(cudaMemset(sp->d_P2, 0, pbytes));
-  LEM_CUDA_TRY(cudaMemset(sp->d_Rint, 0, rbytes));
-  LEM_CUDA_TRY(cudaMemset(sp->d_R2, 0, rbytes));
-  LEM_CUDA_TRY(cudaMemset(sp->d_err, 0, sizeof(int)));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_Pint, 0, pbytes, ctx->stream));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_P2, 0, pbytes, ctx->stream));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_Rint, 0, rbytes, ctx->stream));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_R2, 0, rbytes, ctx->stream));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), ctx->stream));
   LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(sp->bn, sp->np), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     SMEM_BYTES));
   LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(sp->bn, sp->np, true),
@@ -1011,40 +1011,71 @@ static lem_status split_pack(lem_ctx* ctx) {
   return LEM_OK;
 }
 
-lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
+// nsteps LEM steps on a float-float state (uh, ul) already on the device. The scale of each
+// step's residual pieces comes from the previous step's max|r|; the first step of a run takes
+// its own (a measuring pass) unless carry_in, in which case d_carry holds the previous step's
+// max|r| from an earlier run on the same state. With d_carry, the last step's max|r| is left
+// there, so a run split into several calls gives the same result bit for bit as one call.
+lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
   if (sp->packed_gen != ctx->build_gen) LEM_TRY(split_pack(ctx));
-  const int64_t npts = ctx->npts;
-  f64_to_ff_kernel<<<1024, 256, 0, st>>>(d_u, sp->d_uh, sp->d_ul, npts);
-  LEM_CUDA_TRY(cudaGetLastError());
-  // measure max|r| of the first step into rmax[0] (the measuring pass reads rmax[1] only
-  // to form a scale it never uses)
-  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
   const dim3 rgrid((int(ctx->nx) + 2 * sp->Hx + RTX - 1) / RTX, (sp->prow + RTY - 1) / RTY);
-  residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
-                                               sp->d_rmax, sp->d_escale, 1, 1);
-  LEM_CUDA_TRY(cudaGetLastError());
-  const GemmGeom& g = sp->prob.g;
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
+  if (carry_in && d_carry) {
+    LEM_CUDA_TRY(cudaMemcpyAsync(sp->d_rmax, d_carry, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  } else {
+    // measure max|r| of the first step into rmax[0] (the measuring pass reads rmax[1] only
+    // to form a scale it never uses)
+    residual_split_kernel<<<rgrid, 256, 0, st>>>(uh, ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp, sp->d_rmax,
+                                                 sp->d_escale, 1, 1);
+    LEM_CUDA_TRY(cudaGetLastError());
+  }
+  SplitProblem prob = sp->prob;  // the GEMM's epilogue adds into this state
+  prob.g.uh = uh;
+  prob.g.ul = ul;
   cudaLaunchConfig_t cfg{};
   cfg.blockDim = dim3(gemm_threads(sp->np));
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
-  cfg.gridDim = dim3(std::min(g.nMB * g.nNB, sp->nsm));
+  cfg.gridDim = dim3(std::min(prob.g.nMB * prob.g.nNB, sp->nsm));
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
-    residual_split_kernel<<<rgrid, 256, 0, st>>>(sp->d_uh, sp->d_ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp,
-                                                 sp->d_rmax, sp->d_escale, parity, 0);
+    residual_split_kernel<<<rgrid, 256, 0, st>>>(uh, ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp, sp->d_rmax,
+                                                 sp->d_escale, parity, 0);
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
-    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->bn, sp->np), sp->prob,
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->bn, sp->np), prob,
                                     static_cast<const SplitProblem*>(nullptr), 1, 0, parity, sp->d_err));
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
-  ff_to_f64_kernel<<<1024, 256, 0, st>>>(sp->d_uh, sp->d_ul, d_u, npts);
+  // the last step (parity (nsteps - 1) & 1) accumulated its max|r| into rmax[nsteps & 1]
+  if (d_carry && nsteps > 0)
+    LEM_CUDA_TRY(cudaMemcpyAsync(d_carry, sp->d_rmax + (nsteps & 1), sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  return LEM_OK;
+}
+
+// FP64 state <-> float-float state on the context stream (every float-float state the split
+// kernels leave is normalised, |ul| <= ulp(uh) / 2, so the conversion to float-float of a value
+// they wrote returns the same pair).
+lem_status split_to_ff(lem_ctx* ctx, const double* d_u, float* uh, float* ul) {
+  f64_to_ff_kernel<<<1024, 256, 0, ctx->stream>>>(d_u, uh, ul, ctx->npts);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
+}
+
+lem_status split_from_ff(lem_ctx* ctx, const float* uh, const float* ul, double* d_u) {
+  ff_to_f64_kernel<<<1024, 256, 0, ctx->stream>>>(uh, ul, d_u, ctx->npts);
+  LEM_CUDA_TRY(cudaGetLastError());
+  return LEM_OK;
+}
+
+lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
+  SplitPlan* sp = ctx->split;
+  LEM_TRY(split_to_ff(ctx, d_u, sp->d_uh, sp->d_ul));
+  LEM_TRY(split_run(ctx, sp->d_uh, sp->d_ul, nsteps, nullptr, false));
+  return split_from_ff(ctx, sp->d_uh, sp->d_ul, d_u);
 }
 
 // ------------------------------------------------------------------ multi-problem steps
@@ -1251,10 +1282,12 @@ lem_status split_check_error(lem_ctx* ctx) {
 void split_destroy(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   if (!sp) return;
-  cudaFree(sp->d_uh); cudaFree(sp->d_ul); cudaFree(sp->d_Rint); cudaFree(sp->d_R2);
-  cudaFree(sp->d_Pint); cudaFree(sp->d_P2); cudaFree(sp->d_eP); cudaFree(sp->d_S);
-  cudaFree(sp->d_P3); cudaFree(sp->d_R3);
-  cudaFree(sp->d_rmax); cudaFree(sp->d_escale); cudaFree(sp->d_err); cudaFree(sp->d_rb);
+  for (void* p : {static_cast<void*>(sp->d_uh), static_cast<void*>(sp->d_ul), static_cast<void*>(sp->d_Rint),
+                  static_cast<void*>(sp->d_R2), static_cast<void*>(sp->d_Pint), static_cast<void*>(sp->d_P2),
+                  static_cast<void*>(sp->d_eP), static_cast<void*>(sp->d_S), static_cast<void*>(sp->d_P3),
+                  static_cast<void*>(sp->d_R3), static_cast<void*>(sp->d_rmax), static_cast<void*>(sp->d_escale),
+                  static_cast<void*>(sp->d_err), static_cast<void*>(sp->d_rb)})
+    if (p) cudaFreeAsync(p, ctx->stream);  // stream-ordered (the memory came from cudaMallocAsync)
   delete sp;
   ctx->split = nullptr;
 }

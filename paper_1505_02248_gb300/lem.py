@@ -72,6 +72,8 @@ class ServerStats(C.Structure):
         ("device_bytes", C.c_int64), ("ctx_hits", C.c_int64), ("ctx_misses", C.c_int64),
         ("ctx_adopted", C.c_int64), ("worker_admit_s", C.c_double), ("worker_issue_s", C.c_double),
         ("worker_build_s", C.c_double), ("ctx_built", C.c_int64), ("adopt_failed", C.c_int64),
+        ("tier_completed", C.c_int64 * 2), ("tier_dof_steps", C.c_int64 * 2),
+        ("tier_p50_ms", C.c_double * 2), ("tier_p99_ms", C.c_double * 2),
     ]
 
 
@@ -393,7 +395,11 @@ class Server:
     def stats(self) -> dict:
         st = ServerStats()
         check(self._lib.lem_server_get_stats(self._h, C.byref(st)), "lem_server_get_stats")
-        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+        out = {}
+        for f, _ in ServerStats._fields_:
+            v = getattr(st, f)
+            out[f] = list(v) if f.startswith("tier_") else v
+        return out
 
     def reset_stats(self):
         check(self._lib.lem_server_reset_stats(self._h), "lem_server_reset_stats")
