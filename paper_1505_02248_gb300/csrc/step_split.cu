@@ -309,6 +309,50 @@ __global__ void __launch_bounds__(256) residual_multi_kernel(const ResProblem* _
   residual_tile(q.uh, q.ul, q.Rint, q.R2, q.R3, q.p, q.rmax, q.escale, parity, measure, lb % q.gx, lb / q.gx);
 }
 
+// FP64 -> float-float: h = v rounded to the nearest float, l = v - h rounded to the nearest
+// float, the values the FP64 conversions give, built from the bits with integer operations (an
+// FP64 conversion issues on this part's slow FP64 pipe). Exponents outside [-70, 100] (zero
+// included) take the FP64 conversions.
+__device__ __forceinline__ void f64_to_pair(double v, float& h, float& l) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int E = int((b >> 52) & 0x7FFull) - 1023;
+  if (E < -70 || E > 100) {
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - double(h));
+    return;
+  }
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
+  unsigned long long q = m >> 29;                                          // 24 bits
+  const unsigned long long rem = m & ((1ull << 29) - 1);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (q & 1ull))) ++q;     // round to nearest even
+  const int diff = int(static_cast<long long>(m) - static_cast<long long>(q << 29));  // |diff| <= 2^28
+  int e = E;
+  if (q == (1ull << 24)) {  // rounded up to the next binade
+    q >>= 1;
+    ++e;
+  }
+  const unsigned sign = unsigned(b >> 63) << 31;
+  h = __uint_as_float(sign | (unsigned(e + 127) << 23) | unsigned(q & 0x7FFFFFull));
+  // v - h = sign * diff * 2^(E - 52), exact; its nearest float (+0 when it is 0, as in FP64)
+  const float lf = __int2float_rn(diff) * __int_as_float((E - 52 + 127) << 23);
+  l = diff == 0 ? 0.0f : __uint_as_float(__float_as_uint(lf) ^ sign);
+}
+
+// float -> double from the bits (exact); zeros keep their sign, subnormals, infinities and NaN
+// take the FP64 conversion
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned ex = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double(static_cast<long long>(static_cast<unsigned long long>(b >> 31) << 63));
+  if (ex == 0u || ex == 255u) return double(x);
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(b >> 31) << 63) |
+                                                     (static_cast<unsigned long long>(ex - 127u + 1023u) << 52) |
+                                                     (static_cast<unsigned long long>(b & 0x7FFFFFu) << 29)));
+}
+
+// float-float -> FP64: h + l rounded once (one FP64 add)
+__device__ __forceinline__ double pair_to_f64(float h, float l) { return f32_to_f64(h) + f32_to_f64(l); }
+
 // FP64 <-> float-float for every problem of a batch; to_ff also clears each max|r| pair.
 struct ConvProblem {
   double* u;
@@ -329,30 +373,30 @@ __global__ void __launch_bounds__(256) convert_multi_kernel(const ConvProblem* _
   if (to_ff) {
     if (b0 == 0 && threadIdx.x < 2) q.rmax[threadIdx.x] = 0u;
     for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
-      const double v = q.u[k];
-      const float h = __double2float_rn(v);
+      float h, l;
+      f64_to_pair(q.u[k], h, l);
       q.uh[k] = h;
-      q.ul[k] = __double2float_rn(v - double(h));
+      q.ul[k] = l;
     }
   } else {
-    for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) q.u[k] = double(q.uh[k]) + double(q.ul[k]);
+    for (int64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) q.u[k] = pair_to_f64(q.uh[k], q.ul[k]);
   }
 }
 
 __global__ void f64_to_ff_kernel(const double* __restrict__ u, float* __restrict__ uh,
                                  float* __restrict__ ul, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const double v = u[i];
-    const float h = __double2float_rn(v);
+    float h, l;
+    f64_to_pair(u[i], h, l);
     uh[i] = h;
-    ul[i] = __double2float_rn(v - double(h));
+    ul[i] = l;
   }
 }
 
 __global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __restrict__ ul,
                                  double* __restrict__ u, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    u[i] = double(uh[i]) + double(ul[i]);
+    u[i] = pair_to_f64(uh[i], ul[i]);
 }
 
 // Per owner row i of P (FP64, n_int x n_loc, window row-major): eP_i with
