@@ -11,9 +11,9 @@
 //     that). er comes from the previous step's max|r|.
 //  2. split_gemm_kernel: Y = P R (M = Ty*Tx owner rows, N = tiles, K = window nodes).
 //     P is stored per row i as P*2^eP_i = P_int + P2 with |P_int| <= 2^9 an integer.
-//     Each K block is one window row (Wx = 16, 32, 48 or 64 nodes, loaded as 128-byte
-//     swizzled rows of 64): TMA loads P_int/P2 and the 128 windows' rows of r_int/r2
-//     straight from the padded residual
+//     Each K block is one window row (Wx = 16, 32, 48 or 64 nodes: ceil(Wx / 16) * 16 columns
+//     loaded into 128-byte swizzled rows): TMA loads P_int/P2 and the 128 windows' rows of
+//     r_int/r2 straight from the padded residual
 //     through a 4D tensor map (the halo gather happens inside TMA). One thread issues
 //     tcgen05.mma: P_int r_int into the main TMEM accumulator and P_int r2, P2 r_int and
 //     P2 r2 into a correction accumulator. Because sum_k |P_int| |r_int| < 2^24
@@ -83,6 +83,7 @@ struct GemmGeom {
   int bnp;              // windows per block (BNx * BNy <= BN, a multiple of 16): the MMA's N
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int drain_rows;       // three pieces: window rows per correction drain
+  int kx;               // K columns loaded per window row: Wx rounded up to 16 (the MMA's K steps)
   int unit0;            // multi-problem launch: this problem's first unit
   int fault;            // test hook (LEM_FAULT=timeout): CTA 0 arms its first stage but loads
                         // nothing, so the MMA issuer's bounded wait expires
@@ -593,7 +594,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (s_abort) break;
           uint8_t* st = tiles + s * STAGE_BYTES;
           // the stage's bytes: NP P pieces and NP residual pieces of bnp window rows each
-          ptx::mbar_arrive_expect_tx(&full[s], uint32_t(NP) * uint32_t(A_BYTES + g.bnp * KB * 2));
+          // (TMA lands each row's kx columns at their places in the 128-byte swizzled row; the
+          // rest of the row is never read: the MMAs take ceil(Wx / 16) K steps of 16)
+          ptx::mbar_arrive_expect_tx(&full[s], uint32_t(NP) * uint32_t((BM + g.bnp) * g.kx * 2));
           if (g.fault && blockIdx.x == 0 && it == 0) {  // test hook: the bytes never arrive
             issued = it + 1;
             continue;
@@ -1011,10 +1014,13 @@ lem_status split_prepare(lem_ctx* ctx) {
     __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
     cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(Mpad)};
     cuuint64_t ps[1] = {cuuint64_t(sp->Wy) * KB * 2};
-    cuuint32_t pbox[2] = {KB, cuuint32_t(BM)};
+    // only the window row's used columns: kx = Wx rounded up to 16 (a 96-byte box for 48-wide
+    // windows lands at the same swizzled places as the first 48 columns of a 128-byte row)
+    const cuuint32_t kx = cuuint32_t((sp->Wx + 15) / 16 * 16);
+    cuuint32_t pbox[2] = {kx, cuuint32_t(BM)};
     cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
     cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
-    cuuint32_t rbox[4] = {KB, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
+    cuuint32_t rbox[4] = {kx, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
     for (int k = 0; k < 3; ++k) {
       LEM_TRY(encode_f16_map(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
       LEM_TRY(encode_f16_map(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
@@ -1026,7 +1032,8 @@ lem_status split_prepare(lem_ctx* ctx) {
   g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bnp = sp->bn;
   // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
   // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
-  g.drain_rows = std::max(1, 64 / (((sp->Wx + 15) / 16) * 16));
+  g.kx = (sp->Wx + 15) / 16 * 16;
+  g.drain_rows = std::max(1, 64 / g.kx);
   if (const char* e = std::getenv("LEM_SPLIT_DRAIN_ROWS")) g.drain_rows = std::max(1, std::atoi(e));  // tuning knob
   g.unit0 = 0;
   {
@@ -1168,7 +1175,8 @@ static int batch_block_width(const SplitPlan* sp, int cap) {
     int bx = 0, by = 0;
     group_tiles(sp->ntx, sp->nty, w, &bx, &by);
     const int64_t blocks = int64_t((sp->ntx + bx - 1) / bx) * ((sp->nty + by - 1) / by);
-    const int64_t cost = blocks * int64_t(sp->np) * (A_BYTES + int64_t(w) * KB * 2);
+    const int64_t kx = (sp->Wx + 15) / 16 * 16;
+    const int64_t cost = blocks * int64_t(sp->np) * (BM + int64_t(w)) * kx * 2;
     if (best_cost < 0 || cost <= best_cost) {
       best_cost = cost;
       best = w;
@@ -1212,7 +1220,7 @@ lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, in
       __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
       cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
       cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
-      cuuint32_t rbox[4] = {KB, cuuint32_t(bx), 1, cuuint32_t(by)};
+      cuuint32_t rbox[4] = {cuuint32_t(g.kx), cuuint32_t(bx), 1, cuuint32_t(by)};
       for (int q = 0; q < 3; ++q) {
         const lem_status e = encode_f16_map(&probs[k].tm[3 + q], rbase[q], 4, rd, rs, rbox, "residual slice");
         if (e != LEM_OK) {
