@@ -87,6 +87,7 @@ struct GemmGeom {
   int unit0;            // multi-problem launch: this problem's first unit
   int fault;            // test hook (LEM_FAULT=timeout): CTA 0 arms its first stage but loads
                         // nothing, so the MMA issuer's bounded wait expires
+  const __half* Pt;     // P pieces as pre-swizzled tiles [M blocks][Wy][NP][BM x KB]
   const int* eP;        // per owner row: P scale exponent
   const int* escale;    // [2] residual scale exponent of each step parity
   unsigned* rmax;       // [2] max|r| accumulators (the GEMM clears the current one)
@@ -401,13 +402,19 @@ __global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __re
 }
 
 // Per owner row i of P (FP64, n_int x n_loc, window row-major): eP_i with
-// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 (+ P3) in the [M][Wy*kpad]
-// K layout (each window row zero-padded to kpad), and S_i = sum_k |P_int[i,k]| (the
-// exactness bound of the main product).
-__global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx, int kpad,
-                              __half* __restrict__ Pint, __half* __restrict__ P2, __half* __restrict__ P3,
-                              int* __restrict__ eP,
-                              double* __restrict__ S) {
+// max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 (+ P3), and S_i =
+// sum_k |P_int[i,k]| (the exactness bound of the main product). The pieces are stored as the
+// shared-memory images the MMA reads: one tile per (M block, window row, piece) of BM rows x
+// KB columns (the window row zero-padded to KB), 128-byte rows with the 16-byte chunks of row
+// r permuted by r mod 8 (the 128-byte swizzle of a 1024-byte aligned tile), so that one bulk
+// copy of 16 KB loads a tile (Pt: [M blocks][Wy][np][BM x KB]).
+__device__ __forceinline__ int64_t ptile_index(int i, int wy, int q, int k, int Wy, int np) {
+  const int mb = i / BM, r = i % BM;
+  return ((int64_t(mb) * Wy + wy) * np + q) * (BM * KB) + r * KB + (((k >> 3) ^ (r & 7)) << 3) + (k & 7);
+}
+
+__global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx, int kpad, int np,
+                              __half* __restrict__ Pt, int* __restrict__ eP, double* __restrict__ S) {
   const int i = blockIdx.x;
   if (i >= M) return;
   __shared__ double red[256];
@@ -431,9 +438,9 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
     const double xi = rint(x);
     const __half hi = __double2half(xi);  // exact: |xi| <= 2^9
     const __half h2 = __double2half(x - xi);
-    Pint[int64_t(i) * Wy * kpad + col] = hi;
-    P2[int64_t(i) * Wy * kpad + col] = h2;
-    if (P3) P3[int64_t(i) * Wy * kpad + col] = __double2half(x - xi - double(__half2float(h2)));
+    Pt[ptile_index(i, wy, 0, wx, Wy, np)] = hi;
+    Pt[ptile_index(i, wy, 1, wx, Wy, np)] = h2;
+    if (np == 3) Pt[ptile_index(i, wy, 2, wx, Wy, np)] = __double2half(x - xi - double(__half2float(h2)));
     sum += fabs(xi);
   }
   red[threadIdx.x] = sum;
@@ -557,7 +564,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     ptx::fence_barrier_init();
     if (!MULTI) {
-      for (int q = 0; q < 2 * NP; ++q) ptx::tma_prefetch_desc(&one.tm[q < NP ? q : 3 + q - NP]);
+      for (int q = 0; q < NP; ++q) ptx::tma_prefetch_desc(&one.tm[3 + q]);
     }
     // max|r| of this step's parity has been consumed by the residual kernel; clear it for
     // the next-but-one step (no other kernel touches it while this one runs)
@@ -603,14 +610,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // its own barrier, so the MMAs on the first pieces start while the later ones stream.
           // (TMA lands each row's kx columns at their places in the 128-byte swizzled row; the
           // rest of the row is never read: the MMAs take ceil(Wx / 16) K steps of 16)
-          const uint32_t piece_bytes = uint32_t((BM + g.bnp) * g.kx * 2);
+          // a piece: its P tile (one 16 KB bulk copy of the pre-swizzled image) and its window
+          // tile (bnp TMA rows of kx columns)
+          const uint32_t piece_bytes = uint32_t(A_BYTES + g.bnp * g.kx * 2);
+          const __half* ptile = g.Pt + (int64_t(m0 / BM) * g.Wy + kb) * NP * (BM * KB);
           const bool fault = g.fault && blockIdx.x == 0 && it == 0;  // test hook: bytes never arrive
           for (int q = 0; q < NG; ++q) ptx::mbar_arrive_expect_tx(&full[s * NG + q], piece_bytes * (NP / NG));
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             if (fault) continue;
             uint64_t* bar = &full[s * NG + (NG == 1 ? 0 : q)];
-            ptx::tma_load_2d(st + q * A_BYTES, &pr->tm[q], bar, kb * KB, m0);
+            ptx::bulk_load(st + q * A_BYTES, ptile + q * (BM * KB), A_BYTES, bar);
             ptx::tma_load_4d(st + R_OFF + q * B_BYTES, &pr->tm[3 + q], bar, 0, tx0, kb, ty0);
           }
           issued = it + 1;
@@ -887,9 +897,7 @@ struct SplitPlan {
   __half* d_Rint = nullptr;
   __half* d_R2 = nullptr;
   __half* d_R3 = nullptr;
-  __half* d_Pint = nullptr;
-  __half* d_P2 = nullptr;
-  __half* d_P3 = nullptr;
+  __half* d_Pt = nullptr;  // P pieces as pre-swizzled tiles [M blocks][Wy][np][BM x KB]
   int* d_eP = nullptr;
   double* d_S = nullptr;
   unsigned* d_rmax = nullptr;
@@ -1003,20 +1011,17 @@ lem_status split_prepare(lem_ctx* ctx) {
   sp->rp.rb = nullptr;  // device value, set from the packed propagator in split_pack
   const size_t npts = size_t(ctx->npts);
   const size_t rbytes = sizeof(__half) * size_t(sp->prow) * sp->pitch;
-  // P slices padded to whole 128-row M blocks (zero rows past Ty*Tx)
+  // P pieces padded to whole 128-row M blocks (zero rows past Ty*Tx)
   const int Mpad = (sp->M + BM - 1) / BM * BM;
-  const size_t pbytes = sizeof(__half) * size_t(Mpad) * sp->Wy * KB;
+  const size_t pbytes = sizeof(__half) * size_t(Mpad) * sp->Wy * KB * sp->np;
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_uh), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_ul), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Rint), rbytes));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R2), rbytes));
-  LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Pint), pbytes));
-  LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P2), pbytes));
+  LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Pt), pbytes));
   if (sp->np == 3) {
     LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_R3), rbytes));
-    LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_P3), pbytes));
     LEM_CUDA_TRY(cudaMemsetAsync(sp->d_R3, 0, rbytes, ctx->stream));
-    LEM_CUDA_TRY(cudaMemsetAsync(sp->d_P3, 0, pbytes, ctx->stream));
   }
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_eP), sizeof(int) * sp->M));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_S), sizeof(double) * sp->M));
@@ -1025,8 +1030,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_err), sizeof(int)));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_rb), sizeof(int)));
   sp->rp.rb = sp->d_rb;
-  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_Pint, 0, pbytes, ctx->stream));
-  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_P2, 0, pbytes, ctx->stream));
+  LEM_CUDA_TRY(cudaMemsetAsync(sp->d_Pt, 0, pbytes, ctx->stream));
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_Rint, 0, rbytes, ctx->stream));
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_R2, 0, rbytes, ctx->stream));
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_err, 0, sizeof(int), ctx->stream));
@@ -1034,26 +1038,19 @@ lem_status split_prepare(lem_ctx* ctx) {
                                     SMEM_BYTES));
   LEM_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel_for(sp->bn, sp->np, true),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  // tensor maps: P slices [M][Wy*64] fp16 (2D, box 64 x rows); residual slices through a 4D
-  // overlapping view of the padded array: (wx, tx, wy, ty) -> R[ty*Ty + wy][tx*Tx + wx]
+  // residual pieces through a 4D overlapping view of the padded array: (wx, tx, wy, ty) ->
+  // R[ty*Ty + wy][tx*Tx + wx] (tm[3..5]; tm[0..2] unused: P tiles come by bulk copy)
   {
     SplitProblem& pr = sp->prob;
-    // with two pieces the third maps alias the second (never loaded)
-    __half* pbase[3] = {sp->d_Pint, sp->d_P2, sp->np == 3 ? sp->d_P3 : sp->d_P2};
+    // with two pieces the third map aliases the second (never loaded)
     __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
-    cuuint64_t pd[2] = {cuuint64_t(sp->Wy) * KB, cuuint64_t(Mpad)};
-    cuuint64_t ps[1] = {cuuint64_t(sp->Wy) * KB * 2};
     // only the window row's used columns: kx = Wx rounded up to 16 (a 96-byte box for 48-wide
     // windows lands at the same swizzled places as the first 48 columns of a 128-byte row)
     const cuuint32_t kx = cuuint32_t((sp->Wx + 15) / 16 * 16);
-    cuuint32_t pbox[2] = {kx, cuuint32_t(BM)};
     cuuint64_t rd[4] = {KB, cuuint64_t(sp->ntx), cuuint64_t(sp->Wy), cuuint64_t(sp->nty)};
     cuuint64_t rs[3] = {cuuint64_t(sp->Tx) * 2, cuuint64_t(sp->pitch) * 2, cuuint64_t(sp->Ty) * sp->pitch * 2};
     cuuint32_t rbox[4] = {kx, cuuint32_t(sp->BNx), 1, cuuint32_t(sp->BNy)};
-    for (int k = 0; k < 3; ++k) {
-      LEM_TRY(encode_f16_map(&pr.tm[k], pbase[k], 2, pd, ps, pbox, "P slice"));
-      LEM_TRY(encode_f16_map(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
-    }
+    for (int k = 0; k < 3; ++k) LEM_TRY(encode_f16_map(&pr.tm[3 + k], rbase[k], 4, rd, rs, rbox, "residual slice"));
   }
   GemmGeom& g = sp->prob.g;
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
@@ -1069,6 +1066,7 @@ lem_status split_prepare(lem_ctx* ctx) {
     const char* f = std::getenv("LEM_FAULT");
     g.fault = f && std::strcmp(f, "timeout") == 0;
   }
+  g.Pt = sp->d_Pt;
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
   cudaFuncAttributes fa{};
   LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(sp->bn, sp->np)));
@@ -1083,8 +1081,8 @@ lem_status split_prepare(lem_ctx* ctx) {
 static lem_status split_pack(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
-  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->d_Pint, sp->d_P2,
-                                       sp->d_P3, sp->d_eP, sp->d_S);
+  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->np, sp->d_Pt, sp->d_eP,
+                                       sp->d_S);
   choose_rb_kernel<<<1, 256, 0, st>>>(sp->d_S, sp->M, sp->d_rb, sp->d_err);
   LEM_CUDA_TRY(cudaGetLastError());
   sp->packed_gen = ctx->build_gen;
@@ -1364,8 +1362,8 @@ void split_destroy(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   if (!sp) return;
   for (void* p : {static_cast<void*>(sp->d_uh), static_cast<void*>(sp->d_ul), static_cast<void*>(sp->d_Rint),
-                  static_cast<void*>(sp->d_R2), static_cast<void*>(sp->d_Pint), static_cast<void*>(sp->d_P2),
-                  static_cast<void*>(sp->d_eP), static_cast<void*>(sp->d_S), static_cast<void*>(sp->d_P3),
+                  static_cast<void*>(sp->d_R2), static_cast<void*>(sp->d_Pt),
+                  static_cast<void*>(sp->d_eP), static_cast<void*>(sp->d_S),
                   static_cast<void*>(sp->d_R3), static_cast<void*>(sp->d_rmax), static_cast<void*>(sp->d_escale),
                   static_cast<void*>(sp->d_err), static_cast<void*>(sp->d_rb)})
     if (p) cudaFreeAsync(p, ctx->stream);  // stream-ordered (the memory came from cudaMallocAsync)
