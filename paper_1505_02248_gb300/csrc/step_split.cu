@@ -87,7 +87,7 @@ struct GemmGeom {
   int unit0;            // multi-problem launch: this problem's first unit
   int fault;            // test hook (LEM_FAULT=timeout): CTA 0 arms its first stage but loads
                         // nothing, so the MMA issuer's bounded wait expires
-  const __half* Pt;     // P pieces as pre-swizzled tiles [M blocks][Wy][NP][BM x KB]
+  const __half* Pt;     // P pieces as shared-memory images [M blocks][Wy][NP][BM x kx]
   const int* eP;        // per owner row: P scale exponent
   const int* escale;    // [2] residual scale exponent of each step parity
   unsigned* rmax;       // [2] max|r| accumulators (the GEMM clears the current one)
@@ -405,16 +405,18 @@ __global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __re
 // max_k |P[i,k]| 2^eP_i < 2^P_INT_BITS, then P 2^eP_i = P_int + P2 (+ P3), and S_i =
 // sum_k |P_int[i,k]| (the exactness bound of the main product). The pieces are stored as the
 // shared-memory images the MMA reads: one tile per (M block, window row, piece) of BM rows x
-// KB columns (the window row zero-padded to KB), 128-byte rows with the 16-byte chunks of row
-// r permuted by r mod 8 (the 128-byte swizzle of a 1024-byte aligned tile), so that one bulk
-// copy of 16 KB loads a tile (Pt: [M blocks][Wy][np][BM x KB]).
-__device__ __forceinline__ int64_t ptile_index(int i, int wy, int q, int k, int Wy, int np) {
+// kx columns (kx = Wx rounded up to 16, the MMA's K steps), in the unswizzled K-major layout
+// of 8-row x 16-byte core matrices (128 contiguous bytes each; K-adjacent ones 128 B apart,
+// row-adjacent ones kx * 16 B apart), so that one bulk copy of BM * kx * 2 bytes with no
+// padding loads a tile (Pt: [M blocks][Wy][np][BM x kx]).
+__device__ __forceinline__ int64_t ptile_index(int i, int wy, int q, int k, int Wy, int np, int kx) {
   const int mb = i / BM, r = i % BM;
-  return ((int64_t(mb) * Wy + wy) * np + q) * (BM * KB) + r * KB + (((k >> 3) ^ (r & 7)) << 3) + (k & 7);
+  return ((int64_t(mb) * Wy + wy) * np + q) * (BM * kx) + ((r >> 3) * (kx >> 3) + (k >> 3)) * 64 + (r & 7) * 8 +
+         (k & 7);
 }
 
 __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M, int Wy, int Wx, int kpad, int np,
-                              __half* __restrict__ Pt, int* __restrict__ eP, double* __restrict__ S) {
+                              int kx, __half* __restrict__ Pt, int* __restrict__ eP, double* __restrict__ S) {
   const int i = blockIdx.x;
   if (i >= M) return;
   __shared__ double red[256];
@@ -438,9 +440,11 @@ __global__ void pack_p_kernel(const double* __restrict__ P, int64_t n_loc, int M
     const double xi = rint(x);
     const __half hi = __double2half(xi);  // exact: |xi| <= 2^9
     const __half h2 = __double2half(x - xi);
-    Pt[ptile_index(i, wy, 0, wx, Wy, np)] = hi;
-    Pt[ptile_index(i, wy, 1, wx, Wy, np)] = h2;
-    if (np == 3) Pt[ptile_index(i, wy, 2, wx, Wy, np)] = __double2half(x - xi - double(__half2float(h2)));
+    if (wx < kx) {  // (columns past kx are zero and never read)
+      Pt[ptile_index(i, wy, 0, wx, Wy, np, kx)] = hi;
+      Pt[ptile_index(i, wy, 1, wx, Wy, np, kx)] = h2;
+      if (np == 3) Pt[ptile_index(i, wy, 2, wx, Wy, np, kx)] = __double2half(x - xi - double(__half2float(h2)));
+    }
     sum += fabs(xi);
   }
   red[threadIdx.x] = sum;
@@ -610,17 +614,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // its own barrier, so the MMAs on the first pieces start while the later ones stream.
           // (TMA lands each row's kx columns at their places in the 128-byte swizzled row; the
           // rest of the row is never read: the MMAs take ceil(Wx / 16) K steps of 16)
-          // a piece: its P tile (one 16 KB bulk copy of the pre-swizzled image) and its window
-          // tile (bnp TMA rows of kx columns)
-          const uint32_t piece_bytes = uint32_t(A_BYTES + g.bnp * g.kx * 2);
-          const __half* ptile = g.Pt + (int64_t(m0 / BM) * g.Wy + kb) * NP * (BM * KB);
+          // a piece: its P tile (one bulk copy of BM * kx * 2 bytes, the unswizzled image) and
+          // its window tile (bnp TMA rows of kx columns)
+          const uint32_t piece_bytes = uint32_t((BM + g.bnp) * g.kx * 2);
+          const __half* ptile = g.Pt + (int64_t(m0 / BM) * g.Wy + kb) * NP * (BM * g.kx);
           const bool fault = g.fault && blockIdx.x == 0 && it == 0;  // test hook: bytes never arrive
           for (int q = 0; q < NG; ++q) ptx::mbar_arrive_expect_tx(&full[s * NG + q], piece_bytes * (NP / NG));
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             if (fault) continue;
             uint64_t* bar = &full[s * NG + (NG == 1 ? 0 : q)];
-            ptx::bulk_load(st + q * A_BYTES, ptile + q * (BM * KB), A_BYTES, bar);
+            ptx::bulk_load(st + q * A_BYTES, ptile + q * (BM * g.kx), uint32_t(BM * g.kx * 2), bar);
             ptx::tma_load_4d(st + R_OFF + q * B_BYTES, &pr->tm[3 + q], bar, 0, tx0, kb, ty0);
           }
           issued = it + 1;
@@ -668,46 +672,49 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
           ptx::tc_fence_after();
           const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
-          const uint64_t dPi = ptx::sw128_kmajor_desc(base);
-          const uint64_t dP2 = ptx::sw128_kmajor_desc(base + A_BYTES);
+          // P tiles: unswizzled core matrices (K-adjacent 128 B apart, row groups kx * 16 B
+          // apart); residual tiles: 128-byte swizzled rows
+          const uint32_t sbo = uint32_t(g.kx) * 16u;
+          const uint64_t dPi = ptx::plain_kmajor_desc(base, 128, sbo);
+          const uint64_t dP2 = ptx::plain_kmajor_desc(base + A_BYTES, 128, sbo);
           const uint64_t dRi = ptx::sw128_kmajor_desc(base + R_OFF);
           const uint64_t dR2 = ptx::sw128_kmajor_desc(base + R_OFF + B_BYTES);
-          const uint64_t dP3 = ptx::sw128_kmajor_desc(base + 2 * A_BYTES);       // NP == 3 only
-          const uint64_t dR3 = ptx::sw128_kmajor_desc(base + R_OFF + 2 * B_BYTES);  // NP == 3 only
+          const uint64_t dP3 = ptx::plain_kmajor_desc(base + 2 * A_BYTES, 128, sbo);  // NP == 3 only
+          const uint64_t dR3 = ptx::sw128_kmajor_desc(base + R_OFF + 2 * B_BYTES);    // NP == 3 only
           // ceil(Wx / 16) K steps: P is zero beyond Wx in each padded window row.
           if constexpr (NP == 2) {
             // two pieces: the main product on piece 0 while piece 1 still streams, then the
             // three corrections (GB300, 2048^2: 65.8 us per launch against 70.7 us waiting for
             // the whole stage)
             for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
+              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;  // 16 K: 32 B (swizzled rows), two core matrices
               const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-              ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
+              ptx::mma_f16(main, dPi + advA, dRi + adv, idesc, acc);  // exact: integer partial sums
             }
             if (!ptx::mbar_wait(&full[s * NG + 1], ph, WAIT_NS)) { ok = false; break; }
             ptx::tc_fence_after();
             for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4;
+              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;
               const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-              ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, acc);
-              ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
+              ptx::mma_f16(corr, dPi + advA, dR2 + adv, idesc, acc);
+              ptx::mma_f16(corr, dP2 + advA, dRi + adv, idesc, 1u);
+              ptx::mma_f16(corr, dP2 + advA, dR2 + adv, idesc, 1u);
             }
           } else {
             // three pieces: the whole stage (waited above), then the six products of each K step
             // in turn (issuing them piece by piece measured 152 us against 133 us per 2048^2
             // launch)
             for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4;  // 16 fp16 = 32 B along K
+              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;  // 16 K: 32 B (swizzled rows), two core matrices
               const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
               // DRAIN: each row group starts a fresh correction sum
               const uint32_t cacc = DRAIN ? ((group_first && kk == 0) ? 0u : 1u) : acc;
-              ptx::mma_f16(main, dPi + adv, dRi + adv, idesc, acc);  // exact: integer partial sums
-              ptx::mma_f16(corr, dPi + adv, dR2 + adv, idesc, cacc);
-              ptx::mma_f16(corr, dP2 + adv, dRi + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP2 + adv, dR2 + adv, idesc, 1u);
-              ptx::mma_f16(corr, dPi + adv, dR3 + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP3 + adv, dRi + adv, idesc, 1u);
+              ptx::mma_f16(main, dPi + advA, dRi + adv, idesc, acc);  // exact: integer partial sums
+              ptx::mma_f16(corr, dPi + advA, dR2 + adv, idesc, cacc);
+              ptx::mma_f16(corr, dP2 + advA, dRi + adv, idesc, 1u);
+              ptx::mma_f16(corr, dP2 + advA, dR2 + adv, idesc, 1u);
+              ptx::mma_f16(corr, dPi + advA, dR3 + adv, idesc, 1u);
+              ptx::mma_f16(corr, dP3 + advA, dRi + adv, idesc, 1u);
             }
           }
           ptx::mma_commit(&empty[s]);
@@ -1013,7 +1020,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   const size_t rbytes = sizeof(__half) * size_t(sp->prow) * sp->pitch;
   // P pieces padded to whole 128-row M blocks (zero rows past Ty*Tx)
   const int Mpad = (sp->M + BM - 1) / BM * BM;
-  const size_t pbytes = sizeof(__half) * size_t(Mpad) * sp->Wy * KB * sp->np;
+  const size_t pbytes = sizeof(__half) * size_t(Mpad) * sp->Wy * ((sp->Wx + 15) / 16 * 16) * sp->np;
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_uh), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_ul), sizeof(float) * npts));
   LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_Rint), rbytes));
@@ -1081,8 +1088,8 @@ lem_status split_prepare(lem_ctx* ctx) {
 static lem_status split_pack(lem_ctx* ctx) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
-  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->np, sp->d_Pt, sp->d_eP,
-                                       sp->d_S);
+  pack_p_kernel<<<sp->M, 256, 0, st>>>(ctx->d_P, ctx->n_loc, sp->M, sp->Wy, sp->Wx, KB, sp->np, sp->prob.g.kx,
+                                       sp->d_Pt, sp->d_eP, sp->d_S);
   choose_rb_kernel<<<1, 256, 0, st>>>(sp->d_S, sp->M, sp->d_rb, sp->d_err);
   LEM_CUDA_TRY(cudaGetLastError());
   sp->packed_gen = ctx->build_gen;
