@@ -14,10 +14,14 @@ closed forms, library routines or brute force, never on the oracle itself:
   phi_3: the scalar closed form (e^z - 1 - z - z^2/2) / z^3
   exprb32: the local error against a library ODE solver (scipy DOP853) falls by about 2^4
            per halving of dt (third order); a dropped factor 2 leaves about 2^3
+  truncation: each side's extent against the one predicted from the Bessel tails of the 1D
+           random-walk kernel (upwind advection makes the two sides differ); the window
+           offsets of an anisotropic 2D window against their ranges worked out by hand
 """
 import numpy as np
 import pytest
 import scipy.sparse as sp
+from scipy import integrate, special
 from scipy.integrate import solve_ivp
 
 import oracle.lem_oracle as OL
@@ -124,6 +128,41 @@ def check_rb3_local_order():
     return errs[0] / errs[1] >= 10.0
 
 
+def check_truncation_extents():
+    # 1D periodic upwind advection-diffusion (W = mu + c, E = mu) on a long mesh: the window's
+    # phi_1 rows follow the lattice random-walk kernel; predict each side's extent from it
+    mu, c, tol = 2.0, 1.0, 1e-6  # (both sides move by one when tol is not split over them)
+    n = 512
+    coef = W.stencil_advdiff_1d(mu, c, 1.0, upwind=True)
+    X = OL.assemble_operator((n,), ("periodic",), coef, 1.0)
+    wins = OL.decompose((n,), ("periodic",), (16,), (40,))
+    P = OL.local_propagators(X, wins, "phi", tiles=[0])[0]
+    Wc, Ec = coef["W"], coef["E"]
+
+    def kern(k, s):
+        z = 2.0 * s * np.sqrt(Wc * Ec)
+        return np.exp(-s * (Wc + Ec) + z) * (Ec / Wc) ** (k / 2.0) * special.ive(abs(k), z)
+    ks = np.arange(-60, 61)
+    f = np.array([integrate.quad(lambda s: kern(k, s), 0.0, 1.0, epsabs=1e-16, epsrel=1e-13)[0] for k in ks])
+
+    def side(beyond):
+        e = 0
+        while f[beyond(e)].sum() > 0.25 * tol * f.sum():
+            e += 1
+        return e
+    want = (0, 0, side(lambda e: ks < -e), side(lambda e: ks > e))
+    return OL.truncation_extents(P, wins[0], (n,), tol) == want
+
+
+def check_window_offsets_by_hand():
+    # tile (4, 8) with H (6, 2) on a periodic 40 x 40 mesh: window 16 x 12, owners at window
+    # rows 6..9 and columns 2..9; offsets run from -9 to 9 along y and from -9 to 9 along x,
+    # but owner (0, 0) sees rows -6..9 and columns -2..9
+    w = OL.decompose((40, 40), ("periodic", "periodic"), (4, 8), (6, 2))[0]
+    oy, ox = OL.window_offsets(w, (40, 40))
+    return (oy[0].min(), oy[0].max(), ox[0].min(), ox[0].max()) == (-6, 9, -2, 9) and oy.shape == (32, 192)
+
+
 # ---------------------------------------------------------------- mutations
 def m_drop_pade_term(mp):
     b = list(OL._B)
@@ -210,6 +249,29 @@ def m_rb3_factor_one(mp):
     mp.setattr(OL, "rb3_defect", lambda u, U, um, dt: 0.5 * orig(u, U, um, dt))
 
 
+def m_trunc_sides_swapped(mp):
+    orig = OL.truncation_extents
+
+    def bad(P, window, shape, tol):
+        ly, hy, lx, hx = orig(P, window, shape, tol)
+        return (hy, ly, hx, lx)
+    mp.setattr(OL, "truncation_extents", bad)
+
+
+def m_trunc_whole_tol_per_side(mp):
+    orig = OL.truncation_extents
+    mp.setattr(OL, "truncation_extents", lambda P, window, shape, tol: orig(P, window, shape, 4.0 * tol))
+
+
+def m_offsets_axes_swapped(mp):
+    orig = OL.window_offsets
+
+    def bad(window, shape):
+        oy, ox = orig(window, shape)
+        return ox, oy
+    mp.setattr(OL, "window_offsets", bad)
+
+
 CASES = {
     "dropped Pade term": (m_drop_pade_term, check_expm),
     "theta_13 too large": (m_theta_too_large, check_expm),
@@ -224,6 +286,9 @@ CASES = {
     "Schroedinger stencil conjugated": (m_conjugate_stencil, check_free_schroedinger),
     "phi_k one block off": (m_phik_off_by_one, check_phi3),
     "exprb32 correction factor 1": (m_rb3_factor_one, check_rb3_local_order),
+    "truncation sides swapped": (m_trunc_sides_swapped, check_truncation_extents),
+    "truncation tol not split over the sides": (m_trunc_whole_tol_per_side, check_truncation_extents),
+    "window offsets with the axes swapped": (m_offsets_axes_swapped, check_window_offsets_by_hand),
 }
 
 
