@@ -217,7 +217,9 @@ lem_status lem_plan_query(const lem_problem_desc* desc, int64_t* ntiles, int64_t
                           int64_t* n_loc, int64_t* n_int, int32_t* tile_info);
 
 /* Per-kernel timing of the dominant propagator-apply kernel (for benchmarks).
- * lem_set_timing(ctx, 1) makes later lem_step calls bracket every launch of the apply
+ * lem_set_timing(ctx, k) with k >= 1 makes later lem_step calls bracket every k-th launch
+ * (k = 1: every launch; an event between two launches keeps the second from starting its
+ * set-up while the first finishes, so a period larger than 1 disturbs less) of the apply
  * kernel (the tcgen05 split GEMM, the FP64 apply GEMMs, the GEMV -- with LEM_SCHEME_RB3 both
  * stages of a step together -- or the persistent multi-step GEMV) with CUDA events on the
  * context stream; lem_get_timing synchronises, adds the elapsed times of all recorded

@@ -62,6 +62,7 @@ lem::Stencil lem_ctx::stencil() const {
 cudaError_t lem_ctx::timing_begin(cudaEvent_t* stop) {
   *stop = nullptr;
   if (!timing) return cudaSuccess;
+  if (timing_count++ % timing_period != 0) return cudaSuccess;
   if (ev_used + 2 > ev_pool.size()) {
     for (int i = 0; i < 256; ++i) {
       cudaEvent_t e;
@@ -439,7 +440,10 @@ lem_status lem_get_band(lem_ctx* ctx, int64_t cls, int32_t* ext, int64_t* row_va
 
 lem_status lem_set_timing(lem_ctx* ctx, int enable) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
+  if (enable < 0) return fail(LEM_EINVAL, "enable < 0");
   ctx->timing = enable != 0;
+  ctx->timing_period = enable > 1 ? enable : 1;
+  ctx->timing_count = 0;
   return LEM_OK;
 }
 

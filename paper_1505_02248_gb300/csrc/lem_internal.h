@@ -120,6 +120,8 @@ struct lem_ctx {
   lem::BandPlan* band = nullptr;
   // optional event timing of the apply kernel
   bool timing = false;
+  int timing_period = 1;               // bracket every timing_period-th apply launch
+  int64_t timing_count = 0;
   std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop)
   size_t ev_used = 0;
   cudaError_t timing_begin(cudaEvent_t* stop);

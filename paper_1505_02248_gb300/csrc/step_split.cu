@@ -267,6 +267,14 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
   }
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the previous kernel of the stream finishes; it waits for that kernel's results
+// here (a no-op for an ordinary launch) and lets the next kernel start its own set-up.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __global__ void __launch_bounds__(256) residual_split_kernel(const float* __restrict__ uh,
                                                              const float* __restrict__ ul,
                                                              __half* __restrict__ Rint,
@@ -274,6 +282,7 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
                                                              __half* __restrict__ R3, ResParams p,
                                                              unsigned* rmax, int* escale, int parity,
                                                              int measure) {
+  pdl_wait_and_release();
   residual_tile(uh, ul, Rint, R2, R3, p, rmax, escale, parity, measure, int(blockIdx.x), int(blockIdx.y));
 }
 
@@ -570,13 +579,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (!MULTI) {
       for (int q = 0; q < NP; ++q) ptx::tma_prefetch_desc(&one.tm[3 + q]);
     }
-    // max|r| of this step's parity has been consumed by the residual kernel; clear it for
-    // the next-but-one step (no other kernel touches it while this one runs)
-    if (!MULTI) {
-      if (blockIdx.x == 0) one.g.rmax[parity] = 0u;
-    } else {
-      for (int i = int(blockIdx.x); i < nprob; i += int(gridDim.x)) many[i].g.rmax[parity] = 0u;
-    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -586,6 +588,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // the set-up above may overlap the residual kernel's tail; everything below reads its output
+  pdl_wait_and_release();
+  if (threadIdx.x == 0) {
+    // max|r| of this step's parity has been consumed by the residual kernel; clear it for
+    // the next-but-one step (no other kernel touches it while this one runs)
+    if (!MULTI) {
+      if (blockIdx.x == 0) one.g.rmax[parity] = 0u;
+    } else {
+      for (int i = int(blockIdx.x); i < nprob; i += int(gridDim.x)) many[i].g.rmax[parity] = 0u;
+    }
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -1119,15 +1132,29 @@ lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d
   SplitProblem prob = sp->prob;  // the GEMM's epilogue adds into this state
   prob.g.uh = uh;
   prob.g.ul = ul;
+  // residual and GEMM launches alternate with programmatic stream serialization: each may
+  // start its set-up while the previous one finishes (both kernels wait for their input)
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg{};
   cfg.blockDim = dim3(gemm_threads(sp->np));
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = st;
   cfg.gridDim = dim3(std::min(prob.g.nMB * prob.g.nNB, sp->nsm));
+  cfg.attrs = pdl;
+  cfg.numAttrs = 1;
+  cudaLaunchConfig_t rcfg{};
+  rcfg.blockDim = dim3(256);
+  rcfg.gridDim = rgrid;
+  rcfg.stream = st;
+  rcfg.attrs = pdl;
+  rcfg.numAttrs = 1;
   for (int k = 0; k < nsteps; ++k) {
     const int parity = k & 1;
-    residual_split_kernel<<<rgrid, 256, 0, st>>>(uh, ul, sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp, sp->d_rmax,
-                                                 sp->d_escale, parity, 0);
+    LEM_CUDA_TRY(cudaLaunchKernelEx(&rcfg, residual_split_kernel, static_cast<const float*>(uh),
+                                    static_cast<const float*>(ul), sp->d_Rint, sp->d_R2, sp->d_R3, sp->rp, sp->d_rmax,
+                                    sp->d_escale, parity, 0));
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
     LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->bn, sp->np), prob,

@@ -345,8 +345,9 @@ class Lem:
         check(self._lib.lem_get_band(self._h, -1, ext, C.byref(nv)), "lem_get_band")
         return int(nv.value)
 
-    def set_timing(self, on: bool):
-        check(self._lib.lem_set_timing(self._h, 1 if on else 0), "lem_set_timing")
+    def set_timing(self, on, period: int = 1):
+        """Bracket every `period`-th apply-kernel launch with CUDA events (on: True/False)."""
+        check(self._lib.lem_set_timing(self._h, max(1, int(period)) if on else 0), "lem_set_timing")
 
     def get_timing(self):
         """(total_ms, launches) of the apply kernel since the last call."""
