@@ -241,7 +241,8 @@ lem_status lem_get_timing(lem_ctx* ctx, double* total_ms, int64_t* launches);
  * - Needs built propagators (lem_build_propagators first: LEM_ENOTREADY otherwise) and
  *   no Jacobian refresh (reaction with refresh > 0: LEM_EINVAL), since building allocates.
  * - Real problems with the exponential Euler scheme only; the porous-medium problem
- *   (reaction 2) is refused (LEM_EINVAL).
+ *   (reaction 2) and truncated propagators (lem_set_truncation with tol >= 0) are refused
+ *   (LEM_EINVAL).
  * - Problems whose scratch, npts (+ ntiles*(n_loc + n_int) on the GEMM path) doubles (each
  *   part rounded up to 32), exceeds 8 MiB are rejected with LEM_EINVAL and a message giving
  *   both sizes.
