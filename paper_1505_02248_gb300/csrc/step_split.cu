@@ -492,6 +492,49 @@ __global__ void choose_rb_kernel(const double* __restrict__ S, int M, int* rb, i
   }
 }
 
+// Shared-memory descriptors of one stage's operand pieces at K step 0.
+struct StageDesc {
+  uint64_t P[3], R[3];
+};
+// K step kk of 16: P (unswizzled core matrices) advances 256 B, the residual (128-byte
+// swizzled rows) 32 B; in 16-byte units of the descriptor's address field.
+constexpr uint64_t ADV_P = 256 >> 4, ADV_R = 32 >> 4;
+
+// Main product P_int r_int over KS K steps (exact: integer partial sums).
+template <int KS>
+__device__ __forceinline__ void issue_main(uint32_t main, const StageDesc& d, uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int kk = 0; kk < KS; ++kk)
+    ptx::mma_f16(main, d.P[0] + kk * ADV_P, d.R[0] + kk * ADV_R, idesc, kk == 0 ? acc0 : 1u);
+}
+// Two-piece corrections P_int r2 + P2 r_int + P2 r2.
+template <int KS>
+__device__ __forceinline__ void issue_corr2(uint32_t corr, const StageDesc& d, uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+  for (int kk = 0; kk < KS; ++kk) {
+    const uint64_t a = kk * ADV_P, r = kk * ADV_R;
+    ptx::mma_f16(corr, d.P[0] + a, d.R[1] + r, idesc, kk == 0 ? acc0 : 1u);
+    ptx::mma_f16(corr, d.P[1] + a, d.R[0] + r, idesc, 1u);
+    ptx::mma_f16(corr, d.P[1] + a, d.R[1] + r, idesc, 1u);
+  }
+}
+// Three pieces: per K step the main product and the five corrections P_int r2, P2 r_int,
+// P2 r2, P_int r3, P3 r_int.
+template <int KS>
+__device__ __forceinline__ void issue_six(uint32_t main, uint32_t corr, const StageDesc& d, uint32_t idesc,
+                                          uint32_t acc0, uint32_t cacc0) {
+#pragma unroll
+  for (int kk = 0; kk < KS; ++kk) {
+    const uint64_t a = kk * ADV_P, r = kk * ADV_R;
+    ptx::mma_f16(main, d.P[0] + a, d.R[0] + r, idesc, kk == 0 ? acc0 : 1u);
+    ptx::mma_f16(corr, d.P[0] + a, d.R[1] + r, idesc, kk == 0 ? cacc0 : 1u);
+    ptx::mma_f16(corr, d.P[1] + a, d.R[0] + r, idesc, 1u);
+    ptx::mma_f16(corr, d.P[1] + a, d.R[1] + r, idesc, 1u);
+    ptx::mma_f16(corr, d.P[0] + a, d.R[2] + r, idesc, 1u);
+    ptx::mma_f16(corr, d.P[2] + a, d.R[0] + r, idesc, 1u);
+  }
+}
+
 // Persistent GEMM: each CTA walks output units u = blockIdx.x, + gridDim.x, ...
 // A unit is one (M block, window block) tile of one problem: of the single problem `one`
 // (M block u % nMB, window block u / nMB), or, when `many` is given, of the problem whose
@@ -654,10 +697,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // each collecting drain_rows window rows before the epilogue takes it. The epilogue folds a
     // tile's main sum into its last correction buffer and frees main at once.
     if (lane == 0) {
+      // The issue loop is kept short: a tcgen05.mma costs this thread tens of cycles to issue,
+      // about as long as an N = 128 product takes on the tensor pipe, so descriptors are set
+      // up once per tile and only advanced per stage and K step.
       bool ok = true;
-      int it = 0, lt = 0, kc = 0;
+      int lt = 0, kc = 0;
+      int s = 0;         // ring slot of the next stage
+      uint32_t ph = 0;   // its fill phase
+      int cj = 0;        // DRAIN: correction buffer of the current row group (kc % 3)
       int64_t cur = cur0;
       int u, kb0, kb1;
+      const uint32_t tiles_addr = ptx::smem_u32(tiles);
       for (; ok && next_seg(cur, u, kb0, kb1); ++lt) {
         int lu;
         const GemmGeom& g = locate(u, lu)->g;
@@ -672,68 +722,77 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         const uint32_t main = DRAIN ? tmem : tmem + b * 2 * BN;
         uint32_t corr = main + BN;
-        for (int kb = kb0; kb < kb1; ++kb, ++it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1;
+        // stage-0 descriptors of the pieces. P tiles: unswizzled core matrices (K-adjacent
+        // 128 B apart, row groups kx * 16 B apart); residual tiles: 128-byte swizzled rows.
+        // Stage s adds s * STAGE_BYTES to the (16-byte unit) address field.
+        const uint32_t sbo = uint32_t(g.kx) * 16u;
+        StageDesc d0;
+        d0.P[0] = ptx::plain_kmajor_desc(tiles_addr, 128, sbo);
+        d0.P[1] = d0.P[0] + uint64_t(A_BYTES >> 4);
+        d0.P[2] = d0.P[0] + uint64_t(2 * A_BYTES >> 4);  // NP == 3 only
+        d0.R[0] = ptx::sw128_kmajor_desc(tiles_addr + R_OFF);
+        d0.R[1] = d0.R[0] + uint64_t(B_BYTES >> 4);
+        d0.R[2] = d0.R[0] + uint64_t(2 * B_BYTES >> 4);  // NP == 3 only
+        int gpos = 0;  // DRAIN: window row within its row group
+        for (int kb = kb0; kb < kb1; ++kb) {
           if (!ptx::mbar_wait(&full[s * NG], ph, WAIT_NS)) { ok = false; break; }
-          const bool group_first = DRAIN && (kb - kb0) % dr == 0;
-          const bool group_last = DRAIN && ((kb - kb0) % dr == dr - 1 || kb == kb1 - 1);
+          const bool group_first = DRAIN && gpos == 0;
+          const bool group_last = DRAIN && (gpos == dr - 1 || kb == kb1 - 1);
           if (group_first) {
-            const int j = kc % 3;
-            if (kc >= 3 && !ptx::mbar_wait(&ce[j], ((kc / 3) - 1) & 1, WAIT_NS)) { ok = false; break; }
-            corr = tmem + (1 + j) * BN;
+            if (kc >= 3 && !ptx::mbar_wait(&ce[cj], ((kc / 3) - 1) & 1, WAIT_NS)) { ok = false; break; }
+            corr = tmem + (1 + cj) * BN;
           }
           ptx::tc_fence_after();
-          const uint32_t base = ptx::smem_u32(tiles + s * STAGE_BYTES);
-          // P tiles: unswizzled core matrices (K-adjacent 128 B apart, row groups kx * 16 B
-          // apart); residual tiles: 128-byte swizzled rows
-          const uint32_t sbo = uint32_t(g.kx) * 16u;
-          const uint64_t dPi = ptx::plain_kmajor_desc(base, 128, sbo);
-          const uint64_t dP2 = ptx::plain_kmajor_desc(base + A_BYTES, 128, sbo);
-          const uint64_t dRi = ptx::sw128_kmajor_desc(base + R_OFF);
-          const uint64_t dR2 = ptx::sw128_kmajor_desc(base + R_OFF + B_BYTES);
-          const uint64_t dP3 = ptx::plain_kmajor_desc(base + 2 * A_BYTES, 128, sbo);  // NP == 3 only
-          const uint64_t dR3 = ptx::sw128_kmajor_desc(base + R_OFF + 2 * B_BYTES);    // NP == 3 only
+          const uint64_t sd = uint64_t(s) * uint64_t(STAGE_BYTES >> 4);
+          StageDesc d;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            d.P[q] = d0.P[q] + sd;
+            d.R[q] = d0.R[q] + sd;
+          }
+          const uint32_t acc0 = kb > kb0 ? 1u : 0u;  // the tile's first product starts the sum
           // ceil(Wx / 16) K steps: P is zero beyond Wx in each padded window row.
           if constexpr (NP == 2) {
             // two pieces: the main product on piece 0 while piece 1 still streams, then the
             // three corrections (GB300, 2048^2: 65.8 us per launch against 70.7 us waiting for
             // the whole stage)
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;  // 16 K: 32 B (swizzled rows), two core matrices
-              const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-              ptx::mma_f16(main, dPi + advA, dRi + adv, idesc, acc);  // exact: integer partial sums
+            switch (ksteps) {
+              case 1: issue_main<1>(main, d, idesc, acc0); break;
+              case 2: issue_main<2>(main, d, idesc, acc0); break;
+              case 3: issue_main<3>(main, d, idesc, acc0); break;
+              default: issue_main<4>(main, d, idesc, acc0); break;
             }
             if (!ptx::mbar_wait(&full[s * NG + 1], ph, WAIT_NS)) { ok = false; break; }
             ptx::tc_fence_after();
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;
-              const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-              ptx::mma_f16(corr, dPi + advA, dR2 + adv, idesc, acc);
-              ptx::mma_f16(corr, dP2 + advA, dRi + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP2 + advA, dR2 + adv, idesc, 1u);
+            switch (ksteps) {
+              case 1: issue_corr2<1>(corr, d, idesc, acc0); break;
+              case 2: issue_corr2<2>(corr, d, idesc, acc0); break;
+              case 3: issue_corr2<3>(corr, d, idesc, acc0); break;
+              default: issue_corr2<4>(corr, d, idesc, acc0); break;
             }
           } else {
             // three pieces: the whole stage (waited above), then the six products of each K step
             // in turn (issuing them piece by piece measured 152 us against 133 us per 2048^2
             // launch)
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const uint64_t adv = uint64_t(kk * 32) >> 4, advA = uint64_t(kk * 256) >> 4;  // 16 K: 32 B (swizzled rows), two core matrices
-              const uint32_t acc = (kb > kb0 || kk > 0) ? 1u : 0u;
-              // DRAIN: each row group starts a fresh correction sum
-              const uint32_t cacc = DRAIN ? ((group_first && kk == 0) ? 0u : 1u) : acc;
-              ptx::mma_f16(main, dPi + advA, dRi + adv, idesc, acc);  // exact: integer partial sums
-              ptx::mma_f16(corr, dPi + advA, dR2 + adv, idesc, cacc);
-              ptx::mma_f16(corr, dP2 + advA, dRi + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP2 + advA, dR2 + adv, idesc, 1u);
-              ptx::mma_f16(corr, dPi + advA, dR3 + adv, idesc, 1u);
-              ptx::mma_f16(corr, dP3 + advA, dRi + adv, idesc, 1u);
+            // DRAIN: each row group starts a fresh correction sum
+            const uint32_t cacc0 = DRAIN ? (group_first ? 0u : 1u) : acc0;
+            switch (ksteps) {
+              case 1: issue_six<1>(main, corr, d, idesc, acc0, cacc0); break;
+              case 2: issue_six<2>(main, corr, d, idesc, acc0, cacc0); break;
+              case 3: issue_six<3>(main, corr, d, idesc, acc0, cacc0); break;
+              default: issue_six<4>(main, corr, d, idesc, acc0, cacc0); break;
             }
           }
           ptx::mma_commit(&empty[s]);
           if (group_last) {
-            ptx::mma_commit(&cf[kc % 3]);
+            ptx::mma_commit(&cf[cj]);
             ++kc;
+            cj = cj == 2 ? 0 : cj + 1;
+          }
+          if (DRAIN) gpos = gpos + 1 == dr ? 0 : gpos + 1;
+          if (++s == STAGES) {
+            s = 0;
+            ph ^= 1u;
           }
         }
         if (ok) ptx::mma_commit(&accf[b]);
