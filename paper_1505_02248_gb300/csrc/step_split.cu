@@ -81,6 +81,7 @@ struct GemmGeom {
   int M;                // owner rows (Ty * Tx); M blocks past it are masked
   int nbx;              // window blocks per row of the tile grid
   int bnp;              // windows per block (BNx * BNy <= BN, a multiple of 16): the MMA's N
+  int lbx;              // log2 BNx (BNx is a power of two)
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int drain_rows;       // three pieces: window rows per correction drain
   int kx;               // K columns loaded per window row: Wx rounded up to 16 (the MMA's K steps)
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int n = c0 + i;
-          const int ty = ty0 + n / g.BNx, tx = tx0 + n % g.BNx;
+          const int ty = ty0 + (n >> g.lbx), tx = tx0 + (n & ((1 << g.lbx) - 1));
           const bool in = row_in && ty < g.nty && tx < g.ntx;
           inside |= uint32_t(in) << i;
           node[i] = in ? (ty * g.Ty) * g.nx + tx * g.Tx + rowbase : rowbase;
@@ -986,6 +987,13 @@ struct SplitPlan {
   SplitProblem prob{};  // tensor maps and GEMM geometry
   int packed_gen = -1;
 };
+
+// log2 of a power of two
+static int log2_exact(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
 
 // Windows of a CTA tile form a BNx x BNy rectangle of the tile grid with BNx*BNy = bn (both
 // powers of two). Blocks may overhang the grid at its right and bottom edges (TMA zero-fills
@@ -1134,6 +1142,7 @@ lem_status split_prepare(lem_ctx* ctx) {
   GemmGeom& g = sp->prob.g;
   g.Wy = sp->Wy; g.Wx = sp->Wx; g.Ty = sp->Ty; g.Tx = sp->Tx; g.nx = int(ctx->nx);
   g.BNx = sp->BNx; g.BNy = sp->BNy; g.ntx = sp->ntx; g.nty = sp->nty; g.M = sp->M;
+  g.lbx = log2_exact(sp->BNx);
   g.nbx = sp->nbx; g.nMB = (sp->M + BM - 1) / BM; g.nNB = sp->nbx * sp->nby; g.bnp = sp->bn;
   // three pieces: drain the correction after about 64 K elements (a 48- or 64-wide row, two
   // rows of up to 32, four of 16), so small windows do not pay a handshake per short row
@@ -1335,6 +1344,7 @@ lem_status split_batch_prepare(lem_ctx* const* ctxs, double* const* d_states, in
       int bx = 0, by = 0;
       group_tiles(sp->ntx, sp->nty, w, &bx, &by);
       g.BNx = bx; g.BNy = by; g.bnp = w;
+      g.lbx = log2_exact(bx);
       g.nbx = (sp->ntx + bx - 1) / bx;
       g.nNB = g.nbx * ((sp->nty + by - 1) / by);
       __half* rbase[3] = {sp->d_Rint, sp->d_R2, sp->np == 3 ? sp->d_R3 : sp->d_R2};
