@@ -180,15 +180,18 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   // stage u over padded rows y0-1 .. y0+RTY and columns x0-1 .. x0+RTX: the three wrapped
   // mesh columns of this thread first, then row by row
+  auto wrap = [](int v, int n) {  // v mod n in [0, n); one add or subtract in the usual case
+    if (v >= 0 && v < n) return v;
+    if (v < 0 && v >= -n) return v + n;
+    if (v >= n && v < 2 * n) return v - n;
+    v %= n;  // meshes smaller than the halo
+    return v < 0 ? v + n : v;
+  };
   int gx[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    int x = (x0 + tx + 32 * j - 1 - p.Hx) % p.nx;
-    gx[j] = x < 0 ? x + p.nx : x;
-  }
+  for (int j = 0; j < 3; ++j) gx[j] = wrap(x0 + tx + 32 * j - 1 - p.Hx, p.nx);
   for (int ly = ty; ly < RTY + 2; ly += 8) {
-    int y = (y0 + ly - 1 - p.Hy) % p.ny;
-    y = y < 0 ? y + p.ny : y;
+    const int y = wrap(y0 + ly - 1 - p.Hy, p.ny);
     const float* rh = uh + int64_t(y) * p.nx;
     const float* rl = ul + int64_t(y) * p.nx;
 #pragma unroll
@@ -202,30 +205,20 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
   }
   __syncthreads();
   float rabs = 0.0f;
-  auto one = [&](int cy, int cx) -> ffv {
-    // r = sum_nbr c_j (u_j - u_C) + (sum_all c) u_C, every term and the sum in float-float:
-    // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
-    // about log2(|c d| / |r|) bits of r.
-    const float ch = sh[cy][cx], cl = sl[cy][cx];
-    ffv acc{0.0f, 0.0f};
-    const ffv dW = ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl);
-    const ffv dE = ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl);
-    const ffv dS = ff_sub(sh[cy - 1][cx], sl[cy - 1][cx], ch, cl);
-    const ffv dN = ff_sub(sh[cy + 1][cx], sl[cy + 1][cx], ch, cl);
-    if (p.has_lo) {
-      ff_mac<true>(acc, p.c_hi[1], p.c_lo[1], dW);
-      ff_mac<true>(acc, p.c_hi[2], p.c_lo[2], dE);
-      ff_mac<true>(acc, p.c_hi[3], p.c_lo[3], dS);
-      ff_mac<true>(acc, p.c_hi[4], p.c_lo[4], dN);
-      ff_mac<true>(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
-    } else {
-      ff_mac<false>(acc, p.c_hi[1], 0.0f, dW);
-      ff_mac<false>(acc, p.c_hi[2], 0.0f, dE);
-      ff_mac<false>(acc, p.c_hi[3], 0.0f, dS);
-      ff_mac<false>(acc, p.c_hi[4], 0.0f, dN);
-      if (p.csum_hi != 0.0f) ff_mac<false>(acc, p.csum_hi, 0.0f, ffv{ch, cl});
-    }
-    return two_sum(acc.h, acc.l);  // normalised: |r.l| <= ulp(r.h) / 2
+  // r = sum_nbr c_j (u_j - u_C) + (sum_all c) u_C, every term and the sum in float-float:
+  // the W/E (S/N) differences of a smooth field nearly cancel, so a float sum would lose
+  // about log2(|c d| / |r|) bits of r. The first product starts the sum as 0 + p, 0 + pe
+  // (what adding it to a zero pair gives).
+  auto first = [&](float ch, float cl, ffv d) -> ffv {
+    const float q = __fmul_rn(ch, d.h);
+    float pe = fmaf(ch, d.h, -q);
+    if (p.has_lo) pe = fmaf(cl, d.h, pe);
+    pe = fmaf(ch, d.l, pe);
+    return {__fadd_rn(0.0f, q), __fadd_rn(0.0f, __fadd_rn(0.0f, pe))};
+  };
+  auto rest = [&](ffv& acc, float ch, float cl, ffv d) {
+    if (p.has_lo) ff_mac<true>(acc, ch, cl, d);
+    else ff_mac<false>(acc, ch, 0.0f, d);
   };
   // r 2^er = r_int + r2 (+ r3), split from the float-float value: r_int an integer, the
   // remainder t + l (t exact in float) rounded to FP16 twice. Three pieces carry about rb + 22
@@ -237,17 +230,36 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
     h2 = __float2half_rn(__fadd_rn(t, rl));
     h3 = __float2half_rn(__fadd_rn(__fsub_rn(t, __half2float(h2)), rl));  // t - r2 exact
   };
+  // Each thread forms columns tx and tx + 32 of four consecutive rows 4 ty .. 4 ty + 3, so the
+  // difference to the row above, u_N - u_C, is the next row's u_S - u_C negated (exactly: the
+  // float-float difference is antisymmetric under round-to-nearest).
+  const bool csum = p.has_lo || p.csum_hi != 0.0f;
 #pragma unroll
-  for (int k = 0; k < RTY / 8; ++k) {
-    const int ly = ty + 8 * k;
-    const int yp = y0 + ly;
-    if (yp >= p.prow) continue;
+  for (int j = 0; j < 2; ++j) {
+    const int lx = tx + 32 * j;
+    const int xp = x0 + lx;
+    if (xp >= wpad) continue;
+    const int cx = lx + 1;
+    const int cy0 = 4 * ty + 1;
+    // u_{row0} - u_{row0 - 1}: the first row's u_S - u_C, negated
+    ffv below = ff_sub(sh[cy0][cx], sl[cy0][cx], sh[cy0 - 1][cx], sl[cy0 - 1][cx]);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int lx = tx + 32 * j;
-      const int xp = x0 + lx;
-      if (xp >= wpad) continue;
-      const ffv r = one(ly + 1, lx + 1);
+    for (int k = 0; k < 4; ++k) {
+      const int cy = cy0 + k;
+      const int yp = y0 + cy - 1;
+      if (yp >= p.prow) break;
+      const float ch = sh[cy][cx], cl = sl[cy][cx];
+      const ffv dW = ff_sub(sh[cy][cx - 1], sl[cy][cx - 1], ch, cl);
+      const ffv dE = ff_sub(sh[cy][cx + 1], sl[cy][cx + 1], ch, cl);
+      const ffv dS{-below.h, -below.l};
+      const ffv dN = ff_sub(sh[cy + 1][cx], sl[cy + 1][cx], ch, cl);
+      below = dN;
+      ffv acc = first(p.c_hi[1], p.c_lo[1], dW);
+      rest(acc, p.c_hi[2], p.c_lo[2], dE);
+      rest(acc, p.c_hi[3], p.c_lo[3], dS);
+      rest(acc, p.c_hi[4], p.c_lo[4], dN);
+      if (csum) rest(acc, p.csum_hi, p.csum_lo, ffv{ch, cl});
+      const ffv r = two_sum(acc.h, acc.l);  // normalised: |r.l| <= ulp(r.h) / 2
       rabs = fmaxf(rabs, fabsf(r.h));
       if (measure) continue;
       __half h1, h2, h3;
