@@ -82,6 +82,9 @@ struct GemmGeom {
   int nbx;              // window blocks per row of the tile grid
   int bnp;              // windows per block (BNx * BNy <= BN, a multiple of 16): the MMA's N
   int lbx;              // log2 BNx (BNx is a power of two)
+  int balance;          // one problem: spread the last, partial wave's window rows over every CTA
+  float* part;          // balance: per CTA, the folded sums of a tile part it leaves to another CTA
+  unsigned* flags;      // balance: per CTA and lane quarter, the launch epoch of its stored part
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int drain_rows;       // three pieces: window rows per correction drain
   int kx;               // K columns loaded per window row: Wx rounded up to 16 (the MMA's K steps)
@@ -557,7 +560,7 @@ __device__ __forceinline__ void issue_six(uint32_t main, uint32_t corr, const St
 template <int BN, int NP, bool MULTI>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ SplitProblem one, const SplitProblem* __restrict__ many, int nprob,
-                      int nunits_many, int parity, int* err) {
+                      int nunits_many, int parity, int* err, unsigned epoch) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = Shape<BN, NP>::STAGES, STAGE_BYTES = Shape<BN, NP>::STAGE_BYTES;
@@ -606,16 +609,47 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tx0 = (nb % g.nbx) * g.BNx;
     ty0 = (nb / g.nbx) * g.BNy;
   };
-  // Work items: whole units u = unit0, + step, ... (kb1 = -1: all window rows of the unit)
-  auto next_seg = [&](int64_t& cur, int& u, int& kb0, int& kb1) -> bool {
-    if (cur >= nunits) return false;
-    u = int(cur);
-    kb0 = 0;
-    kb1 = -1;
-    cur += nunit_step;
+  // Work items (segments: unit u, window rows kb0 .. kb1 - 1; kb1 = -1: all rows of the unit).
+  // Without balance: whole units u = unit0, + step, ... With balance (one problem whose unit
+  // count is not a multiple of the grid): the full waves' units as before, then the window rows
+  // of the remaining units, laid end to end, in equal consecutive ranges, one per CTA; a unit
+  // whose rows fall to several CTAs is finished by the CTA holding its first rows (which it
+  // reaches last), after the others have stored the folded sums of their rows.
+  const bool balanced = !MULTI && one.g.balance;
+  const int waves = nunits / nunit_step;
+  const int tail0 = waves * nunit_step;  // first unit of the partial wave
+  const int64_t tail_rows = int64_t(nunits - tail0) * one.g.Wy;
+  auto range_start = [&](int c) { return int64_t(c) * tail_rows / nunit_step; };
+  struct Cur {
+    int w;      // whole units taken
+    int64_t q;  // next tail row (balance) or next unit (no balance)
+  };
+  auto next_seg = [&](Cur& cur, int& u, int& kb0, int& kb1) -> bool {
+    if (!balanced) {
+      if (cur.q >= nunits) return false;
+      u = int(cur.q);
+      kb0 = 0;
+      kb1 = -1;
+      cur.q += nunit_step;
+      return true;
+    }
+    if (cur.w < waves) {
+      u = unit0 + cur.w * nunit_step;
+      kb0 = 0;
+      kb1 = -1;
+      ++cur.w;
+      return true;
+    }
+    const int64_t q1 = range_start(unit0 + 1);
+    if (cur.q >= q1) return false;
+    const int Wy = one.g.Wy;
+    u = tail0 + int(cur.q / Wy);
+    kb0 = int(cur.q % Wy);
+    kb1 = int(kb0 + q1 - cur.q < Wy ? kb0 + q1 - cur.q : Wy);
+    cur.q += kb1 - kb0;
     return true;
   };
-  const int64_t cur0 = int64_t(unit0);
+  const Cur cur0{0, balanced ? range_start(unit0) : int64_t(unit0)};
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -660,7 +694,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int it = 0, issued = 0;
-      int64_t cur = cur0;
+      Cur cur = cur0;
       int u, kb0, kb1;
       while (!s_abort && next_seg(cur, u, kb0, kb1)) {
         int lu;
@@ -718,7 +752,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       int s = 0;         // ring slot of the next stage
       uint32_t ph = 0;   // its fill phase
       int cj = 0;        // DRAIN: correction buffer of the current row group (kc % 3)
-      int64_t cur = cur0;
+      Cur cur = cur0;
       int u, kb0, kb1;
       const uint32_t tiles_addr = ptx::smem_u32(tiles);
       for (; ok && next_seg(cur, u, kb0, kb1); ++lt) {
@@ -820,7 +854,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int lane_base = 32 * (warp & 3);  // tcgen05.ld: a warp reaches lane quarter warp % 4
     const int row = lane_base + lane;       // TMEM lane = owner row within the M block
     int lt = 0, kc = 0;
-    int64_t cur = cur0;
+    Cur cur = cur0;
     int u, kb0, kb1;
     for (; next_seg(cur, u, kb0, kb1); ++lt) {
       int lu;
@@ -910,6 +944,43 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
       };
       if constexpr (DRAIN) {
+        // balance: a part that does not start the unit stores its folded sums for the CTA
+        // holding the unit's first rows, which adds the later parts' sums (in row order)
+        const bool whole = kb0 == 0 && kb1 == g.Wy;
+        const int quarter = warp & 3;
+        if (!whole && kb0 > 0) {
+          float* dst = g.part + int64_t(blockIdx.x) * BN * BM + row;
+#pragma unroll
+          for (int q = 0; q < BN / 16; ++q) {
+            if (q * 16 >= g.bnp) break;
+            float vm[16];
+            ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[(q * 16 + i) * BM] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::mbar_arrive(&acce[b]);
+            ptx::mbar_arrive(&ce[fold]);
+          }
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) ptx::st_release_gpu(g.flags + blockIdx.x * 4 + quarter, epoch);
+          continue;
+        }
+        // the CTAs holding this unit's later rows (balance, a part starting the unit)
+        int partner0 = 0, npartners = 0;
+        if (!whole) {
+          const int64_t base = int64_t(u - tail0) * g.Wy;
+          partner0 = int(blockIdx.x) + 1;
+          // (every CTA's range holds at least one row: the host balances only then)
+          for (int c = partner0; c < nunit_step && range_start(c) < base + g.Wy; ++c) {
+            ++npartners;
+            if (lane == 0 && !ptx::wait_flag_gpu(g.flags + c * 4 + quarter, epoch, WAIT_NS)) atomicExch(err, ERR_TIMEOUT_EPI);
+          }
+          __syncwarp();
+        }
         // fold main + correction (FP32, as without the drain) into the last row group's
         // correction buffer and free main at once, so the next tile's MMAs start during the
         // scatter below; that buffer is released after the scatter
@@ -921,6 +992,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
 #pragma unroll
           for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
+          for (int p = 0; p < npartners; ++p) {
+            const float* src = g.part + int64_t(partner0 + p) * BN * BM + row + int64_t(q * 16) * BM;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], __ldcg(src + i * BM));
+          }
           ptx::tmem_st_32x32b_x16(t_fold + q * 16, vm);
         }
         ptx::tmem_wait_st();
@@ -960,7 +1036,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
 }
 
-using GemmKernel = void (*)(SplitProblem, const SplitProblem*, int, int, int, int*);
+using GemmKernel = void (*)(SplitProblem, const SplitProblem*, int, int, int, int*, unsigned);
 
 int gemm_threads(int) { return GEMM_THREADS; }
 
@@ -997,6 +1073,9 @@ struct SplitPlan {
   int* d_err = nullptr;
   int* d_rb = nullptr;
   SplitProblem prob{};  // tensor maps and GEMM geometry
+  float* d_part = nullptr;     // balance: per CTA, one stored tile part (BN x BM floats)
+  unsigned* d_flags = nullptr; // balance: per CTA and lane quarter, the epoch of its part
+  unsigned epoch = 0;          // GEMM launches so far (the flags' values)
   int packed_gen = -1;
 };
 
@@ -1167,6 +1246,25 @@ lem_status split_prepare(lem_ctx* ctx) {
     g.fault = f && std::strcmp(f, "timeout") == 0;
   }
   g.Pt = sp->d_Pt;
+  // balance the last, partial wave (three pieces, at least one full wave, and at least 8 of its
+  // window rows per CTA, so every CTA's range is a real part; LEM_SPLIT_BALANCE=0 keeps whole
+  // units, for comparison)
+  {
+    const int units = g.nMB * g.nNB;
+    const int64_t tail_rows = int64_t(units % sp->nsm) * g.Wy;
+    const char* e = std::getenv("LEM_SPLIT_BALANCE");
+    g.balance = sp->np == 3 && units > sp->nsm && units % sp->nsm != 0 && tail_rows >= int64_t(8) * sp->nsm &&
+                !(e && std::strcmp(e, "0") == 0);
+    g.part = nullptr;
+    g.flags = nullptr;
+    if (g.balance) {
+      LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_part), sizeof(float) * size_t(sp->nsm) * sp->bn * BM));
+      LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_flags), sizeof(unsigned) * size_t(sp->nsm) * 4));
+      LEM_CUDA_TRY(cudaMemsetAsync(sp->d_flags, 0, sizeof(unsigned) * size_t(sp->nsm) * 4, ctx->stream));
+      g.part = sp->d_part;
+      g.flags = sp->d_flags;
+    }
+  }
   g.eP = sp->d_eP; g.escale = sp->d_escale; g.rmax = sp->d_rmax; g.uh = sp->d_uh; g.ul = sp->d_ul;
   cudaFuncAttributes fa{};
   LEM_CUDA_TRY(cudaFuncGetAttributes(&fa, gemm_kernel_for(sp->bn, sp->np)));
@@ -1238,7 +1336,7 @@ lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d
     cudaEvent_t stop;
     LEM_CUDA_TRY(ctx->timing_begin(&stop));
     LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(sp->bn, sp->np), prob,
-                                    static_cast<const SplitProblem*>(nullptr), 1, 0, parity, sp->d_err));
+                                    static_cast<const SplitProblem*>(nullptr), 1, 0, parity, sp->d_err, ++sp->epoch));
     ctx->timing_end(stop);
   }
   LEM_CUDA_TRY(cudaGetLastError());
@@ -1429,7 +1527,8 @@ lem_status split_batch_step(SplitBatch* b, int nsteps, cudaStream_t st, cudaEven
     residual_multi_kernel<<<b->res_blocks, 256, 0, st>>>(b->d_res, b->d_res_first, b->n, parity, 0);
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[1 + 2 * k], st));
     LEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_kernel_for(b->bn, b->np, true), b->first,
-                                    static_cast<const SplitProblem*>(b->d_probs), b->n, b->nunits, parity, b->d_err));
+                                    static_cast<const SplitProblem*>(b->d_probs), b->n, b->nunits, parity, b->d_err,
+                                    0u));
     if (ev) LEM_CUDA_TRY(cudaEventRecord(ev[2 + 2 * k], st));
   }
   convert_multi_kernel<<<b->conv_blocks, 256, 0, st>>>(b->d_conv, b->d_conv_first, b->n, 0);
@@ -1480,7 +1579,8 @@ void split_destroy(lem_ctx* ctx) {
                   static_cast<void*>(sp->d_R2), static_cast<void*>(sp->d_Pt),
                   static_cast<void*>(sp->d_eP), static_cast<void*>(sp->d_S),
                   static_cast<void*>(sp->d_R3), static_cast<void*>(sp->d_rmax), static_cast<void*>(sp->d_escale),
-                  static_cast<void*>(sp->d_err), static_cast<void*>(sp->d_rb)})
+                  static_cast<void*>(sp->d_err), static_cast<void*>(sp->d_rb), static_cast<void*>(sp->d_part),
+                  static_cast<void*>(sp->d_flags)})
     if (p) cudaFreeAsync(p, ctx->stream);  // stream-ordered (the memory came from cudaMallocAsync)
   delete sp;
   ctx->split = nullptr;

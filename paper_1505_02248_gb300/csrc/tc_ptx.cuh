@@ -52,6 +52,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// ---------------------------------------------------------------- flags between CTAs
+// publish v at *p after this thread's earlier writes (release, GPU scope)
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// wait until *p == v (acquire, GPU scope) for at most limit_ns; false on timeout
+__device__ __forceinline__ bool wait_flag_gpu(const unsigned* p, unsigned v, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    unsigned x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    if (x == v) return true;
+    if ((it & 63u) == 63u && globaltimer() - t0 > limit_ns) return false;
+  }
+}
+
 // ---------------------------------------------------------------- TMA
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
