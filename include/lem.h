@@ -177,8 +177,12 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps);
 
 /* Same as lem_step on a HOST state (pinned or pageable): copies it to the device,
  * advances nsteps, copies it back and synchronises. The first call allocates a device copy
- * of the state, kept by the context. Errors: those of lem_step, LEM_ENOMEM, LEM_ETIMEOUT
- * (a bounded wait in a tensor-core kernel expired), LEM_ECUDA. */
+ * of the state, kept by the context. On the tensor-core split path (apply path
+ * LEM_APPLY_TC_SPLIT, propagators built) with pinned host memory that is mapped into the
+ * device's address space, the state is read and written in place by the kernels that convert
+ * it to and from the float-float state instead (same results, no device copy).
+ * Errors: those of lem_step, LEM_ENOMEM, LEM_ETIMEOUT (a bounded wait in a tensor-core kernel
+ * expired), LEM_ECUDA. */
 lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps);
 
 /* Copy class `cls`'s propagator (n_int x n_loc, row-major, FP64, zero padded) into host

@@ -339,6 +339,19 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   if (!h_state) return fail(LEM_EINVAL, "state is NULL");
   DeviceGuard g(ctx->device);
+  // The tensor-core split path reads the FP64 state once (into its float-float state) and
+  // writes it once at the end. When the host buffer is pinned memory mapped into the device's
+  // address space, those two kernels use it in place: one pass over the host link each way
+  // and no separate copies.
+  if (ctx->split && ctx->built && ctx->band_tol < 0.0 && nsteps > 0) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, h_state) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+      LEM_TRY(lem_step(ctx, static_cast<double*>(at.devicePointer), nsteps));
+      LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      return split_check_error(ctx);
+    }
+    cudaGetLastError();  // (pageable memory: the query's error, if any, is not the caller's)
+  }
   const size_t bytes = sizeof(double) * ctx->npts * (ctx->cplx ? 2 : 1);
   if (!ctx->d_state_tmp) LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->d_state_tmp), bytes));
   LEM_CUDA_TRY(cudaMemcpyAsync(ctx->d_state_tmp, h_state, bytes, cudaMemcpyHostToDevice, ctx->stream));

@@ -202,3 +202,23 @@ def test_split_rough_decaying_field_100_steps():
         errs[prec] = rel_l2(u.cpu().numpy(), ref)
     print(f"rough decaying 64^2, 100 steps: rel_l2 {errs}")
     assert errs["split"] <= TOL_SPLIT_100
+
+
+@pytest.mark.parametrize("prec", ["split", "split_fast"])
+def test_step_host_pinned_pageable_and_device_agree_bit_for_bit(prec):
+    """lem_step_host on a split context: with a pinned host buffer the conversion kernels read
+    and write it in place, with a pageable one it is copied; both give the device step's bits."""
+    wl = W.advdiff2d(side=256, ell=8.0, seed=31)
+    dev, pin, pag = (L.Lem.from_workload(wl, prec=prec) for _ in range(3))
+    u = torch.tensor(wl["u0"], device="cuda")
+    dev.step(u, 6)
+    dev.sync()
+    pin.build()  # (the in-place path takes built contexts)
+    assert L.APPLY_PATHS[pin.info()["apply_path"]] == "tc_split"
+    hp = torch.tensor(wl["u0"]).pin_memory()
+    pin.step_host(hp.numpy(), 6)
+    hq = wl["u0"].copy()
+    pag.step_host(hq, 6)
+    ref = u.cpu().numpy()
+    assert np.array_equal(hp.numpy(), ref)
+    assert np.array_equal(hq, ref)
