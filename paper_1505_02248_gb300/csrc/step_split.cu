@@ -62,13 +62,14 @@ struct Shape {
   static constexpr int NBUF = BN == 256 ? 1 : 2;                    // TMEM accumulator sets
   static_assert(STAGES >= 2, "at least two stages");
 };
-// Thread roles: warp 0 TMA producer, warp 1 MMA issuer, warps 2-5 the epilogue (one per
-// TMEM lane quarter). With two pieces the epilogue reads the accumulators once per tile. With
-// three pieces (DRAIN) it also drains the correction accumulator into registers after every
-// window row: the tensor pipe's FP32 accumulation of the correction then spans only
-// 5 * ceil(Wx/16) MMAs, and the sum over window rows is a correctly rounded FP32 add. (Six
-// warps keep the 255-register limit: an SM sub-partition holds at most two of them.)
-constexpr int EPI_WARPS = 4;
+// Thread roles: warp 0 TMA producer, warp 1 MMA issuer, warps 2-9 the epilogue, two per TMEM
+// lane quarter (warp % 4), the one of warps 2-5 taking the even 32-column blocks of the
+// accumulators and the one of warps 6-9 the odd ones. With two pieces the epilogue reads the
+// accumulators once per tile. With three pieces (DRAIN) it also drains the correction
+// accumulator into registers after every window row: the tensor pipe's FP32 accumulation of
+// the correction then spans only 5 * ceil(Wx/16) MMAs, and the sum over window rows is a
+// correctly rounded FP32 add. Two warps per quarter halve each drain and each scatter.
+constexpr int EPI_WARPS = 8;
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int P_INT_BITS = 9;            // |P_int| <= 2^9
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
@@ -84,7 +85,7 @@ struct GemmGeom {
   int lbx;              // log2 BNx (BNx is a power of two)
   int balance;          // one problem: spread the last, partial wave's window rows over every CTA
   float* part;          // balance: per CTA, the folded sums of a tile part it leaves to another CTA
-  unsigned* flags;      // balance: per CTA and lane quarter, the launch epoch of its stored part
+  unsigned* flags;      // balance: per CTA and epilogue warp, the launch epoch of its stored part
   int nMB, nNB;         // M blocks of 128 owner rows, window blocks of BN windows
   int drain_rows;       // three pieces: window rows per correction drain
   int kx;               // K columns loaded per window row: Wx rounded up to 16 (the MMA's K steps)
@@ -853,6 +854,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ------------------------------------------------------------ epilogue
     const int lane_base = 32 * (warp & 3);  // tcgen05.ld: a warp reaches lane quarter warp % 4
     const int row = lane_base + lane;       // TMEM lane = owner row within the M block
+    const int half = (warp - 2) >> 2;       // this warp's 32-column blocks: 2 lb + half
+    constexpr int NLB = BN / 64;            // 32-column blocks per warp
     int lt = 0, kc = 0;
     Cur cur = cur0;
     int u, kb0, kb1;
@@ -862,11 +865,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       if (kb1 < 0) kb1 = g.Wy;
       const int nbuf = DRAIN ? 1 : NBUF;
       const int b = lt % nbuf;
-      float cs[DRAIN ? BN : 1];  // DRAIN: correction summed over row groups
-      int fold = 0;              // DRAIN: the correction buffer of the tile's last row group
+      float cs[DRAIN ? BN / 2 : 1];  // DRAIN: correction summed over row groups (this warp's columns)
+      int fold = 0;                  // DRAIN: the correction buffer of the tile's last row group
       if constexpr (DRAIN) {
 #pragma unroll
-        for (int i = 0; i < BN; ++i) cs[i] = 0.0f;
+        for (int i = 0; i < BN / 2; ++i) cs[i] = 0.0f;
         bool ok = true;
         const int ngroups = (kb1 - kb0 + g.drain_rows - 1) / g.drain_rows;
         for (int gi = 0; gi < ngroups; ++gi, ++kc) {
@@ -875,12 +878,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           ptx::tc_fence_after();
           const uint32_t tc = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + j) * BN);
 #pragma unroll
-          for (int h = 0; h < BN / 64; ++h) {  // 64 columns per load round trip
-            if (h * 64 >= g.bnp) break;       // (columns past bnp hold nothing of this unit)
-            uint32_t r[64];
-            ptx::tmem_ld_32x32b_x64(tc + h * 64, r);
+          for (int lb = 0; lb < NLB; ++lb) {  // 32 columns per load round trip
+            const int col0 = (2 * lb + half) * 32;
+            if (col0 >= g.bnp) break;        // (columns past bnp hold nothing of this unit)
+            uint32_t r[32];
+            ptx::tmem_ld_32x32b_x32(tc + col0, r);
 #pragma unroll
-            for (int i = 0; i < 64; ++i) cs[h * 64 + i] = __fadd_rn(cs[h * 64 + i], __uint_as_float(r[i]));
+            for (int i = 0; i < 32; ++i) cs[lb * 32 + i] = __fadd_rn(cs[lb * 32 + i], __uint_as_float(r[i]));
           }
           if (gi + 1 < ngroups) {  // the last buffer stays held: it receives the folded sum
             ptx::tc_fence_before();
@@ -910,8 +914,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int rowbase = iy * g.nx + ix;
       float* __restrict__ uh = g.uh;
       float* __restrict__ ul = g.ul;
-      // one batch of NB windows (columns c0 .. c0 + NB - 1): y = (main + corr) 2^-(eP_i + er)
-      // added into the owner nodes
       // one batch of 16 windows (columns c0 .. c0 + 15): y = (main + corr) 2^-(eP_i + er) added
       // into the owner nodes
       auto batch = [&](int c0, const float (&vm)[16], const float (&vc)[16]) {
@@ -947,16 +949,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // balance: a part that does not start the unit stores its folded sums for the CTA
         // holding the unit's first rows, which adds the later parts' sums (in row order)
         const bool whole = kb0 == 0 && kb1 == g.Wy;
-        const int quarter = warp & 3;
+        const int ew = warp - 2;  // this epilogue warp's flag
         if (!whole && kb0 > 0) {
           float* dst = g.part + int64_t(blockIdx.x) * BN * BM + row;
 #pragma unroll
-          for (int q = 0; q < BN / 16; ++q) {
-            if (q * 16 >= g.bnp) break;
-            float vm[16];
-            ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+          for (int lb = 0; lb < NLB; ++lb) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dst[(q * 16 + i) * BM] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
+            for (int c = 0; c < 2; ++c) {
+              const int col0 = (2 * lb + half) * 32 + c * 16;
+              if (col0 >= g.bnp) break;
+              float vm[16];
+              ptx::tmem_ld_32x32b_x16(t_lane + col0, vm);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) dst[(col0 + i) * BM] = __fadd_rn(vm[i], cs[(lb * 32 + c * 16 + i) % (DRAIN ? BN / 2 : 1)]);
+            }
           }
           ptx::tc_fence_before();
           __syncwarp();
@@ -966,7 +972,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           }
           __threadfence();
           __syncwarp();
-          if (lane == 0) ptx::st_release_gpu(g.flags + blockIdx.x * 4 + quarter, epoch);
+          if (lane == 0) ptx::st_release_gpu(g.flags + blockIdx.x * EPI_WARPS + ew, epoch);
           continue;
         }
         // the CTAs holding this unit's later rows (balance, a part starting the unit)
@@ -977,7 +983,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // (every CTA's range holds at least one row: the host balances only then)
           for (int c = partner0; c < nunit_step && range_start(c) < base + g.Wy; ++c) {
             ++npartners;
-            if (lane == 0 && !ptx::wait_flag_gpu(g.flags + c * 4 + quarter, epoch, WAIT_NS)) atomicExch(err, ERR_TIMEOUT_EPI);
+            if (lane == 0 && !ptx::wait_flag_gpu(g.flags + c * EPI_WARPS + ew, epoch, WAIT_NS))
+              atomicExch(err, ERR_TIMEOUT_EPI);
           }
           __syncwarp();
         }
@@ -986,18 +993,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // scatter below; that buffer is released after the scatter
         const uint32_t t_fold = tmem + (uint32_t(lane_base) << 16) + uint32_t((1 + fold) * BN);
 #pragma unroll
-        for (int q = 0; q < BN / 16; ++q) {  // unrolled: cs is indexed statically
-          if (q * 16 >= g.bnp) break;
-          float vm[16];
-          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
+        for (int lb = 0; lb < NLB; ++lb) {  // unrolled: cs is indexed statically
 #pragma unroll
-          for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], cs[(q * 16 + i) % (DRAIN ? BN : 1)]);
-          for (int p = 0; p < npartners; ++p) {
-            const float* src = g.part + int64_t(partner0 + p) * BN * BM + row + int64_t(q * 16) * BM;
+          for (int c = 0; c < 2; ++c) {
+            const int col0 = (2 * lb + half) * 32 + c * 16;
+            if (col0 >= g.bnp) break;
+            float vm[16];
+            ptx::tmem_ld_32x32b_x16(t_lane + col0, vm);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], __ldcg(src + i * BM));
+            for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], cs[(lb * 32 + c * 16 + i) % (DRAIN ? BN / 2 : 1)]);
+            for (int p = 0; p < npartners; ++p) {
+              const float* src = g.part + int64_t(partner0 + p) * BN * BM + row + int64_t(col0) * BM;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) vm[i] = __fadd_rn(vm[i], __ldcg(src + i * BM));
+            }
+            ptx::tmem_st_32x32b_x16(t_fold + col0, vm);
           }
-          ptx::tmem_st_32x32b_x16(t_fold + q * 16, vm);
         }
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
@@ -1005,23 +1016,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) ptx::mbar_arrive(&acce[b]);
         const float zero[16] = {};
 #pragma unroll 1
-        for (int q = 0; q < g.bnp / 16; ++q) {
-          float vm[16];
-          ptx::tmem_ld_32x32b_x16(t_fold + q * 16, vm);
-          batch(q * 16, vm, zero);
-        }
+        for (int lb = 0; lb < NLB; ++lb)
+          for (int c = 0; c < 2; ++c) {
+            const int col0 = (2 * lb + half) * 32 + c * 16;
+            if (col0 >= g.bnp) break;
+            float vm[16];
+            ptx::tmem_ld_32x32b_x16(t_fold + col0, vm);
+            batch(col0, vm, zero);
+          }
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&ce[fold]);
         continue;
       } else {
 #pragma unroll 1
-        for (int q = 0; q < g.bnp / 16; ++q) {
-          float vm[16], vc[16];
-          ptx::tmem_ld_32x32b_x16(t_lane + q * 16, vm);
-          ptx::tmem_ld_32x32b_x16(t_lane + BN + q * 16, vc);
-          batch(q * 16, vm, vc);
-        }
+        for (int lb = 0; lb < NLB; ++lb)
+          for (int c = 0; c < 2; ++c) {
+            const int col0 = (2 * lb + half) * 32 + c * 16;
+            if (col0 >= g.bnp) break;
+            float vm[16], vc[16];
+            ptx::tmem_ld_32x32b_x16(t_lane + col0, vm);
+            ptx::tmem_ld_32x32b_x16(t_lane + BN + col0, vc);
+            batch(col0, vm, vc);
+          }
       }
       ptx::tc_fence_before();
       __syncwarp();
@@ -1074,7 +1091,7 @@ struct SplitPlan {
   int* d_rb = nullptr;
   SplitProblem prob{};  // tensor maps and GEMM geometry
   float* d_part = nullptr;     // balance: per CTA, one stored tile part (BN x BM floats)
-  unsigned* d_flags = nullptr; // balance: per CTA and lane quarter, the epoch of its part
+  unsigned* d_flags = nullptr; // balance: per CTA and epilogue warp, the epoch of its part
   unsigned epoch = 0;          // GEMM launches so far (the flags' values)
   int packed_gen = -1;
 };
@@ -1259,8 +1276,8 @@ lem_status split_prepare(lem_ctx* ctx) {
     g.flags = nullptr;
     if (g.balance) {
       LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_part), sizeof(float) * size_t(sp->nsm) * sp->bn * BM));
-      LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_flags), sizeof(unsigned) * size_t(sp->nsm) * 4));
-      LEM_CUDA_TRY(cudaMemsetAsync(sp->d_flags, 0, sizeof(unsigned) * size_t(sp->nsm) * 4, ctx->stream));
+      LEM_TRY(dev_alloc(ctx, reinterpret_cast<void**>(&sp->d_flags), sizeof(unsigned) * size_t(sp->nsm) * EPI_WARPS));
+      LEM_CUDA_TRY(cudaMemsetAsync(sp->d_flags, 0, sizeof(unsigned) * size_t(sp->nsm) * EPI_WARPS, ctx->stream));
       g.part = sp->d_part;
       g.flags = sp->d_flags;
     }
