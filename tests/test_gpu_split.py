@@ -222,3 +222,28 @@ def test_step_host_pinned_pageable_and_device_agree_bit_for_bit(prec):
     ref = u.cpu().numpy()
     assert np.array_equal(hp.numpy(), ref)
     assert np.array_equal(hq, ref)
+
+
+def test_balanced_last_wave_matches_whole_units(monkeypatch):
+    """1792^2 (tiles 32, 224 units of 128 owner rows x 128 windows on a 152-SM GB300): the
+    full wave runs whole units and the remaining 72 units' window rows are spread over every
+    CTA, a split unit finished by the CTA holding its first rows. The result must agree with
+    whole units (LEM_SPLIT_BALANCE=0) up to the order of the correction sums, and both with
+    the FP64 GPU LEM within the split tier's bar."""
+    wl = W.advdiff2d(side=1792, seed=7)
+    steps = 30
+    monkeypatch.setenv("LEM_SPLIT_BALANCE", "0")
+    whole = L.Lem.from_workload(wl, prec="split")
+    monkeypatch.delenv("LEM_SPLIT_BALANCE")
+    bal = L.Lem.from_workload(wl, prec="split")
+    fp64 = L.Lem.from_workload(wl, prec="fp64")
+    u_b = torch.tensor(wl["u0"], device="cuda")
+    u_w = torch.tensor(wl["u0"], device="cuda")
+    u_d = torch.tensor(wl["u0"], device="cuda")
+    bal.step(u_b, steps)
+    whole.step(u_w, steps)
+    fp64.step(u_d, steps)
+    torch.cuda.synchronize()
+    b, w, d = (x.cpu().numpy() for x in (u_b, u_w, u_d))
+    assert rel_l2(b, w) <= 1e-8
+    assert rel_l2(b, d) <= TOL_SPLIT_100 and rel_l2(w, d) <= TOL_SPLIT_100
