@@ -128,7 +128,7 @@ def fp64_dgemm_tflops(dev, n=8192, reps=5):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("step_split.cu", "tc_ptx.cuh"):
+    for name in ("step_split.cu", "tc_ptx.cuh", "ff_convert.h"):
         with open(os.path.join(ROOT, "paper_1505_02248_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -532,11 +532,12 @@ def run_batch(a):
                                   ("block_cap" if c["fused"] else "lanes"): c["n_cap"] if c["fused"] else c["lanes"],
                                   "ms": round(c["ms"], 4), "chosen": bool(c["chosen"])} for c in cands],
                    "lane_load_ms": {"max": float(loads.max()), "mean": float(loads.mean())}},
-        # per problem and launch: FP64->float-float, max|r| pass, (residual + GEMM) per LEM
-        # step, float-float->FP64 (split); residual, gather, GEMM, scatter per step (FP64)
-        # fused: conversion, max|r| pass, (residual + GEMM) per LEM step, conversion back
+        # per problem and launch (lanes): max|r| pass (with the FP64 -> float-float conversion),
+        # (residual + GEMM) per LEM step, float-float -> FP64 (split); residual, gather, GEMM,
+        # scatter per step (FP64). Fused: conversion, max|r| pass, (residual + GEMM) per LEM
+        # step, conversion back
         "gpu_launches": a.steps * (3 + 2 * a.inner) if sched["fused"] else
-        a.steps * sum((3 + 2 * a.inner) if L.APPLY_PATHS[c.info()["apply_path"]] == "tc_split"
+        a.steps * sum((2 + 2 * a.inner) if L.APPLY_PATHS[c.info()["apply_path"]] == "tc_split"
                       else 4 * a.inner for c in ctxs),
     }
     if gemm_n:
@@ -951,9 +952,9 @@ def main():
                    "propagator": f"{info['n_int']}x{info['n_loc']} phi_1 (shared)", "lem_steps_per_step": a.inner,
                    "prec": a.prec, "apply_path": path, "l2": "256 MiB write between timed steps",
                    "parallelism": f"replicas x{world}", "build_ms": round(build_ms, 1)},
-        # split: FP64->float-float, max|r| pass, (residual + GEMM) per LEM step, float-float->FP64;
-        # FP64: residual, gather, GEMM, scatter per LEM step
-        "gpu_launches": a.steps * ((3 + 2 * a.inner) if path == "tc_split" else
+        # split: max|r| pass (which also converts FP64 -> float-float), (residual + GEMM) per LEM
+        # step, float-float -> FP64; FP64: residual, gather, GEMM, scatter per LEM step
+        "gpu_launches": a.steps * ((2 + 2 * a.inner) if path == "tc_split" else
                                    a.inner * (2 if "gemv" in path else 4)),
     }
     if gemm_launches:

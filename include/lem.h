@@ -169,7 +169,9 @@ lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state);
 /* Advance the device state d_state (FP64, row-major, in/out; complex: interleaved pairs) by
  * nsteps LEM steps (Sec. 3 steps 1-3). Builds the propagators first if they do not exist;
  * for a nonlinear problem (reaction 1 or 2) it rebuilds them every `refresh` steps. Small linear real problems on
- * the GEMV paths run all nsteps in one cooperative launch (identical results). Work is
+ * the GEMV paths run all nsteps in one cooperative launch (identical results). On the
+ * tensor-core split path the call's first kernel (the first step's measuring residual pass)
+ * reads d_state, converting it to the float-float state the steps run on. Work is
  * enqueued on the context stream; the call returns after enqueueing (no synchronisation)
  * unless a rebuild is due.
  * Errors: LEM_EINVAL (nsteps < 0, NULL state), LEM_ECUDA. */

@@ -299,7 +299,9 @@ lem_status lem_build_propagators(lem_ctx* ctx, const double* d_state) {
   return LEM_OK;  // the split path repacks the new propagator lazily (build_gen)
 }
 
-lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
+// lem_step's work; device_state false: d_state is mapped host memory, which the split path
+// reads with a separate streaming conversion rather than in its first stencil pass
+static lem_status step_impl(lem_ctx* ctx, double* d_state, int nsteps, bool device_state) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   if (!d_state) return fail(LEM_EINVAL, "state is NULL");
   if (nsteps < 0) return fail(LEM_EINVAL, "nsteps < 0");
@@ -316,7 +318,7 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
     }
     return LEM_OK;
   }
-  if (ctx->split) return split_step(ctx, d_state, nsteps);
+  if (ctx->split) return split_step(ctx, d_state, nsteps, device_state);
   if (ctx->apply_path == LEM_APPLY_FP64_GEMV || ctx->apply_path == LEM_APPLY_F32_GEMV) {
     bool done = false;  // small linear problems: every step in one persistent launch
     LEM_TRY(step_gemv_multi(ctx, d_state, nsteps, ctx->apply_path == LEM_APPLY_F32_GEMV, &done));
@@ -335,6 +337,8 @@ lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) {
   return LEM_OK;
 }
 
+lem_status lem_step(lem_ctx* ctx, double* d_state, int nsteps) { return step_impl(ctx, d_state, nsteps, true); }
+
 lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
   if (!ctx) return fail(LEM_EINVAL, "ctx is NULL");
   if (!h_state) return fail(LEM_EINVAL, "state is NULL");
@@ -346,7 +350,7 @@ lem_status lem_step_host(lem_ctx* ctx, double* h_state, int nsteps) {
   if (ctx->split && ctx->built && ctx->band_tol < 0.0 && nsteps > 0) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, h_state) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
-      LEM_TRY(lem_step(ctx, static_cast<double*>(at.devicePointer), nsteps));
+      LEM_TRY(step_impl(ctx, static_cast<double*>(at.devicePointer), nsteps, false));
       LEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
       return split_check_error(ctx);
     }

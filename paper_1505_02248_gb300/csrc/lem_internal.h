@@ -154,11 +154,17 @@ lem_status step_gemv_multi(lem_ctx* ctx, double* d_u, int nsteps, bool f32, bool
 lem_status gemv_set_smem(lem_ctx* ctx);
 // step_split.cu
 lem_status split_prepare(lem_ctx* ctx);
-lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps);
+// nsteps split steps of the FP64 state d_u. fuse_io: the first kernel of the run (the measuring
+// residual pass) reads d_u itself (a state in device memory); otherwise a separate streaming
+// conversion does (a state in mapped host memory, read once over the link). A streaming
+// conversion writes the result back either way.
+lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps, bool fuse_io);
 // the steps of split_step on a resident float-float state, with the residual scale carried
 // across calls through d_carry (one unsigned on the device; carry_in: it holds the previous
-// step's max|r|), and the conversions split_step does around them
-lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in);
+// step's max|r|), and the conversions split_step does around them. in64 (with carry_in false):
+// the measuring pass reads the FP64 state there and writes (uh, ul) from it.
+lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in,
+                     const double* in64 = nullptr);
 lem_status split_to_ff(lem_ctx* ctx, const double* d_u, float* uh, float* ul);
 lem_status split_from_ff(lem_ctx* ctx, const float* uh, const float* ul, double* d_u);
 void split_destroy(lem_ctx* ctx);

@@ -35,6 +35,7 @@
 #include <string>
 #include <vector>
 
+#include "ff_convert.h"
 #include "lem_internal.h"
 #include "tc_ptx.cuh"
 
@@ -168,10 +169,16 @@ constexpr int RTX = 64, RTY = 32;  // residual output tile (padded coordinates) 
 // per block. Each thread then forms the outputs of columns tx and tx + 32 in four rows, so a
 // warp's shared-memory reads and its FP16 stores are consecutive (no bank conflicts).
 // measure != 0: only accumulate max|r| into rmax[parity ^ 1].
+// FROM64: the patch comes from the FP64 state u64 instead, converted to float-float as it is
+// staged, and the padded interior's nodes (each mesh node once over the grid) also write that
+// float-float state to (oh, ol).
+template <bool FROM64 = false>
 __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, const float* __restrict__ ul,
                                               __half* __restrict__ Rint, __half* __restrict__ R2,
                                               __half* __restrict__ R3, const ResParams& p, unsigned* rmax,
-                                              int* escale, int parity, int measure, int bx, int by) {
+                                              int* escale, int parity, int measure, int bx, int by,
+                                              const double* __restrict__ u64 = nullptr, float* __restrict__ oh = nullptr,
+                                              float* __restrict__ ol = nullptr) {
   constexpr int SW = RTX + 3;  // staged row stride (odd: conflict-free column reads)
   __shared__ float sh[RTY + 2][SW], sl[RTY + 2][SW];
   __shared__ float red[8];
@@ -196,14 +203,36 @@ __device__ __forceinline__ void residual_tile(const float* __restrict__ uh, cons
   for (int j = 0; j < 3; ++j) gx[j] = wrap(x0 + tx + 32 * j - 1 - p.Hx, p.nx);
   for (int ly = ty; ly < RTY + 2; ly += 8) {
     const int y = wrap(y0 + ly - 1 - p.Hy, p.ny);
-    const float* rh = uh + int64_t(y) * p.nx;
-    const float* rl = ul + int64_t(y) * p.nx;
+    if constexpr (FROM64) {
+      const double* rv = u64 + int64_t(y) * p.nx;
+      // padded row yp = y0 + ly - 1 inside [Hy, Hy + ny) is mesh row y = yp - Hy
+      const int yp = y0 + ly - 1;
+      const bool row_own = ly >= 1 && ly <= RTY && yp >= p.Hy && yp < p.Hy + p.ny;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int lx = tx + 32 * j;
-      if (lx < RTX + 2) {
-        sh[ly][lx] = rh[gx[j]];
-        sl[ly][lx] = rl[gx[j]];
+      for (int j = 0; j < 3; ++j) {
+        const int lx = tx + 32 * j;
+        if (lx < RTX + 2) {
+          float h, l;
+          f64_to_pair(rv[gx[j]], h, l);
+          sh[ly][lx] = h;
+          sl[ly][lx] = l;
+          const int xp = x0 + lx - 1;  // inside [Hx, Hx + nx): mesh column gx[j] = xp - Hx
+          if (row_own && lx >= 1 && lx <= RTX && xp >= p.Hx && xp < p.Hx + p.nx) {
+            oh[int64_t(y) * p.nx + gx[j]] = h;
+            ol[int64_t(y) * p.nx + gx[j]] = l;
+          }
+        }
+      }
+    } else {
+      const float* rh = uh + int64_t(y) * p.nx;
+      const float* rl = ul + int64_t(y) * p.nx;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int lx = tx + 32 * j;
+        if (lx < RTX + 2) {
+          sh[ly][lx] = rh[gx[j]];
+          sl[ly][lx] = rl[gx[j]];
+        }
       }
     }
   }
@@ -303,6 +332,16 @@ __global__ void __launch_bounds__(256) residual_split_kernel(const float* __rest
   residual_tile(uh, ul, Rint, R2, R3, p, rmax, escale, parity, measure, int(blockIdx.x), int(blockIdx.y));
 }
 
+// The measuring pass (max|r| of the first step into rmax[0]) on the FP64 state u64, which it
+// also converts to the float-float state (uh, ul) the steps run on.
+__global__ void __launch_bounds__(256) residual_measure_f64_kernel(const double* __restrict__ u64,
+                                                                   float* __restrict__ uh, float* __restrict__ ul,
+                                                                   ResParams p, unsigned* rmax, int* escale) {
+  pdl_wait_and_release();
+  residual_tile<true>(nullptr, nullptr, nullptr, nullptr, nullptr, p, rmax, escale, 1, 1, int(blockIdx.x),
+                      int(blockIdx.y), u64, uh, ul);
+}
+
 // One problem of a multi-problem step: its residual arrays, parameters and block range.
 struct ResProblem {
   ResParams p;
@@ -337,50 +376,6 @@ __global__ void __launch_bounds__(256) residual_multi_kernel(const ResProblem* _
   residual_tile(q.uh, q.ul, q.Rint, q.R2, q.R3, q.p, q.rmax, q.escale, parity, measure, lb % q.gx, lb / q.gx);
 }
 
-// FP64 -> float-float: h = v rounded to the nearest float, l = v - h rounded to the nearest
-// float, the values the FP64 conversions give, built from the bits with integer operations (an
-// FP64 conversion issues on this part's slow FP64 pipe). Exponents outside [-70, 100] (zero
-// included) take the FP64 conversions.
-__device__ __forceinline__ void f64_to_pair(double v, float& h, float& l) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int E = int((b >> 52) & 0x7FFull) - 1023;
-  if (E < -70 || E > 100) {
-    h = __double2float_rn(v);
-    l = __double2float_rn(v - double(h));
-    return;
-  }
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
-  unsigned long long q = m >> 29;                                          // 24 bits
-  const unsigned long long rem = m & ((1ull << 29) - 1);
-  if (rem > (1ull << 28) || (rem == (1ull << 28) && (q & 1ull))) ++q;     // round to nearest even
-  const int diff = int(static_cast<long long>(m) - static_cast<long long>(q << 29));  // |diff| <= 2^28
-  int e = E;
-  if (q == (1ull << 24)) {  // rounded up to the next binade
-    q >>= 1;
-    ++e;
-  }
-  const unsigned sign = unsigned(b >> 63) << 31;
-  h = __uint_as_float(sign | (unsigned(e + 127) << 23) | unsigned(q & 0x7FFFFFull));
-  // v - h = sign * diff * 2^(E - 52), exact; its nearest float (+0 when it is 0, as in FP64)
-  const float lf = __int2float_rn(diff) * __int_as_float((E - 52 + 127) << 23);
-  l = diff == 0 ? 0.0f : __uint_as_float(__float_as_uint(lf) ^ sign);
-}
-
-// float -> double from the bits (exact); zeros keep their sign, subnormals, infinities and NaN
-// take the FP64 conversion
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned ex = (b >> 23) & 0xFFu;
-  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double(static_cast<long long>(static_cast<unsigned long long>(b >> 31) << 63));
-  if (ex == 0u || ex == 255u) return double(x);
-  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(b >> 31) << 63) |
-                                                     (static_cast<unsigned long long>(ex - 127u + 1023u) << 52) |
-                                                     (static_cast<unsigned long long>(b & 0x7FFFFFu) << 29)));
-}
-
-// float-float -> FP64: h + l rounded once (one FP64 add)
-__device__ __forceinline__ double pair_to_f64(float h, float l) { return f32_to_f64(h) + f32_to_f64(l); }
-
 // FP64 <-> float-float for every problem of a batch; to_ff also clears each max|r| pair.
 struct ConvProblem {
   double* u;
@@ -411,9 +406,33 @@ __global__ void __launch_bounds__(256) convert_multi_kernel(const ConvProblem* _
   }
 }
 
-__global__ void f64_to_ff_kernel(const double* __restrict__ u, float* __restrict__ uh,
-                                 float* __restrict__ ul, int64_t n) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+// FP64 <-> float-float over n values, two per thread and iteration when the arrays allow it
+// (the FP64 one 16-byte aligned, the float ones 8-byte aligned): a warp then reads and writes
+// whole contiguous runs (256 bytes of each float array, 512 of the FP64 one), which also keeps
+// writes over the host link to a mapped host state in whole lines. An odd last value, or
+// unaligned arrays, go one by one.
+__device__ __forceinline__ bool pairs_aligned(const void* u64, const void* a, const void* b) {
+  return (reinterpret_cast<uintptr_t>(u64) & 15u) == 0 &&
+         ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 7u) == 0;
+}
+
+__global__ void __launch_bounds__(256) f64_to_ff_kernel(const double* __restrict__ u, float* __restrict__ uh,
+                                                        float* __restrict__ ul, int64_t n) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t done = 0;
+  if (pairs_aligned(u, uh, ul)) {
+    const int64_t n2 = n >> 1;
+    for (int64_t k = t; k < n2; k += stride) {
+      const double2 v = reinterpret_cast<const double2*>(u)[k];
+      float2 h, l;
+      f64_to_pair(v.x, h.x, l.x);
+      f64_to_pair(v.y, h.y, l.y);
+      reinterpret_cast<float2*>(uh)[k] = h;
+      reinterpret_cast<float2*>(ul)[k] = l;
+    }
+    done = n2 << 1;
+  }
+  for (int64_t i = done + t; i < n; i += stride) {
     float h, l;
     f64_to_pair(u[i], h, l);
     uh[i] = h;
@@ -421,10 +440,20 @@ __global__ void f64_to_ff_kernel(const double* __restrict__ u, float* __restrict
   }
 }
 
-__global__ void ff_to_f64_kernel(const float* __restrict__ uh, const float* __restrict__ ul,
-                                 double* __restrict__ u, int64_t n) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    u[i] = pair_to_f64(uh[i], ul[i]);
+__global__ void __launch_bounds__(256) ff_to_f64_kernel(const float* __restrict__ uh, const float* __restrict__ ul,
+                                                        double* __restrict__ u, int64_t n) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t done = 0;
+  if (pairs_aligned(u, uh, ul)) {
+    const int64_t n2 = n >> 1;
+    for (int64_t k = t; k < n2; k += stride) {
+      const float2 h = reinterpret_cast<const float2*>(uh)[k];
+      const float2 l = reinterpret_cast<const float2*>(ul)[k];
+      reinterpret_cast<double2*>(u)[k] = make_double2(pair_to_f64(h.x, l.x), pair_to_f64(h.y, l.y));
+    }
+    done = n2 << 1;
+  }
+  for (int64_t i = done + t; i < n; i += stride) u[i] = pair_to_f64(uh[i], ul[i]);
 }
 
 // Per owner row i of P (FP64, n_int x n_loc, window row-major): eP_i with
@@ -1309,7 +1338,8 @@ static lem_status split_pack(lem_ctx* ctx) {
 // its own (a measuring pass) unless carry_in, in which case d_carry holds the previous step's
 // max|r| from an earlier run on the same state. With d_carry, the last step's max|r| is left
 // there, so a run split into several calls gives the same result bit for bit as one call.
-lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in) {
+lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d_carry, bool carry_in,
+                     const double* in64) {
   SplitPlan* sp = ctx->split;
   cudaStream_t st = ctx->stream;
   if (sp->packed_gen != ctx->build_gen) LEM_TRY(split_pack(ctx));
@@ -1317,6 +1347,10 @@ lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d
   LEM_CUDA_TRY(cudaMemsetAsync(sp->d_rmax, 0, sizeof(unsigned) * 2, st));
   if (carry_in && d_carry) {
     LEM_CUDA_TRY(cudaMemcpyAsync(sp->d_rmax, d_carry, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+  } else if (in64) {
+    // the same measuring pass, on the FP64 state, which it converts to (uh, ul) as it goes
+    residual_measure_f64_kernel<<<rgrid, 256, 0, st>>>(in64, uh, ul, sp->rp, sp->d_rmax, sp->d_escale);
+    LEM_CUDA_TRY(cudaGetLastError());
   } else {
     // measure max|r| of the first step into rmax[0] (the measuring pass reads rmax[1] only
     // to form a scale it never uses)
@@ -1366,22 +1400,27 @@ lem_status split_run(lem_ctx* ctx, float* uh, float* ul, int nsteps, unsigned* d
 // FP64 state <-> float-float state on the context stream (every float-float state the split
 // kernels leave is normalised, |ul| <= ulp(uh) / 2, so the conversion to float-float of a value
 // they wrote returns the same pair).
+// (eight 256-thread blocks per SM)
 lem_status split_to_ff(lem_ctx* ctx, const double* d_u, float* uh, float* ul) {
-  f64_to_ff_kernel<<<1024, 256, 0, ctx->stream>>>(d_u, uh, ul, ctx->npts);
+  f64_to_ff_kernel<<<8 * ctx->split->nsm, 256, 0, ctx->stream>>>(d_u, uh, ul, ctx->npts);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
 }
 
 lem_status split_from_ff(lem_ctx* ctx, const float* uh, const float* ul, double* d_u) {
-  ff_to_f64_kernel<<<1024, 256, 0, ctx->stream>>>(uh, ul, d_u, ctx->npts);
+  ff_to_f64_kernel<<<8 * ctx->split->nsm, 256, 0, ctx->stream>>>(uh, ul, d_u, ctx->npts);
   LEM_CUDA_TRY(cudaGetLastError());
   return LEM_OK;
 }
 
-lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps) {
+lem_status split_step(lem_ctx* ctx, double* d_u, int nsteps, bool fuse_io) {
   SplitPlan* sp = ctx->split;
-  LEM_TRY(split_to_ff(ctx, d_u, sp->d_uh, sp->d_ul));
-  LEM_TRY(split_run(ctx, sp->d_uh, sp->d_ul, nsteps, nullptr, false));
+  if (fuse_io && nsteps > 0) {
+    LEM_TRY(split_run(ctx, sp->d_uh, sp->d_ul, nsteps, nullptr, false, d_u));
+  } else {
+    LEM_TRY(split_to_ff(ctx, d_u, sp->d_uh, sp->d_ul));
+    LEM_TRY(split_run(ctx, sp->d_uh, sp->d_ul, nsteps, nullptr, false));
+  }
   return split_from_ff(ctx, sp->d_uh, sp->d_ul, d_u);
 }
 

@@ -224,6 +224,33 @@ def test_step_host_pinned_pageable_and_device_agree_bit_for_bit(prec):
     assert np.array_equal(hq, ref)
 
 
+@pytest.mark.parametrize("prec", ["split", "split_fast"])
+@pytest.mark.parametrize("nsteps", [1, 4])
+@pytest.mark.parametrize("side,tile,H", [
+    (160, 32, 8),              # 5 x 5 tiles; the padded 176-wide grid ends in a part tile
+    (24, 8, 4),                # mesh smaller than one 64 x 32 residual tile: every halo wraps
+    (96, 16, 5),               # 26-wide windows
+    (128, (32, 16), (16, 8)),  # anisotropic windows (64 x 32)
+])
+def test_device_state_conversion_in_measuring_pass_matches_streaming_one(prec, nsteps, side, tile, H):
+    """On a device state the measuring residual pass converts the FP64 state to float-float as
+    it stages it (each mesh node written once); on a mapped pinned host state a separate
+    streaming kernel converts it over the host link. Two calls in a row on each must give the
+    same bits."""
+    wl = W.advdiff2d(side=side, tile=tile, overlap=H, nu=7.0, a=(2.0, 1.0), dt=2.0, ell=8.0, seed=13)
+    dev, pin = (L.Lem.from_workload(wl, prec=prec) for _ in range(2))
+    assert dev.info()["split_path"] == 1
+    pin.build()
+    u = torch.tensor(wl["u0"], device="cuda")
+    hp = torch.tensor(wl["u0"]).pin_memory()
+    for _ in range(2):
+        dev.step(u, nsteps)
+        pin.step_host(hp.numpy(), nsteps)
+        dev.sync()
+        assert np.array_equal(hp.numpy(), u.cpu().numpy())
+    assert not np.array_equal(hp.numpy(), wl["u0"])
+
+
 def test_balanced_last_wave_matches_whole_units(monkeypatch):
     """1792^2 (tiles 32, 224 units of 128 owner rows x 128 windows on a 152-SM GB300): the
     full wave runs whole units and the remaining 72 units' window rows are spread over every
